@@ -1,0 +1,222 @@
+/*
+ * mb.h — C ABI of the GB300 rigid multiblob mobility library (libmb.so).
+ *
+ * The library solves the mobility problem of rigid multiblob bodies above a
+ * no-slip wall at z = 0 (Balboa Usabiaga et al., "Hydrodynamics of
+ * Suspensions of Passive and Active Rigid Particles: A Rigid Multiblob
+ * Approach", Sections 2.1-2.2 and 5) on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ *   Arrays are contiguous, row-major, FP64 unless stated: positions r and
+ *   blob vectors are N x 3, body vectors n_b x 3, quaternions n_b x 4 with the
+ *   scalar first (s, x, y, z), rotation R = (s^2 - v.v) I + 2 v v^T + 2 s [v]x.
+ *   Body p owns blobs blob_start[p] .. blob_start[p+1]-1 (int64 CSR offsets).
+ *   Units are arbitrary but consistent; a is the blob radius, eta the
+ *   viscosity.  wall != 0 adds the single-wall correction, wall == 0 gives the
+ *   unbounded-domain RPY mobility.
+ *
+ *   Pointers are DEVICE pointers owned by the caller unless a call says
+ *   otherwise; the library never frees them.  Calls are stream-ordered on the
+ *   given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *   stream).  Argument errors are detected on the host and returned before
+ *   any work is queued.  A context may be used by one host thread and one
+ *   stream at a time; it owns all workspace (packed positions, factors,
+ *   Krylov basis), grown on demand up to its HBM budget.
+ *
+ *   Every call returns an mb_status; mb_last_error() gives a message for the
+ *   last failing call on a context.  The library never aborts the process.
+ */
+#ifndef MB_H
+#define MB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MB_OK = 0,
+    MB_EINVAL = 1,         /* bad argument (null pointer, N < 0, a <= 0 ...) */
+    MB_ENOMEM = 2,         /* workspace would exceed the context's HBM budget,
+                              or cudaMalloc failed                           */
+    MB_ECUDA = 3,          /* a CUDA runtime call failed                      */
+    MB_ENOTCONVERGED = 4,  /* Krylov solver hit maxit; best iterate written   */
+    MB_ETIMEOUT = 5,       /* a bounded device wait ran out                   */
+    MB_ESINGULAR = 6       /* a Cholesky factorisation broke down (a body's
+                              mobility block not positive definite, e.g. a
+                              blob below z = a)                               */
+} mb_status;
+
+typedef enum {
+    MB_FP64 = 0,          /* pair kernel in FP64                               */
+    MB_FP32_KAHAN = 1,    /* pair kernel in FP32 (hi/lo positions, Kahan-
+                             compensated accumulation), result in FP64         */
+    MB_MIXED_REFINE = 2   /* solver only: FP32 pair kernel inside the Krylov
+                             iteration, FP64 pair kernel for the true residual
+                             of every restart (iterative refinement)           */
+} mb_precision;
+
+typedef struct mb_context mb_context;
+
+/* Solver parameters.  tol is the target of ||b - A x||_2 / ||b||_2 for the
+ * saddle-point system (Eq. saddle_M), measured with the FP64 pair kernel
+ * (or FP32 when prec == MB_FP32_KAHAN).  maxit caps the total number of
+ * Krylov iterations, restart the Krylov subspace size between restarts. */
+typedef struct {
+    double a;
+    double eta;
+    int wall;
+    double tol;
+    int maxit;
+    int restart;
+    mb_precision prec;
+} mb_params;
+
+typedef struct {
+    int iters;            /* Krylov iterations (matvecs inside Arnoldi)       */
+    int restarts;         /* completed restart cycles                         */
+    int converged;        /* 1 if rel_residual <= tol                         */
+    double rel_residual;  /* true relative residual of the returned solution  */
+    double setup_ms;      /* blob build + preconditioner setup, wall clock    */
+    double solve_ms;      /* Krylov solve, wall clock                         */
+} mb_info;
+
+/* Human-readable name of a status code (static storage). */
+const char *mb_status_string(mb_status s);
+
+/* Message describing the last failing call on ctx (valid until the next
+ * call on ctx; "" if none).  ctx may be NULL for context-creation errors. */
+const char *mb_last_error(const mb_context *ctx);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * workspace the context may allocate (0 = 90% of the device's free memory
+ * at creation).  *ctx receives the handle. */
+mb_status mb_context_create(mb_context **ctx, int device, size_t hbm_budget_bytes);
+
+/* Free the context and all its workspace.  Waits for the device. */
+mb_status mb_context_destroy(mb_context *ctx);
+
+/* Bytes of workspace currently held by the context. */
+size_t mb_context_workspace_bytes(const mb_context *ctx);
+
+/*
+ * Measurement support.  With profiling on, the library brackets every launch
+ * of the pair kernel (the O(N^2) direct sum) with CUDA events recorded on the
+ * launching stream.  mb_profile_read synchronises on those events and
+ * returns the summed pair-kernel time in milliseconds and the number of
+ * pair-kernel launches since the last reset; `kernel_launches` receives the
+ * number of kernels of any kind this process has launched through the
+ * library (a running count, never reset).  reset != 0 clears the recorded
+ * events.  Any output pointer may be NULL.
+ */
+mb_status mb_profile_enable(mb_context *ctx, int on);
+mb_status mb_profile_read(mb_context *ctx, double *pair_kernel_ms, int64_t *pair_launches,
+                          int64_t *kernel_launches, int reset);
+
+/*
+ * u = M(r) f — product of the blob-blob mobility with blob forces.
+ * Section 2.1.1: M_ij is the RPY tensor of Eq. RPYTensor (with its overlap
+ * regularisation for r_ij <= 2a; M_ii = I/(6 pi eta a)) plus, if wall != 0,
+ * the translation-translation Rotne-Prager-Blake correction for a no-slip
+ * wall at z = 0, W(x, y) = eta^-1 (1 + a^2/6 Lap_x)(1 + a^2/6 Lap_y) G_img(x, y)
+ * with G_img the image part of Blake's Green's function (Eq. MobilityFaxen).
+ * Section 5 evaluates this product by O(N^2) direct summation on a GPU; so
+ * does this call.
+ *
+ *   r, f : N x 3 positions and forces (read only)
+ *   u    : N x 3 velocities (written)
+ *   prec : MB_FP64 or MB_FP32_KAHAN
+ * r, f and u may all be device pointers (the call is asynchronous on
+ * `stream`) or all host pointers (staged through the context's workspace
+ * with copies on `stream`; the call returns after u is written; pinned host
+ * memory makes the copies faster).  Mixing kinds is MB_EINVAL.  With the
+ * wall, every z must be > 0 (blobs at z < a are computed as written but the
+ * matrix need not be positive definite); this is not checked.  N = 0 is a
+ * no-op.
+ */
+mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, int64_t n,
+                             double a, double eta, int wall, mb_precision prec, double *u,
+                             void *stream);
+
+/*
+ * Blob positions r_i = q_p + R(theta_p) rho_i for every blob i of body p
+ * (Section 2.1: tracking point q_p and orientation quaternion theta_p of the
+ * reference configuration rho).  Device pointers: q (n_b x 3), theta
+ * (n_b x 4, need not be normalised: it is normalised on the fly), blob_start
+ * (n_b + 1), rho (N x 3) -> r (N x 3), N = blob_start[n_b].  n_blobs must
+ * equal blob_start[n_b] (not checked on the device).
+ */
+mb_status mb_blob_positions(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                            const double *q, const double *theta, const int64_t *blob_start,
+                            const double *rho, double *r, void *stream);
+
+/*
+ * Kinematic map of Eq. noslip_rigid: v_i = U_p + Omega_p x (r_i - q_p) for
+ * each blob i of body p.  UO is n_b x 6 (U then Omega per body); v is N x 3.
+ */
+mb_status mb_K_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
+                     const double *q, const int64_t *blob_start, const double *UO, double *v,
+                     void *stream);
+
+/*
+ * Adjoint kinematic map (force and torque balance rows of Eq. rigidSystem):
+ * FT_p = (sum_i lambda_i, sum_i (r_i - q_p) x lambda_i) over the blobs of
+ * body p.  lambda is N x 3; FT is n_b x 6 (force then torque).
+ */
+mb_status mb_KT_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
+                      const double *q, const int64_t *blob_start, const double *lambda,
+                      double *FT, void *stream);
+
+/*
+ * Block-diagonal preconditioner setup (Section 2.2.2, Eqs.
+ * M_tilde_block_diag and indef_block_P): for every body p, assemble its
+ * blob mobility block M^(pp) (with the wall if wall != 0), factor it by FP64
+ * Cholesky, form the 6 x 6 body Schur complement N~_p =
+ * (K_p^T M^(pp)-1 K_p)^-1, and store the body's explicit inverse of the
+ * indefinite block [[M^(pp), -K_p], [-K_p^T, 0]] in the context.  r are the
+ * blob positions (device, N x 3).  Synchronises the stream; returns
+ * MB_ESINGULAR (with the first failing body in mb_last_error) if a block is
+ * not positive definite.
+ */
+mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
+                           const double *q, const int64_t *blob_start, double a, double eta,
+                           int wall, void *stream);
+
+/*
+ * Apply the preconditioner set up by the last mb_precond_setup on ctx:
+ * solve [[M~, -K], [-K^T, 0]] [lambda; UO] = [w; g] (Eq. saddle_M_precon)
+ * body by body.  w, lambda: N x 3; g, UO: n_b x 6 (device).
+ */
+mb_status mb_precond_apply(mb_context *ctx, const double *w, const double *g, double *lambda,
+                           double *UO, void *stream);
+
+/*
+ * Solve the mobility problem (Eq. saddle_M):
+ *   [[M, -K], [-K^T, 0]] [lambda; U] = [slip; -F]
+ * for the blob constraint forces lambda and the rigid-body motions (U, Omega)
+ * by right-preconditioned flexible GMRES with the block-diagonal
+ * preconditioner (Section 2.2), initial guess zero, restarted every
+ * params->restart iterations on the true residual.
+ *
+ *   q, theta, blob_start, rho : bodies (device; see mb_blob_positions)
+ *   F, T    : n_b x 3 applied forces and torques (device)
+ *   slip    : N x 3 apparent slip (Eq. noslip_explicit) or NULL for none
+ *   U, Omega: n_b x 3 outputs; lambda: N x 3 output (device)
+ *   info    : host struct, may be NULL
+ * Synchronises the stream.  Returns MB_ENOTCONVERGED (with the best
+ * iterate written) if maxit is reached, MB_ESINGULAR if a body block is not
+ * positive definite.
+ */
+mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *q,
+                            const double *theta, const int64_t *blob_start, const double *rho,
+                            const double *F, const double *T, const double *slip,
+                            const mb_params *params, double *U, double *Omega, double *lambda,
+                            mb_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MB_H */

@@ -1,1 +1,309 @@
-"""GB300-native rigid multiblob mobility solver (wall-corrected RPY)."""
+"""GB300-native rigid multiblob mobility solver (wall-corrected RPY).
+
+Thin Python binding over the C ABI of libmb.so (include/mb.h).  It only
+marshals arguments: every step runs in the library's CUDA kernels.  Arrays are
+torch tensors (float64, contiguous; int64 for blob offsets) on the context's
+CUDA device, or CPU tensors where a call accepts host memory.  If libmb.so has
+not been built, every call raises — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "MBError",
+    "Context",
+    "FP64",
+    "FP32_KAHAN",
+    "MIXED_REFINE",
+    "library_path",
+    "load_library",
+    "EXPORTED_SYMBOLS",
+]
+
+FP64, FP32_KAHAN, MIXED_REFINE = 0, 1, 2
+_PREC = {"fp64": FP64, "fp32": FP32_KAHAN, "fp32_kahan": FP32_KAHAN, "mixed": MIXED_REFINE}
+
+STATUS = {
+    0: "MB_OK",
+    1: "MB_EINVAL",
+    2: "MB_ENOMEM",
+    3: "MB_ECUDA",
+    4: "MB_ENOTCONVERGED",
+    5: "MB_ETIMEOUT",
+    6: "MB_ESINGULAR",
+}
+
+EXPORTED_SYMBOLS = [
+    "mb_status_string",
+    "mb_last_error",
+    "mb_context_create",
+    "mb_context_destroy",
+    "mb_context_workspace_bytes",
+    "mb_profile_enable",
+    "mb_profile_read",
+    "mb_mobility_matvec",
+    "mb_blob_positions",
+    "mb_K_apply",
+    "mb_KT_apply",
+    "mb_precond_setup",
+    "mb_precond_apply",
+    "mb_solve_mobility",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libmb.so")
+
+
+class MBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("wall", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("maxit", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("prec", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("rel_residual", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library():
+    """Load libmb.so (built by paper_1602_02170_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not built ({path} missing); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first"
+        )
+    L = ctypes.CDLL(path)
+    vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.mb_status_string.restype = ctypes.c_char_p
+    L.mb_status_string.argtypes = [ci]
+    L.mb_last_error.restype = ctypes.c_char_p
+    L.mb_last_error.argtypes = [vp]
+    L.mb_context_create.argtypes = [ctypes.POINTER(vp), ci, ctypes.c_size_t]
+    L.mb_context_destroy.argtypes = [vp]
+    L.mb_context_workspace_bytes.restype = ctypes.c_size_t
+    L.mb_context_workspace_bytes.argtypes = [vp]
+    L.mb_profile_enable.argtypes = [vp, ci]
+    L.mb_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64), ci]
+    L.mb_mobility_matvec.argtypes = [vp, vp, vp, i64, dbl, dbl, ci, ci, vp, vp]
+    L.mb_blob_positions.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mb_K_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mb_KT_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mb_precond_setup.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, ci, vp]
+    L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.mb_solve_mobility.argtypes = [
+        vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
+        ctypes.POINTER(Info), vp,
+    ]
+    for name in EXPORTED_SYMBOLS:
+        if name not in ("mb_status_string", "mb_last_error", "mb_context_workspace_bytes"):
+            getattr(L, name).restype = ci  # mb_status
+    _lib = L
+    return L
+
+
+def _prec(p) -> int:
+    if isinstance(p, str):
+        return _PREC[p.lower()]
+    return int(p)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context on one CUDA device (owns all workspace)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        import torch
+
+        self._torch = torch
+        self.L = load_library()
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        st = self.L.mb_context_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if st != 0:
+            raise MBError(st, self.L.mb_last_error(None).decode())
+        self.handle = h
+
+    # ------------------------------------------------------------ plumbing
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.L.mb_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != 0:
+            raise MBError(st, self.L.mb_last_error(self.handle).decode())
+
+    def _stream(self, stream):
+        if stream is None:
+            stream = self._torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    def workspace_bytes(self) -> int:
+        return int(self.L.mb_context_workspace_bytes(self.handle))
+
+    def profile_enable(self, on: bool = True):
+        self._check(self.L.mb_profile_enable(self.handle, int(bool(on))))
+
+    def profile_read(self, reset: bool = True):
+        """(summed pair-kernel ms, pair-kernel launches, running kernel-launch count)."""
+        ms = ctypes.c_double()
+        pl = ctypes.c_int64()
+        kl = ctypes.c_int64()
+        self._check(self.L.mb_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(pl),
+                                           ctypes.byref(kl), int(bool(reset))))
+        return ms.value, pl.value, kl.value
+
+    def _dev(self, t, shape=None, dtype=None):
+        torch = self._torch
+        dtype = dtype or torch.float64
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous {dtype} CUDA tensor")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return t
+
+    # ------------------------------------------------------------ calls
+    def mobility_matvec(self, r, f, a, eta=1.0, wall=True, prec="fp32", out=None, stream=None):
+        """u = M(r) f.  r, f: (N, 3) float64, all on the GPU or all on the
+        host (then the library stages them and returns after u is written)."""
+        torch = self._torch
+        n = int(r.shape[0])
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=r.device)
+        for t in (r, f, out):
+            if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (n, 3):
+                raise ValueError("r, f, out must be contiguous float64 (N, 3)")
+        st = self.L.mb_mobility_matvec(
+            self.handle, _ptr(r), _ptr(f), n, float(a), float(eta), int(bool(wall)), _prec(prec),
+            _ptr(out), self._stream(stream),
+        )
+        self._check(st)
+        return out
+
+    def blob_positions(self, q, theta, blob_start, rho, out=None, stream=None):
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(rho.shape[0])
+        self._dev(q, (nb, 3)); self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=q.device)
+        self._check(self.L.mb_blob_positions(
+            self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(out),
+            self._stream(stream)))
+        return out
+
+    def K_apply(self, r, q, blob_start, UO, out=None, stream=None):
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(r.shape[0])
+        self._dev(r, (n, 3)); self._dev(q, (nb, 3)); self._dev(UO, (nb, 6))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=r.device)
+        self._check(self.L.mb_K_apply(self.handle, nb, n, _ptr(r), _ptr(q), _ptr(blob_start),
+                                      _ptr(UO), _ptr(out), self._stream(stream)))
+        return out
+
+    def KT_apply(self, r, q, blob_start, lam, out=None, stream=None):
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(r.shape[0])
+        self._dev(r, (n, 3)); self._dev(q, (nb, 3)); self._dev(lam, (n, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if out is None:
+            out = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
+        self._check(self.L.mb_KT_apply(self.handle, nb, n, _ptr(r), _ptr(q), _ptr(blob_start),
+                                       _ptr(lam), _ptr(out), self._stream(stream)))
+        return out
+
+    def precond_setup(self, r, q, blob_start, a, eta=1.0, wall=True, stream=None):
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(r.shape[0])
+        self._dev(r, (n, 3)); self._dev(q, (nb, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        self._check(self.L.mb_precond_setup(self.handle, nb, n, _ptr(r), _ptr(q),
+                                            _ptr(blob_start), float(a), float(eta),
+                                            int(bool(wall)), self._stream(stream)))
+
+    def precond_apply(self, w, g, stream=None):
+        torch = self._torch
+        lam = torch.empty_like(w)
+        UO = torch.empty_like(g)
+        self._dev(w); self._dev(g)
+        self._check(self.L.mb_precond_apply(self.handle, _ptr(w), _ptr(g), _ptr(lam), _ptr(UO),
+                                            self._stream(stream)))
+        return lam, UO
+
+    def solve_mobility(self, q, theta, blob_start, rho, F, T, a, eta=1.0, wall=True, slip=None,
+                       tol=1e-10, maxit=200, restart=100, prec="fp64", stream=None,
+                       raise_on_nonconvergence=True):
+        """Solve Eq. saddle_M; returns (U, Omega, lambda, info dict)."""
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(rho.shape[0])
+        self._dev(q, (nb, 3)); self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
+        self._dev(F, (nb, 3)); self._dev(T, (nb, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if slip is not None:
+            self._dev(slip, (n, 3))
+        U = torch.empty((nb, 3), dtype=torch.float64, device=q.device)
+        Om = torch.empty((nb, 3), dtype=torch.float64, device=q.device)
+        lam = torch.empty((n, 3), dtype=torch.float64, device=q.device)
+        p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
+                   _prec(prec))
+        info = Info()
+        st = self.L.mb_solve_mobility(
+            self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(F),
+            _ptr(T), _ptr(slip), ctypes.byref(p), _ptr(U), _ptr(Om), _ptr(lam),
+            ctypes.byref(info), self._stream(stream))
+        if st == 4 and not raise_on_nonconvergence:
+            return U, Om, lam, info.as_dict()
+        self._check(st)
+        return U, Om, lam, info.as_dict()

@@ -1,0 +1,144 @@
+// Rigid-body geometry and kinematics on the blobs.
+//   blob build:  r_i = q_p + R(theta_p) rho_i                    (Section 2.1)
+//   K:           v_i = U_p + Omega_p x (r_i - q_p)               (Eq. noslip_rigid)
+//   K^T:         (sum_i lambda_i, sum_i (r_i - q_p) x lambda_i)  (Eq. rigidSystem)
+// One thread per blob for the gathers (the body is found by binary search in
+// the CSR offsets), one warp per body for the segmented reduction of K^T.
+#include <algorithm>
+
+#include "mb_internal.cuh"
+
+namespace mb {
+namespace {
+
+__device__ __forceinline__ int64_t body_of(const int64_t *__restrict__ start, int64_t nb, int64_t i)
+{
+    int64_t lo = 0, hi = nb;  // invariant: start[lo] <= i < start[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (start[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void blob_positions_kernel(int64_t nb, int64_t n, const double *__restrict__ q,
+                                      const double *__restrict__ theta,
+                                      const int64_t *__restrict__ start,
+                                      const double *__restrict__ rho, double *__restrict__ r)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = body_of(start, nb, i);
+        double s = theta[4 * p], x = theta[4 * p + 1], y = theta[4 * p + 2], z = theta[4 * p + 3];
+        const double inv = rsqrt(s * s + x * x + y * y + z * z);
+        s *= inv; x *= inv; y *= inv; z *= inv;
+        const double a = rho[3 * i], b = rho[3 * i + 1], c = rho[3 * i + 2];
+        // R = (s^2 - v.v) I + 2 v v^T + 2 s [v]_x, applied to (a, b, c)
+        const double d = s * s - (x * x + y * y + z * z);
+        const double vr = x * a + y * b + z * c;
+        r[3 * i + 0] = q[3 * p + 0] + d * a + 2.0 * x * vr + 2.0 * s * (y * c - z * b);
+        r[3 * i + 1] = q[3 * p + 1] + d * b + 2.0 * y * vr + 2.0 * s * (z * a - x * c);
+        r[3 * i + 2] = q[3 * p + 2] + d * c + 2.0 * z * vr + 2.0 * s * (x * b - y * a);
+    }
+}
+
+__global__ void K_apply_kernel(int64_t nb, int64_t n, const double *__restrict__ r,
+                               const double *__restrict__ q, const int64_t *__restrict__ start,
+                               const double *__restrict__ UO, double *__restrict__ v, double alpha,
+                               double beta)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = body_of(start, nb, i);
+        const double dx = r[3 * i] - q[3 * p], dy = r[3 * i + 1] - q[3 * p + 1],
+                     dz = r[3 * i + 2] - q[3 * p + 2];
+        const double *u = UO + 6 * p;
+        const double vx = u[0] + (u[4] * dz - u[5] * dy);
+        const double vy = u[1] + (u[5] * dx - u[3] * dz);
+        const double vz = u[2] + (u[3] * dy - u[4] * dx);
+        if (beta == 0.0) {
+            v[3 * i] = alpha * vx;
+            v[3 * i + 1] = alpha * vy;
+            v[3 * i + 2] = alpha * vz;
+        } else {
+            v[3 * i] = alpha * vx + beta * v[3 * i];
+            v[3 * i + 1] = alpha * vy + beta * v[3 * i + 1];
+            v[3 * i + 2] = alpha * vz + beta * v[3 * i + 2];
+        }
+    }
+}
+
+__global__ void KT_apply_kernel(int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
+                                const int64_t *__restrict__ start, const double *__restrict__ lam,
+                                double *__restrict__ FT, double alpha)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < nb;
+         p += warps) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        for (int64_t i = start[p] + lane; i < start[p + 1]; i += 32) {
+            const double lx = lam[3 * i], ly = lam[3 * i + 1], lz = lam[3 * i + 2];
+            const double dx = r[3 * i] - qx, dy = r[3 * i + 1] - qy, dz = r[3 * i + 2] - qz;
+            acc[0] += lx;
+            acc[1] += ly;
+            acc[2] += lz;
+            acc[3] += dy * lz - dz * ly;
+            acc[4] += dz * lx - dx * lz;
+            acc[5] += dx * ly - dy * lx;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        if (lane < 6) {
+            double v = acc[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (lane == c) v = acc[c];
+            FT[6 * p + lane] = alpha * v;
+        }
+    }
+}
+
+int grid_for(int64_t work, int threads)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), 4096));
+}
+
+}  // namespace
+
+mb_status blob_positions(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                         const double *theta, const int64_t *blob_start, const double *rho,
+                         double *r, cudaStream_t s)
+{
+    if (n == 0) return MB_OK;
+    blob_positions_kernel<<<grid_for(n, 256), 256, 0, s>>>(nb, n, q, theta, blob_start, rho, r);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    return MB_OK;
+}
+
+void launch_K_apply(int64_t nb, int64_t n, const double *r, const double *q,
+                    const int64_t *blob_start, const double *UO, double *v, double alpha,
+                    double beta, cudaStream_t s)
+{
+    if (n == 0) return;
+    K_apply_kernel<<<grid_for(n, 256), 256, 0, s>>>(nb, n, r, q, blob_start, UO, v, alpha, beta);
+    count_launch();
+}
+
+void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
+                     const double *lambda, double *FT, double alpha, cudaStream_t s)
+{
+    if (nb == 0) return;
+    KT_apply_kernel<<<grid_for(nb * 32, 256), 256, 0, s>>>(nb, r, q, blob_start, lambda, FT, alpha);
+    count_launch();
+}
+
+}  // namespace mb

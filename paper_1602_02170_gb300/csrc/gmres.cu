@@ -1,0 +1,406 @@
+// Right-preconditioned flexible GMRES on the saddle-point system (Eq. saddle_M)
+//     A [lambda; U] = [M lambda - K U; -K^T lambda] = [slip; -F]
+// with the block-diagonal preconditioner of Section 2.2.2 (precond.cu).
+//
+// Vectors are packed as x = [lambda (3N) | (U, Omega) per body (6 n_b)] in
+// FP64 and stay on the device.  Each Arnoldi step: z_j = P^-1 v_j, w = A z_j,
+// classical Gram-Schmidt applied twice (CGS2), Givens rotations on the
+// device.  The preconditioned vectors z_j are kept (flexible variant), so the
+// update x += Z y is exact even when P^-1 or the inner matvec are inexact.
+// Every restart recomputes the true residual b - A x; with MB_MIXED_REFINE
+// the Arnoldi matvecs use the FP32 pair kernel and the restart residual the
+// FP64 one, which turns restarts into iterative refinement (the inexact-
+// Krylov remark of Section 2.2.1).  Termination is on the true residual,
+// as right preconditioning allows (Section 3, preconditioner discussion).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "mb_internal.cuh"
+
+namespace mb {
+namespace {
+
+constexpr int kRedBlocks = 256;
+constexpr int kRedThreads = 256;
+
+// partial[k * nblk + b] = sum over block b's slice of V[k] . w, for k < nk
+__global__ void multidot_kernel(const double *__restrict__ V, int64_t ld, int nk,
+                                const double *__restrict__ w, int64_t L, double *__restrict__ partial)
+{
+    __shared__ double red[kRedThreads / 32];
+    const int k = blockIdx.y;
+    const double *v = V + (int64_t)k * ld;
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x)
+        acc += v[e] * w[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (kRedThreads / 32) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// out[k] (+)= sum_b partial[k * nblk + b]; one warp per k, fixed order
+__global__ void finish_dots_kernel(const double *__restrict__ partial, int nblk, int nk,
+                                   double *__restrict__ out, int accumulate)
+{
+    const int k = blockIdx.x;
+    if (k >= nk) return;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) acc += partial[k * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[k] = accumulate ? out[k] + acc : acc;
+}
+
+// w -= sum_k V[k] h[k]
+__global__ void subtract_span_kernel(const double *__restrict__ V, int64_t ld, int nk,
+                                     const double *__restrict__ h, double *__restrict__ w, int64_t L)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = w[e];
+        for (int k = 0; k < nk; ++k) acc -= V[(int64_t)k * ld + e] * h[k];
+        w[e] = acc;
+    }
+}
+
+// y = x / d with d = *denom (or sqrt(*denom)); y may alias x
+__global__ void scale_kernel(const double *x, double *y, int64_t L, const double *denom,
+                             int use_sqrt)
+{
+    double d = *denom;
+    if (use_sqrt) d = sqrt(d);
+    const double s = d > 0.0 ? 1.0 / d : 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = s * x[e];
+}
+
+// z = a - b
+__global__ void sub_kernel(const double *__restrict__ a, const double *__restrict__ b,
+                           double *__restrict__ z, int64_t L)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x)
+        z[e] = a[e] - b[e];
+}
+
+// x += sum_k Z[k] y[k]
+__global__ void add_span_kernel(const double *__restrict__ Z, int64_t ld, int nk,
+                                const double *__restrict__ y, double *__restrict__ x, int64_t L)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = x[e];
+        for (int k = 0; k < nk; ++k) acc += Z[(int64_t)k * ld + e] * y[k];
+        x[e] = acc;
+    }
+}
+
+// Small Krylov state in one device array:
+//   H[(m+1) x m] column-major (H[i + j*(m+1)]), cs[m], sn[m], g[m+1], y[m],
+//   h[m+1] (current column), nrm2 (squared norm scratch), est
+struct Small {
+    int m;
+    __host__ __device__ int64_t H(int i, int j) const { return i + (int64_t)j * (m + 1); }
+    __host__ __device__ int64_t cs() const { return (int64_t)(m + 1) * m; }
+    __host__ __device__ int64_t sn() const { return cs() + m; }
+    __host__ __device__ int64_t g() const { return sn() + m; }
+    __host__ __device__ int64_t y() const { return g() + m + 1; }
+    __host__ __device__ int64_t h() const { return y() + m; }
+    __host__ __device__ int64_t nrm2() const { return h() + m + 1; }
+    __host__ __device__ int64_t est() const { return nrm2() + 1; }
+    __host__ __device__ int64_t total() const { return est() + 1; }
+};
+
+// Start a cycle: g = [beta, 0, ...], beta = sqrt(nrm2)
+__global__ void cycle_start_kernel(double *__restrict__ sm, Small L)
+{
+    const double beta = sqrt(sm[L.nrm2()]);
+    for (int i = 0; i <= L.m; ++i) sm[L.g() + i] = 0.0;
+    sm[L.g()] = beta;
+    sm[L.est()] = beta;
+}
+
+// Column j of H is h[0..j] with H[j+1, j] = sqrt(nrm2); apply the previous
+// rotations, form the new one and update g.  est = |g[j+1]|.
+__global__ void givens_kernel(double *__restrict__ sm, Small L, int j)
+{
+    double col[2];
+    for (int i = 0; i <= j; ++i) sm[L.H(i, j)] = sm[L.h() + i];
+    const double hn = sqrt(sm[L.nrm2()]);
+    sm[L.H(j + 1, j)] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double c = sm[L.cs() + i], s = sm[L.sn() + i];
+        col[0] = sm[L.H(i, j)];
+        col[1] = sm[L.H(i + 1, j)];
+        sm[L.H(i, j)] = c * col[0] + s * col[1];
+        sm[L.H(i + 1, j)] = -s * col[0] + c * col[1];
+    }
+    const double a = sm[L.H(j, j)], b = sm[L.H(j + 1, j)];
+    const double rr = hypot(a, b);
+    const double c = rr > 0.0 ? a / rr : 1.0;
+    const double s = rr > 0.0 ? b / rr : 0.0;
+    sm[L.cs() + j] = c;
+    sm[L.sn() + j] = s;
+    sm[L.H(j, j)] = rr;
+    sm[L.H(j + 1, j)] = 0.0;
+    const double gj = sm[L.g() + j];
+    sm[L.g() + j] = c * gj;
+    sm[L.g() + j + 1] = -s * gj;
+    sm[L.est()] = fabs(-s * gj);
+}
+
+// h[i] += y[i] for i <= j: the second CGS pass's coefficients (held in y)
+__global__ void merge_passes_kernel(double *__restrict__ sm, Small L, int j)
+{
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) sm[L.h() + i] += sm[L.y() + i];
+}
+
+// Back substitution R y = g for the leading k x k triangle.
+__global__ void solve_triangle_kernel(double *__restrict__ sm, Small L, int k)
+{
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = sm[L.g() + i];
+        for (int j = i + 1; j < k; ++j) acc -= sm[L.H(i, j)] * sm[L.y() + j];
+        const double d = sm[L.H(i, i)];
+        sm[L.y() + i] = d != 0.0 ? acc / d : 0.0;
+    }
+}
+
+// b = [slip or 0 ; -(F, T) interleaved per body]
+__global__ void build_rhs_kernel(int64_t n, int64_t nb, const double *__restrict__ slip,
+                                 const double *__restrict__ F, const double *__restrict__ T,
+                                 double *__restrict__ b)
+{
+    const int64_t L = 3 * n + 6 * nb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < 3 * n) {
+            b[e] = slip ? slip[e] : 0.0;
+        } else {
+            const int64_t k = e - 3 * n, p = k / 6, c = k % 6;
+            b[e] = c < 3 ? -F[3 * p + c] : -T[3 * p + c - 3];
+        }
+    }
+}
+
+__global__ void unpack_solution_kernel(int64_t n, int64_t nb, const double *__restrict__ x,
+                                       double *__restrict__ U, double *__restrict__ Om,
+                                       double *__restrict__ lam)
+{
+    const int64_t L = 3 * n + 6 * nb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < 3 * n) {
+            lam[e] = x[e];
+        } else {
+            const int64_t k = e - 3 * n, p = k / 6, c = k % 6;
+            if (c < 3) U[3 * p + c] = x[e];
+            else Om[3 * p + c - 3] = x[e];
+        }
+    }
+}
+
+int vec_grid(int64_t L) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 2048)); }
+
+struct Solver {
+    mb_context *ctx;
+    cudaStream_t s;
+    int64_t n, nb, L;
+    const double *r, *q;
+    const int64_t *start;
+    double a, eta;
+    int wall;
+    int m;
+    Small sl;
+    double *V, *Z, *b, *x, *w, *t, *sm, *partial;
+    double *hsm;  // pinned host mirror (2 doubles)
+
+    // y = A x with the pair kernel in precision `prec`
+    mb_status apply_A(const double *xin, double *y, mb_precision prec)
+    {
+        MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s));
+        launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
+        launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    }
+
+    // out[0..nk) = V[0..nk) . w  (accumulate: out += ...)
+    void dots(const double *Vb, int nk, const double *wv, double *out, int accumulate)
+    {
+        const int nblk = (int)std::min<int64_t>(kRedBlocks, ceil_div(L, kRedThreads));
+        multidot_kernel<<<dim3(nblk, nk), kRedThreads, 0, s>>>(Vb, L, nk, wv, L, partial);
+        count_launch();
+        finish_dots_kernel<<<nk, 32, 0, s>>>(partial, nblk, nk, out, accumulate);
+        count_launch();
+    }
+
+    mb_status read_est(double *est)
+    {
+        MB_CUDA_TRY(ctx, cudaMemcpyAsync(hsm, sm + sl.est(), sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+        MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        *est = hsm[0];
+        return MB_OK;
+    }
+};
+
+}  // namespace
+
+mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                         const double *theta, const int64_t *blob_start, const double *rho,
+                         const double *F, const double *T, const double *slip,
+                         const mb_params *p, double *U, double *Omega, double *lambda,
+                         mb_info *info, cudaStream_t s)
+{
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    const int m = std::max(1, std::min(p->restart, 500));
+    const int64_t L = 3 * n + 6 * nb;
+    Small sl{m};
+
+    MB_TRY(ensure(ctx, ctx->sol_r, sizeof(double) * 3 * n, "blob positions"));
+    MB_TRY(ensure(ctx, ctx->sol_V, sizeof(double) * L * (m + 1), "Krylov basis V"));
+    MB_TRY(ensure(ctx, ctx->sol_Z, sizeof(double) * L * m, "Krylov basis Z"));
+    MB_TRY(ensure(ctx, ctx->sol_b, sizeof(double) * L, "rhs"));
+    MB_TRY(ensure(ctx, ctx->sol_x, sizeof(double) * L, "iterate"));
+    MB_TRY(ensure(ctx, ctx->sol_w, sizeof(double) * L, "work vector"));
+    MB_TRY(ensure(ctx, ctx->sol_t, sizeof(double) * L, "work vector"));
+    MB_TRY(ensure(ctx, ctx->sol_small, sizeof(double) * (sl.total() + (m + 1) * kRedBlocks),
+                  "Krylov scalars"));
+    if (!ctx->host_small) MB_CUDA_TRY(ctx, cudaMallocHost(&ctx->host_small, 64));
+
+    double *r = (double *)ctx->sol_r.ptr;
+    MB_TRY(blob_positions(ctx, nb, n, q, theta, blob_start, rho, r, s));
+    MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s));
+    if (p->prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
+    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const auto t1 = clk::now();
+
+    Solver S;
+    S.ctx = ctx; S.s = s; S.n = n; S.nb = nb; S.L = L; S.r = r; S.q = q;
+    S.start = (const int64_t *)ctx->blob_start_copy.ptr;
+    S.a = p->a; S.eta = p->eta; S.wall = p->wall; S.m = m; S.sl = sl;
+    S.V = (double *)ctx->sol_V.ptr; S.Z = (double *)ctx->sol_Z.ptr;
+    S.b = (double *)ctx->sol_b.ptr; S.x = (double *)ctx->sol_x.ptr;
+    S.w = (double *)ctx->sol_w.ptr; S.t = (double *)ctx->sol_t.ptr;
+    S.sm = (double *)ctx->sol_small.ptr; S.partial = S.sm + sl.total();
+    S.hsm = (double *)ctx->host_small;
+
+    const mb_precision inner = p->prec == MB_FP64 ? MB_FP64 : MB_FP32_KAHAN;
+    const mb_precision outer = p->prec == MB_FP32_KAHAN ? MB_FP32_KAHAN : MB_FP64;
+    const int vg = vec_grid(L);
+
+    build_rhs_kernel<<<vg, 256, 0, s>>>(n, nb, slip, F, T, S.b);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaMemsetAsync(S.x, 0, sizeof(double) * L, s));
+    S.dots(S.b, 1, S.b, S.sm + sl.nrm2(), 0);
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    double bnorm2 = 0.0;
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(S.hsm, S.sm + sl.nrm2(), sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    bnorm2 = S.hsm[0];
+    const double bnorm = std::sqrt(bnorm2);
+
+    int iters = 0, restarts = 0, converged = 0;
+    double rel = 0.0;
+    if (!(bnorm > 0.0)) {
+        converged = 1;  // x = 0 solves b = 0
+    } else {
+        for (;;) {
+            // true residual w = b - A x
+            if (iters == 0) {
+                MB_CUDA_TRY(ctx, cudaMemcpyAsync(S.w, S.b, sizeof(double) * L,
+                                                 cudaMemcpyDeviceToDevice, s));
+            } else {
+                MB_TRY(S.apply_A(S.x, S.t, outer));
+                sub_kernel<<<vg, 256, 0, s>>>(S.b, S.t, S.w, L);
+                count_launch();
+            }
+            S.dots(S.w, 1, S.w, S.sm + sl.nrm2(), 0);
+            cycle_start_kernel<<<1, 1, 0, s>>>(S.sm, sl);
+            count_launch();
+            double beta = 0.0;
+            MB_TRY(S.read_est(&beta));
+            rel = beta / bnorm;
+            if (!std::isfinite(rel))
+                return set_err(ctx, MB_ESINGULAR, "non-finite residual (check blob heights)");
+            if (rel <= p->tol) {
+                converged = 1;
+                break;
+            }
+            if (iters >= p->maxit) break;
+            // inner tolerance: the final target, or (mixed) a 1e-5 reduction per cycle
+            double inner_abs = 0.5 * p->tol * bnorm;
+            if (p->prec == MB_MIXED_REFINE) inner_abs = std::max(inner_abs, 1e-5 * beta);
+            scale_kernel<<<vg, 256, 0, s>>>(S.w, S.V, L, S.sm + sl.nrm2(), 1);
+            count_launch();
+            int k = 0;
+            for (int j = 0; j < m && iters < p->maxit; ++j) {
+                double *vj = S.V + (int64_t)j * L;
+                double *zj = S.Z + (int64_t)j * L;
+                double *vn = S.V + (int64_t)(j + 1) * L;
+                precond_apply_packed(ctx, vj, zj, s);
+                MB_TRY(S.apply_A(zj, vn, inner));
+                // CGS2
+                S.dots(S.V, j + 1, vn, S.sm + sl.h(), 0);
+                subtract_span_kernel<<<vg, 256, 0, s>>>(S.V, L, j + 1, S.sm + sl.h(), vn, L);
+                count_launch();
+                S.dots(S.V, j + 1, vn, S.sm + sl.y(), 0);
+                subtract_span_kernel<<<vg, 256, 0, s>>>(S.V, L, j + 1, S.sm + sl.y(), vn, L);
+                count_launch();
+                S.dots(vn, 1, vn, S.sm + sl.nrm2(), 0);
+                // merge the two Gram-Schmidt passes into column j, then rotate
+                merge_passes_kernel<<<1, 32, 0, s>>>(S.sm, sl, j);
+                count_launch();
+                MB_CUDA_TRY(ctx, cudaGetLastError());
+                ++iters;
+                k = j + 1;
+                givens_kernel<<<1, 1, 0, s>>>(S.sm, sl, j);
+                count_launch();
+                scale_kernel<<<vg, 256, 0, s>>>(vn, vn, L, S.sm + sl.nrm2(), 1);
+                count_launch();
+                double est = 0.0;
+                MB_TRY(S.read_est(&est));
+                if (!(est > inner_abs)) break;
+            }
+            solve_triangle_kernel<<<1, 1, 0, s>>>(S.sm, sl, k);
+            count_launch();
+            add_span_kernel<<<vg, 256, 0, s>>>(S.Z, L, k, S.sm + sl.y(), S.x, L);
+            count_launch();
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+            ++restarts;
+        }
+    }
+    unpack_solution_kernel<<<vg, 256, 0, s>>>(n, nb, S.x, U, Omega, lambda);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const auto t2 = clk::now();
+    if (info) {
+        info->iters = iters;
+        info->restarts = restarts;
+        info->converged = converged;
+        info->rel_residual = rel;
+        info->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        info->solve_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    }
+    if (!converged)
+        return set_err(ctx, MB_ENOTCONVERGED, "GMRES reached maxit=%d with relative residual %.3e",
+                       p->maxit, rel);
+    return MB_OK;
+}
+
+}  // namespace mb

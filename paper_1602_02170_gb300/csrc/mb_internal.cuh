@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libmb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mb.h"
+
+namespace mb {
+
+// A grow-only device buffer owned by a context.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace mb
+
+struct mb_context {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;   // HBM bytes the context may hold
+    size_t held = 0;     // bytes currently allocated
+    std::string err;
+
+    // matvec workspace
+    mb::DevBuf pos_hi, pos_lo;   // packed float4 positions (FP32 path)
+    mb::DevBuf partial;          // per-source-chunk partial velocities (FP64)
+    mb::DevBuf stage_r, stage_f, stage_u;  // staging for host-pointer calls
+
+    // preconditioner (last mb_precond_setup)
+    mb::DevBuf pinv;             // per-body explicit inverse, (3n_p+6)^2 doubles
+    mb::DevBuf pinv_off;         // int64 offsets into pinv, n_b + 1
+    mb::DevBuf blob_start_copy;  // int64 copy of blob_start used by apply
+    mb::DevBuf flag;             // int status flags written by kernels
+    int64_t pc_nb = 0, pc_n = 0;
+    int pc_max_np = 0;
+
+    // solver workspace
+    mb::DevBuf sol_r;            // blob positions
+    mb::DevBuf sol_V, sol_Z;     // Krylov bases (restart+1 and restart vectors)
+    mb::DevBuf sol_b, sol_x, sol_w, sol_t; // rhs, iterate, scratch vectors
+    mb::DevBuf sol_small;        // Hessenberg, Givens, dots (doubles)
+    mb::DevBuf sol_dots;         // block partial sums for reductions
+    void *host_small = nullptr;  // pinned host mirror of small scalars
+
+    // measurement: events around pair-kernel launches (mb_profile_*)
+    int profiling = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+};
+
+namespace mb {
+
+mb_status set_err(mb_context *ctx, mb_status s, const char *fmt, ...);
+mb_status cuda_err(mb_context *ctx, cudaError_t e, const char *what);
+// Make `buf` hold at least `bytes`; respects the context budget.
+mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what);
+void release(mb_context *ctx, DevBuf &buf);
+
+// Pair matvec on device pointers (implemented in pair_matvec.cu).
+// f_stride_blob lets the solver pass its packed vectors (stride 3 doubles).
+mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
+// Pack positions once (FP32 path); the matvec then only reads f.
+mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s);
+mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
+
+// Bodies (bodies.cu)
+mb_status blob_positions(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                         const double *theta, const int64_t *blob_start, const double *rho,
+                         double *r, cudaStream_t s);
+// v = alpha * K UO + beta * v   (v: N x 3)
+void launch_K_apply(int64_t nb, int64_t n, const double *r, const double *q,
+                    const int64_t *blob_start, const double *UO, double *v, double alpha,
+                    double beta, cudaStream_t s);
+// FT = alpha * K^T lambda      (FT: n_b x 6)
+void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
+                     const double *lambda, double *FT, double alpha, cudaStream_t s);
+
+// Preconditioner (precond.cu)
+mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
+                        const double *q, const int64_t *blob_start, double a, double eta,
+                        int wall, cudaStream_t s);
+// z = P^-1 v where v = [w (3N); g (6 n_b)] packed contiguously, same for z.
+void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s);
+
+// Solver (gmres.cu)
+mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                         const double *theta, const int64_t *blob_start, const double *rho,
+                         const double *F, const double *T, const double *slip,
+                         const mb_params *p, double *U, double *Omega, double *lambda,
+                         mb_info *info, cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Running count of kernels launched through the library (mb_profile_read).
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Event pair bracketing one pair-kernel launch when profiling is on.
+std::pair<cudaEvent_t, cudaEvent_t> *profile_begin(mb_context *ctx, cudaStream_t s);
+void profile_end(std::pair<cudaEvent_t, cudaEvent_t> *ev, cudaStream_t s);
+
+}  // namespace mb
+
+#define MB_CUDA_TRY(ctx, call)                                   \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return mb::cuda_err((ctx), e_, #call); \
+    } while (0)
+
+#define MB_TRY(call)                       \
+    do {                                   \
+        mb_status s_ = (call);             \
+        if (s_ != MB_OK) return s_;        \
+    } while (0)

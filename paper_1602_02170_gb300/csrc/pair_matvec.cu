@@ -1,0 +1,311 @@
+// O(N^2) direct-summation product u = M f of the wall-corrected RPY blob
+// mobility (Section 2.1.1; Section 5 evaluates it by direct summation on a
+// GPU).
+//
+// Work decomposition: targets are cut into blocks of NT * TPT blobs (one CTA,
+// TPT targets per thread) and sources into S chunks; a persistent grid of one
+// wave of CTAs walks the (target block, source chunk) items.  Each CTA stages
+// NT sources at a time in shared memory (coalesced float4 loads; every thread
+// then reads the same source, a shared-memory broadcast) and accumulates the
+// tile in FP32 registers, folding each tile sum into a Kahan-compensated
+// accumulator.  Chunk partials go to an FP64 buffer that a second kernel sums
+// in a fixed order, so results are deterministic.
+//
+// FP32 positions carry a hi/lo split: d = (hi_i - hi_j) + (lo_i - lo_j); the
+// hi difference is exact for nearby blobs (Sterbenz), so near pairs keep full
+// FP32 accuracy even at |x| of several hundred.
+#include <algorithm>
+
+#include "mb_internal.cuh"
+#include "rpy_wall.cuh"
+
+namespace mb {
+namespace {
+
+constexpr int kNT = 256;   // threads per CTA = sources per shared tile
+constexpr double kPi = 3.14159265358979323846;
+
+__global__ void pack_hilo_kernel(const double *__restrict__ r, int64_t n, float4 *__restrict__ hi,
+                                 float4 *__restrict__ lo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = r[3 * i], y = r[3 * i + 1], z = r[3 * i + 2];
+        const float xh = (float)x, yh = (float)y, zh = (float)z;
+        hi[i] = make_float4(xh, yh, zh, 0.f);
+        lo[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh),
+                            (float)(z - (double)zh), 0.f);
+    }
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+template <bool WALL, int TPT>
+__global__ void __launch_bounds__(kNT) pair_f32_kernel(
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts<float> k,
+    double *__restrict__ out, double scale, int direct)
+{
+    __shared__ float4 sA[kNT];  // (x_hi, y_hi, z_hi, f_x)
+    __shared__ float4 sB[kNT];  // (x_lo, y_lo, z_lo, f_y)
+    __shared__ float sC[kNT];   // f_z
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        float xh[TPT], yh[TPT], zh[TPT], xl[TPT], yl[TPT], zl[TPT];
+        float sx[TPT], sy[TPT], sz[TPT], cx[TPT], cy[TPT], cz[TPT];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            int64_t i = (int64_t)tb * kNT * TPT + t * kNT + threadIdx.x;
+            i = i < n ? i : n - 1;
+            const float4 h = hi[i], l = lo[i];
+            xh[t] = h.x; yh[t] = h.y; zh[t] = h.z;
+            xl[t] = l.x; yl[t] = l.y; zl[t] = l.z;
+            sx[t] = sy[t] = sz[t] = cx[t] = cy[t] = cz[t] = 0.f;
+        }
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
+        for (int64_t jt = j_begin; jt < j_end; jt += kNT) {
+            __syncthreads();
+            {
+                const int64_t j = jt + threadIdx.x;
+                const bool valid = j < j_end;
+                const int64_t jc = valid ? j : j_begin;
+                const float4 h = hi[jc], l = lo[jc];
+                const float fx = valid ? (float)f[3 * jc] : 0.f;
+                const float fy = valid ? (float)f[3 * jc + 1] : 0.f;
+                const float fz = valid ? (float)f[3 * jc + 2] : 0.f;
+                sA[threadIdx.x] = make_float4(h.x, h.y, h.z, fx);
+                sB[threadIdx.x] = make_float4(l.x, l.y, l.z, fy);
+                sC[threadIdx.x] = fz;
+            }
+            __syncthreads();
+            float ax[TPT], ay[TPT], az[TPT];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) ax[t] = ay[t] = az[t] = 0.f;
+#pragma unroll 4
+            for (int s = 0; s < kNT; ++s) {
+                const float4 A = sA[s];
+                const float4 B = sB[s];
+                const float fz = sC[s];
+#pragma unroll
+                for (int t = 0; t < TPT; ++t) {
+                    const float dx = (xh[t] - A.x) + (xl[t] - B.x);
+                    const float dy = (yh[t] - A.y) + (yl[t] - B.y);
+                    const float dz = (zh[t] - A.z) + (zl[t] - B.z);
+                    pair_accumulate<WALL, float>(dx, dy, dz, zh[t], A.z, A.w, B.w, fz, k, ax[t],
+                                                 ay[t], az[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                kahan_add(sx[t], cx[t], ax[t]);
+                kahan_add(sy[t], cy[t], ay[t]);
+                kahan_add(sz[t], cz[t], az[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            const int64_t i = (int64_t)tb * kNT * TPT + t * kNT + threadIdx.x;
+            if (i < n) {
+                const double vx = (double)sx[t] - (double)cx[t];
+                const double vy = (double)sy[t] - (double)cy[t];
+                const double vz = (double)sz[t] - (double)cz[t];
+                double *o = direct ? out + 3 * i : out + 3 * (sc * n + i);
+                const double m = direct ? scale : 1.0;
+                o[0] = m * vx;
+                o[1] = m * vy;
+                o[2] = m * vz;
+            }
+        }
+    }
+}
+
+template <bool WALL>
+__global__ void __launch_bounds__(kNT) pair_f64_kernel(
+    const double *__restrict__ r, const double *__restrict__ f, int64_t n, int64_t chunk,
+    int n_tblocks, int64_t n_items, PairConsts<double> k, double *__restrict__ out, double scale,
+    int direct)
+{
+    __shared__ double sx[kNT], sy[kNT], sz[kNT], sfx[kNT], sfy[kNT], sfz[kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        int64_t i = (int64_t)tb * kNT + threadIdx.x;
+        const int64_t ic = i < n ? i : n - 1;
+        const double xi = r[3 * ic], yi = r[3 * ic + 1], zi = r[3 * ic + 2];
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
+        for (int64_t jt = j_begin; jt < j_end; jt += kNT) {
+            __syncthreads();
+            {
+                const int64_t j = jt + threadIdx.x;
+                const bool valid = j < j_end;
+                const int64_t jc = valid ? j : j_begin;
+                sx[threadIdx.x] = r[3 * jc];
+                sy[threadIdx.x] = r[3 * jc + 1];
+                sz[threadIdx.x] = r[3 * jc + 2];
+                sfx[threadIdx.x] = valid ? f[3 * jc] : 0.0;
+                sfy[threadIdx.x] = valid ? f[3 * jc + 1] : 0.0;
+                sfz[threadIdx.x] = valid ? f[3 * jc + 2] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 2
+            for (int s = 0; s < kNT; ++s) {
+                pair_accumulate<WALL, double>(xi - sx[s], yi - sy[s], zi - sz[s], zi, sz[s], sfx[s],
+                                              sfy[s], sfz[s], k, ux, uy, uz);
+            }
+        }
+        if (i < n) {
+            double *o = direct ? out + 3 * i : out + 3 * (sc * n + i);
+            const double m = direct ? scale : 1.0;
+            o[0] = m * ux;
+            o[1] = m * uy;
+            o[2] = m * uz;
+        }
+    }
+}
+
+// u_i = scale * sum_s partial[s][i]  (fixed order)
+__global__ void reduce_partials_kernel(const double *__restrict__ partial, int64_t n, int S,
+                                       double scale, double *__restrict__ u)
+{
+    const int64_t m = 3 * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += partial[s * m + e];
+        u[e] = scale * acc;
+    }
+}
+
+struct Plan {
+    int n_tblocks = 0;
+    int S = 1;
+    int64_t chunk = 0;
+    int64_t items = 0;
+    int grid = 0;
+};
+
+// Split sources into S chunks so that the items fill whole waves of the
+// resident grid as evenly as possible, with chunks of at least two tiles.
+Plan make_plan(int64_t n, int targets_per_cta, int resident)
+{
+    Plan p;
+    p.n_tblocks = (int)ceil_div(n, targets_per_cta);
+    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(n, 2 * kNT)));
+    double best = -1.0;
+    for (int64_t s = 1; s <= max_s; ++s) {
+        const int64_t chunk = ceil_div(ceil_div(n, s), kNT) * kNT;
+        const int64_t s_eff = ceil_div(n, chunk);
+        const int64_t items = (int64_t)p.n_tblocks * s_eff;
+        const int64_t waves = ceil_div(items, resident);
+        double eff = (double)items / (double)(waves * resident);
+        // a small preference for fewer chunks (less partial traffic)
+        eff -= 1e-3 * (double)s_eff / 64.0;
+        if (items < resident) eff *= (double)items / resident;
+        if (eff > best + 1e-9) {
+            best = eff;
+            p.S = (int)s_eff;
+            p.chunk = chunk;
+        }
+    }
+    p.items = (int64_t)p.n_tblocks * p.S;
+    p.grid = (int)std::min<int64_t>(p.items, resident);
+    return p;
+}
+
+template <typename K>
+int resident_ctas(mb_context *ctx, K kernel)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kNT, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    return occ * ctx->sm_count;
+}
+
+constexpr int kTPT = 1;
+
+}  // namespace
+
+mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s)
+{
+    MB_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * (size_t)n, "packed positions"));
+    MB_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * (size_t)n, "packed positions"));
+    const int grid = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
+    pack_hilo_kernel<<<grid, 256, 0, s>>>(r, n, (float4 *)ctx->pos_hi.ptr,
+                                          (float4 *)ctx->pos_lo.ptr);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    return MB_OK;
+}
+
+mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s)
+{
+    const double scale = 1.0 / (6.0 * kPi * eta * a);
+    Plan p;
+    if (prec == MB_FP64) {
+        const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
+                             : resident_ctas(ctx, pair_f64_kernel<false>);
+        p = make_plan(n, kNT, res);
+    } else {
+        const int res = wall ? resident_ctas(ctx, pair_f32_kernel<true, kTPT>)
+                             : resident_ctas(ctx, pair_f32_kernel<false, kTPT>);
+        p = make_plan(n, kNT * kTPT, res);
+    }
+    double *out = u;
+    const int direct = p.S == 1;
+    if (!direct) {
+        MB_TRY(ensure(ctx, ctx->partial, sizeof(double) * 3 * (size_t)n * p.S, "matvec partials"));
+        out = (double *)ctx->partial.ptr;
+    }
+    auto *ev = profile_begin(ctx, s);
+    if (prec == MB_FP64) {
+        const PairConsts<double> k = PairConsts<double>::make(a);
+        if (wall)
+            pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
+                                                         out, scale, direct);
+        else
+            pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items,
+                                                          k, out, scale, direct);
+    } else {
+        const PairConsts<float> k = PairConsts<float>::make(a);
+        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+        if (wall)
+            pair_f32_kernel<true, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
+                                                               p.items, k, out, scale, direct);
+        else
+            pair_f32_kernel<false, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
+                                                                p.items, k, out, scale, direct);
+    }
+    profile_end(ev, s);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (!direct) {
+        const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
+        reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return MB_OK;
+}
+
+mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s)
+{
+    if (prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
+    return matvec_packed(ctx, r, f, n, a, eta, wall, prec, u, s);
+}
+
+}  // namespace mb

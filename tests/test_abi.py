@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/mb.h declares (no compute calls: these run without a GPU)."""
+import os
+import re
+import subprocess
+
+import paper_1602_02170_gb300 as mb
+from paper_1602_02170_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "mb.h")).read()
+    return sorted(set(re.findall(r"\b(mb_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_library_builds_and_loads():
+    path = B.build()
+    assert os.path.exists(path)
+    L = mb.load_library()
+    assert L.mb_status_string(6) == b"MB_ESINGULAR"
+    assert L.mb_status_string(0) == b"MB_OK"
+
+
+def test_every_declared_symbol_is_exported():
+    B.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (mb_[A-Za-z_0-9]+)", out))
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    assert set(mb.EXPORTED_SYMBOLS) == set(declared)
+
+
+def test_library_targets_sm_103a():
+    B.build()
+    out = subprocess.run(["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True)
+    if out.returncode != 0:
+        import pytest
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_null_context_is_rejected_without_gpu():
+    L = mb.load_library()
+    assert L.mb_context_destroy(None) == 1  # MB_EINVAL
+    assert L.mb_mobility_matvec(None, None, None, 0, 1.0, 1.0, 1, 1, None, None) == 1

@@ -1,0 +1,175 @@
+"""Parity of the body kernels, the block-diagonal preconditioner and the
+mobility solve with the FP64 oracle.
+
+Bars: blob build, K, K^T and the preconditioner are FP64 throughout (1e-12,
+1e-9 for the preconditioner's factorisations); the mobility solve must give
+body velocities (U, Omega) within 1e-6 relative of the oracle's direct solve
+of Eq. saddle_M, and lambda within 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1602_02170_gb300 as mb
+from oracle import oracle as O
+from paper_1602_02170_gb300 import inputs as I
+from tests.gpu_common import ctx, dev, host, rel_l2  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev_susp(s):
+    return dict(
+        q=dev(s.q), theta=dev(s.theta), blob_start=dev(s.blob_start, torch.int64), rho=dev(s.rho),
+        F=dev(s.F), T=dev(s.T),
+    )
+
+
+def test_blob_positions(ctx):
+    s = I.config_small_suspension(2)
+    d = _dev_susp(s)
+    got = host(ctx.blob_positions(d["q"], d["theta"], d["blob_start"], d["rho"]))
+    ref = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    assert np.abs(got - ref).max() <= 1e-13
+
+
+def test_blob_positions_mixed_bodies(ctx):
+    s = I.mixed_suspension(3, 40)
+    d = _dev_susp(s)
+    got = host(ctx.blob_positions(d["q"], d["theta"], d["blob_start"], d["rho"]))
+    ref = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    assert np.abs(got - ref).max() <= 1e-13
+
+
+def test_K_and_KT(ctx):
+    s = I.mixed_suspension(4, 30)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = np.random.default_rng(1)
+    UO = rng.standard_normal((s.n_bodies, 6))
+    lam = rng.standard_normal((s.n_blobs, 3))
+    d = _dev_susp(s)
+    v = host(ctx.K_apply(dev(r), d["q"], d["blob_start"], dev(UO)))
+    np.testing.assert_allclose(v, O.K_apply(UO[:, :3], UO[:, 3:], r, s.q, s.blob_start), atol=1e-13)
+    FT = host(ctx.KT_apply(dev(r), d["q"], d["blob_start"], dev(lam)))
+    F, T = O.KT_apply(lam, r, s.q, s.blob_start)
+    np.testing.assert_allclose(FT, np.concatenate([F, T], 1), atol=1e-12)
+
+
+@pytest.mark.parametrize("wall", [True, False])
+def test_preconditioner_apply(ctx, wall):
+    """Eq. saddle_M_precon solved per body by the GPU (Cholesky + Schur,
+    explicit inverse) equals the oracle's direct LU solve of each body's
+    indefinite block."""
+    s = I.config_small_suspension(3)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal((s.n_blobs, 3))
+    g = rng.standard_normal((s.n_bodies, 6))
+    d = _dev_susp(s)
+    ctx.precond_setup(dev(r), d["q"], d["blob_start"], s.a, 1.0, wall)
+    lam, UO = ctx.precond_apply(dev(w), dev(g))
+    lam_ref, UO_ref = O.precond_apply(r, s.q, s.blob_start, s.a, 1.0, wall, w, g)
+    assert rel_l2(host(lam), lam_ref) <= 1e-9
+    assert rel_l2(host(UO), UO_ref) <= 1e-9
+
+
+def test_preconditioner_mixed_sizes(ctx):
+    """Bodies of different sizes (42-blob shells and 15-blob boomerangs)."""
+    s = I.mixed_suspension(6, 12)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal((s.n_blobs, 3))
+    g = rng.standard_normal((s.n_bodies, 6))
+    d = _dev_susp(s)
+    ctx.precond_setup(dev(r), d["q"], d["blob_start"], s.a, 1.0, True)
+    lam, UO = ctx.precond_apply(dev(w), dev(g))
+    lam_ref, UO_ref = O.precond_apply(r, s.q, s.blob_start, s.a, 1.0, True, w, g)
+    assert rel_l2(host(lam), lam_ref) <= 1e-9
+    assert rel_l2(host(UO), UO_ref) <= 1e-9
+
+
+def test_preconditioner_large_bodies_global_path(ctx):
+    """162-blob shells (486 rows) take the factorisation path that keeps the
+    Cholesky factor in global memory."""
+    s = I.sphere_suspension(5, 3, 162, 0.12, 10.0, 1.2, 1.6)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal((s.n_blobs, 3))
+    g = rng.standard_normal((s.n_bodies, 6))
+    d = _dev_susp(s)
+    ctx.precond_setup(dev(r), d["q"], d["blob_start"], s.a, 1.0, True)
+    lam, UO = ctx.precond_apply(dev(w), dev(g))
+    lam_ref, UO_ref = O.precond_apply(r, s.q, s.blob_start, s.a, 1.0, True, w, g)
+    assert rel_l2(host(lam), lam_ref) <= 1e-8
+    assert rel_l2(host(UO), UO_ref) <= 1e-8
+
+
+def test_preconditioner_singular_block_reported(ctx):
+    """A blob at z = a/2 makes its body's wall-corrected block indefinite: the
+    setup reports MB_ESINGULAR instead of producing NaNs."""
+    s = I.config_small_suspension(1)
+    q = s.q.copy()
+    r = O.blob_positions(q, s.theta, s.blob_start, s.rho)
+    low = np.argmin(r[s.blob_start[2]:s.blob_start[3], 2]) + s.blob_start[2]
+    q[2, 2] -= r[low, 2] - 0.5 * s.a  # lowest blob of body 2 to z = a/2
+    r = O.blob_positions(q, s.theta, s.blob_start, s.rho)
+    d = _dev_susp(s)
+    with pytest.raises(mb.MBError) as ei:
+        ctx.precond_setup(dev(r), dev(q), d["blob_start"], s.a, 1.0, True)
+    assert ei.value.name == "MB_ESINGULAR"
+    assert "body 2" in str(ei.value)
+
+
+def _solve_and_compare(ctx, s, prec, tol, u_tol, slip=None, wall=True):
+    d = _dev_susp(s)
+    U, W, lam, info = ctx.solve_mobility(
+        d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a, s.eta, wall,
+        None if slip is None else dev(slip), tol=tol, maxit=300, restart=100, prec=prec)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    Ur, Wr, lr = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, s.eta, wall, slip)
+    assert info["converged"] == 1 and info["rel_residual"] <= tol
+    assert rel_l2(host(U), Ur) <= u_tol, (rel_l2(host(U), Ur), info)
+    assert rel_l2(host(W), Wr) <= u_tol, (rel_l2(host(W), Wr), info)
+    assert rel_l2(host(lam), lr) <= 1e-5
+    return info
+
+
+def test_solve_fp64_small_suspension(ctx):
+    """8 x 42-blob shells above the wall, FP64, tol 1e-10."""
+    info = _solve_and_compare(ctx, I.config_small_suspension(1), "fp64", 1e-10, 1e-6)
+    assert 3 <= info["iters"] <= 60
+
+
+def test_solve_mixed_refinement_small_suspension(ctx):
+    """FP32 pair kernel inside Arnoldi, FP64 restart residuals: same answer."""
+    _solve_and_compare(ctx, I.config_small_suspension(1), "mixed", 1e-10, 1e-6)
+
+
+def test_solve_fp32_small_suspension(ctx):
+    _solve_and_compare(ctx, I.config_small_suspension(2), "fp32", 1e-6, 1e-5)
+
+
+def test_solve_with_slip_and_free_space(ctx):
+    s = I.config_small_suspension(4)
+    slip = np.random.default_rng(5).standard_normal((s.n_blobs, 3)) * 0.1
+    _solve_and_compare(ctx, s, "fp64", 1e-10, 1e-6, slip=slip)
+    _solve_and_compare(ctx, s, "fp64", 1e-10, 1e-6, wall=False)
+
+
+def test_solve_mixed_bodies(ctx):
+    s = I.mixed_suspension(8, 16)
+    _solve_and_compare(ctx, s, "mixed", 1e-10, 1e-6)
+
+
+def test_solve_not_converged_reports_best_iterate(ctx):
+    s = I.config_small_suspension(1)
+    d = _dev_susp(s)
+    U, W, lam, info = ctx.solve_mobility(
+        d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a, s.eta, True,
+        tol=1e-12, maxit=2, restart=100, prec="fp64", raise_on_nonconvergence=False)
+    assert info["converged"] == 0 and info["iters"] == 2
+    assert np.isfinite(host(U)).all() and info["rel_residual"] < 1.0
+    with pytest.raises(mb.MBError) as ei:
+        ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a,
+                           s.eta, True, tol=1e-12, maxit=2, prec="fp64")
+    assert ei.value.name == "MB_ENOTCONVERGED"
