@@ -58,15 +58,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir=None) -> str:
+    """Compile and link; `out_dir` builds a separate copy (e.g. a variant with
+    extra -D flags) instead of the package's own library."""
+    build_dir = out_dir or BUILD
+    lib = os.path.join(build_dir, "libmb.so")
+    if out_dir is None and not force and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     flags = NVCC_FLAGS + list(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -80,14 +84,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if err:
                 sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     res = subprocess.run(
         [cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True
     )
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -116,6 +116,9 @@ bool bad_phys(double a, double eta) { return !(a > 0.0) || !(eta > 0.0) || !std:
 
 using namespace mb;
 
+static thread_local std::string g_create_err;
+
+
 extern "C" {
 
 const char *mb_status_string(mb_status s)
@@ -132,7 +135,6 @@ const char *mb_status_string(mb_status s)
     return "MB_UNKNOWN";
 }
 
-static thread_local std::string g_create_err;
 
 const char *mb_last_error(const mb_context *ctx)
 {

@@ -22,7 +22,13 @@
 namespace mb {
 namespace {
 
-constexpr int kNT = 256;   // threads per CTA = sources per shared tile
+#ifndef MB_PAIR_NT
+#define MB_PAIR_NT 256
+#endif
+#ifndef MB_PAIR_TPT
+#define MB_PAIR_TPT 1
+#endif
+constexpr int kNT = MB_PAIR_NT;   // threads per CTA = sources per shared tile
 constexpr double kPi = 3.14159265358979323846;
 
 __global__ void pack_hilo_kernel(const double *__restrict__ r, int64_t n, float4 *__restrict__ hi,
@@ -233,7 +239,7 @@ int resident_ctas(mb_context *ctx, K kernel)
     return occ * ctx->sm_count;
 }
 
-constexpr int kTPT = 1;
+constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 
 }  // namespace
 
