@@ -87,7 +87,9 @@ typedef struct {
 const char *mb_status_string(mb_status s);
 
 /* Message describing the last failing call on ctx (valid until the next
- * call on ctx; "" if none).  ctx may be NULL for context-creation errors. */
+ * call on ctx; "" if none).  With ctx == NULL: the last failing call on this
+ * thread that takes no context (mb_context_create,
+ * mb_mobility_matvec_noalloc). */
 const char *mb_last_error(const mb_context *ctx);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
@@ -139,6 +141,37 @@ mb_status mb_profile_read(mb_context *ctx, double *pair_kernel_ms, int64_t *pair
 mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, int64_t n,
                              double a, double eta, int wall, mb_precision prec, double *u,
                              void *stream);
+
+/*
+ * Allocation-free variant of mb_mobility_matvec with MB_FP32_KAHAN.
+ * The paper has no counterpart: this call exists for callers that cannot
+ * allocate device memory — applications whose framework owns the whole
+ * device-memory budget (its caching allocator has reserved it, so a
+ * cudaMalloc would fail or fragment it) and code on latency-critical paths
+ * that cannot take cudaMalloc's implicit device synchronisation.
+ *
+ * It takes no context and allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine).  Its scratch — packed FP32 hi/lo positions
+ * and per-chunk partial sums, about 14 MiB — is one file-scope device array
+ * of the library, sized for at most MB_NOALLOC_MAX_BLOBS blobs; every GPU
+ * that loads the library holds it until the process exits.  Larger N is
+ * rejected with MB_EINVAL before anything is queued.
+ *
+ * The first call on a device (the device current on the calling thread)
+ * looks up the array's device address and the device's SM count; make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents; every element a call reads it has
+ * written first, so no clearing is needed, but calls whose work overlaps on
+ * the GPU (different streams, or host threads) race on it and must be
+ * serialised by the caller.
+ *
+ * r, f, u: N x 3 device pointers (host pointers are MB_EINVAL); the result
+ * is the same product as mb_mobility_matvec (up to FP32 rounding order).
+ * Errors are reported through mb_last_error(NULL).
+ */
+#define MB_NOALLOC_MAX_BLOBS 65536
+mb_status mb_mobility_matvec_noalloc(const double *r, const double *f, int64_t n, double a,
+                                     double eta, int wall, double *u, void *stream);
 
 /*
  * Blob positions r_i = q_p + R(theta_p) rho_i for every blob i of body p

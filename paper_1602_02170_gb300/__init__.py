@@ -20,6 +20,8 @@ __all__ = [
     "library_path",
     "load_library",
     "EXPORTED_SYMBOLS",
+    "mobility_matvec_noalloc",
+    "NOALLOC_MAX_BLOBS",
 ]
 
 FP64, FP32_KAHAN, MIXED_REFINE = 0, 1, 2
@@ -44,6 +46,7 @@ EXPORTED_SYMBOLS = [
     "mb_profile_enable",
     "mb_profile_read",
     "mb_mobility_matvec",
+    "mb_mobility_matvec_noalloc",
     "mb_blob_positions",
     "mb_K_apply",
     "mb_KT_apply",
@@ -120,6 +123,7 @@ def load_library():
     L.mb_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64), ci]
     L.mb_mobility_matvec.argtypes = [vp, vp, vp, i64, dbl, dbl, ci, ci, vp, vp]
+    L.mb_mobility_matvec_noalloc.argtypes = [vp, vp, i64, dbl, dbl, ci, vp, vp]
     L.mb_blob_positions.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_K_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_KT_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
@@ -144,6 +148,35 @@ def _prec(p) -> int:
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+NOALLOC_MAX_BLOBS = 65536
+
+
+def mobility_matvec_noalloc(r, f, a, eta=1.0, wall=True, out=None, stream=None):
+    """u = M(r) f through mb_mobility_matvec_noalloc: FP32 pair kernel, no
+    context and no device allocation inside the library (its scratch is a
+    fixed device array for up to NOALLOC_MAX_BLOBS blobs; concurrent calls
+    on the GPU race on it).  r, f, out: contiguous float64 (N, 3) CUDA
+    tensors on the current device.  `out` is allocated here by torch if not
+    given; pass it to keep the call allocation-free end to end."""
+    import torch
+
+    L = load_library()
+    n = int(r.shape[0])
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float64, device=r.device)
+    for t in (r, f, out):
+        if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (n, 3):
+            raise ValueError("r, f, out must be contiguous float64 (N, 3)")
+    if stream is None:
+        stream = torch.cuda.current_stream(r.device)
+    st = L.mb_mobility_matvec_noalloc(_ptr(r), _ptr(f), n, float(a), float(eta),
+                                      int(bool(wall)), _ptr(out),
+                                      ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise MBError(st, L.mb_last_error(None).decode())
+    return out
 
 
 class Context:

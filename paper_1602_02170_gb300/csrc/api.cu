@@ -118,6 +118,9 @@ using namespace mb;
 
 static thread_local std::string g_create_err;
 
+namespace mb {
+void set_thread_err(const char *msg) { g_create_err = msg; }
+}  // namespace mb
 
 extern "C" {
 

@@ -59,6 +59,8 @@ struct mb_context {
 namespace mb {
 
 mb_status set_err(mb_context *ctx, mb_status s, const char *fmt, ...);
+// Message for calls without a context (read back by mb_last_error(NULL)).
+void set_thread_err(const char *msg);
 mb_status cuda_err(mb_context *ctx, cudaError_t e, const char *what);
 // Make `buf` hold at least `bytes`; respects the context budget.
 mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what);

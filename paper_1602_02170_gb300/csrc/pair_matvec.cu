@@ -15,6 +15,7 @@
 // hi difference is exact for nearby blobs (Sterbenz), so near pairs keep full
 // FP32 accuracy even at |x| of several hundred.
 #include <algorithm>
+#include <mutex>
 
 #include "mb_internal.cuh"
 #include "rpy_wall.cuh"
@@ -203,11 +204,11 @@ struct Plan {
 
 // Split sources into S chunks so that the items fill whole waves of the
 // resident grid as evenly as possible, with chunks of at least two tiles.
-Plan make_plan(int64_t n, int targets_per_cta, int resident)
+Plan make_plan(int64_t n, int targets_per_cta, int resident, int64_t s_cap = 64)
 {
     Plan p;
     p.n_tblocks = (int)ceil_div(n, targets_per_cta);
-    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(n, 2 * kNT)));
+    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(s_cap, ceil_div(n, 2 * kNT)));
     double best = -1.0;
     for (int64_t s = 1; s <= max_s; ++s) {
         const int64_t chunk = ceil_div(ceil_div(n, s), kNT) * kNT;
@@ -314,4 +315,142 @@ mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64
     return matvec_packed(ctx, r, f, n, a, eta, wall, prec, u, s);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP32 matvec (mb_mobility_matvec_noalloc).
+//
+// For callers that must not allocate device memory: host applications whose
+// framework owns the whole device-memory budget (a caching allocator has
+// reserved it, so a cudaMalloc would fail or fragment it) and code on
+// latency-critical paths that cannot take cudaMalloc's implicit device
+// synchronisation.  The scratch that mb_mobility_matvec keeps in its context
+// (packed hi/lo positions and per-chunk partial sums) lives here in one
+// file-scope device array instead, sized for MB_NOALLOC_MAX_BLOBS blobs and at
+// most kNoallocMaxChunks source chunks.  Every GPU that loads the library
+// holds the array until the process exits.  All calls share it: calls whose
+// work overlaps on the GPU race on it.  Each call writes every element it
+// later reads, so nothing needs clearing between calls.
+namespace {
+
+constexpr int64_t kNoallocMaxBlobs = MB_NOALLOC_MAX_BLOBS;
+constexpr int kNoallocMaxChunks = 8;
+constexpr size_t kNoallocPosBytes = sizeof(float4) * kNoallocMaxBlobs;
+constexpr size_t kNoallocBytes =
+    2 * kNoallocPosBytes + sizeof(double) * 3 * kNoallocMaxChunks * kNoallocMaxBlobs;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+    int resident_wall = 0, resident_free = 0;
+};
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+
+// First call on a device: look up the array's device address (host code may
+// not use the symbol itself) and the resident-grid sizes.  No allocation.
+mb_status noalloc_setup(int dev, NoallocDevice **out)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return MB_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            set_thread_err("cudaGetSymbolAddress of the allocation-free scratch failed");
+            return MB_ECUDA;
+        }
+        int sms = 0, occ_w = 0, occ_f = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, pair_f32_kernel<true, kTPT>,
+                                                          kNT, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, pair_f32_kernel<false, kTPT>,
+                                                          kNT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            set_thread_err("device query failed in the allocation-free matvec set-up");
+            return MB_ECUDA;
+        }
+        d.scratch = (unsigned char *)ptr;
+        d.resident_wall = std::max(1, occ_w) * sms;
+        d.resident_free = std::max(1, occ_f) * sms;
+        d.ready = true;
+    }
+    *out = &d;
+    return MB_OK;
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
 }  // namespace mb
+
+extern "C" mb_status mb_mobility_matvec_noalloc(const double *r, const double *f, int64_t n,
+                                                double a, double eta, int wall, double *u,
+                                                void *stream)
+{
+    using namespace mb;
+    set_thread_err("");
+    if (n < 0 || n > kNoallocMaxBlobs) {
+        set_thread_err("N must be in [0, MB_NOALLOC_MAX_BLOBS]");
+        return MB_EINVAL;
+    }
+    if (!(a > 0.0) || !(eta > 0.0)) {
+        set_thread_err("a and eta must be positive");
+        return MB_EINVAL;
+    }
+    if (n == 0) return MB_OK;
+    if (!r || !f || !u || !on_device(r) || !on_device(f) || !on_device(u)) {
+        set_thread_err("r, f and u must be device pointers");
+        return MB_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_thread_err("cudaGetDevice failed");
+        return MB_ECUDA;
+    }
+    NoallocDevice *d = nullptr;
+    mb_status st = noalloc_setup(dev, &d);
+    if (st != MB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float4 *hi = (float4 *)d->scratch;
+    float4 *lo = (float4 *)(d->scratch + kNoallocPosBytes);
+    double *partial = (double *)(d->scratch + 2 * kNoallocPosBytes);
+    const double scale = 1.0 / (6.0 * kPi * eta * a);
+    const int grid_pack = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
+    pack_hilo_kernel<<<grid_pack, 256, 0, s>>>(r, n, hi, lo);
+    count_launch();
+    const Plan p = make_plan(n, kNT * kTPT, wall ? d->resident_wall : d->resident_free,
+                             kNoallocMaxChunks);
+    const int direct = p.S == 1;
+    double *out = direct ? u : partial;
+    const PairConsts<float> k = PairConsts<float>::make(a);
+    if (wall)
+        pair_f32_kernel<true, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
+                                                           p.items, k, out, scale, direct);
+    else
+        pair_f32_kernel<false, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
+                                                            p.items, k, out, scale, direct);
+    count_launch();
+    if (!direct) {
+        const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 1024);
+        reduce_partials_kernel<<<grid, 256, 0, s>>>(partial, n, p.S, scale, u);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_thread_err(cudaGetErrorString(e));
+        return MB_ECUDA;
+    }
+    return MB_OK;
+}
