@@ -48,6 +48,9 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+KERNEL_NAMES = {0: "pair_f32_kernel<wall> (scalar, 1 target/thread)",
+                1: "pair_f32x2_kernel<wall,1> (packed f32x2, 2 targets/thread)",
+                2: "pair_f32x2_kernel<wall,2> (packed f32x2, 4 targets/thread)"}
 WORKLOAD = "wall-RPY mobility matvec, N=65536 blobs, a=0.5, xy~U[0,400]^2, z~U[a,3a], f~N(0,1)"
 METRIC = "blob-pair interactions/s"
 UNIT = "pairs/s"
@@ -235,6 +238,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         ctx.mobility_matvec(r, f, a, 1.0, True, args.prec, out=u)
     torch.cuda.synchronize()
+    variant = ctx.pair_variant(n, True) if args.prec == "fp32" else None
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -309,8 +313,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": traffic_for_kernel(),
-                         "kernel": "pair_f32_kernel<wall>" if args.prec == "fp32" else
-                         "pair_f64_kernel<wall>",
+                         "kernel": KERNEL_NAMES.get(variant, "pair_f64_kernel<wall>"),
                          "kernel_ms_avg": 1e3 * kernel_avg_s,
                          "flops_per_pair": FLOPS_PER_PAIR,
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",

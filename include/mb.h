@@ -143,6 +143,25 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
                              void *stream);
 
 /*
+ * Choice of the FP32 pair-kernel variant used by this context:
+ *   -1  autotune (default): the first FP32 matvec of each size class (half
+ *       octaves of N, with or without the wall) runs every variant once on
+ *       the caller's stream, synchronises, and keeps the fastest for later
+ *       calls — so make that first call before any stream capture;
+ *    0  scalar FP32 kernel, one target per thread;
+ *    1  packed FP32 kernel (paired f32x2 arithmetic), two targets per thread;
+ *    2  packed FP32 kernel, four targets per thread.
+ * All variants compute the same product to FP32 rounding.  Other values are
+ * MB_EINVAL.  Setting a variant clears the autotuner's cache.
+ */
+mb_status mb_context_set_pair_variant(mb_context *ctx, int variant);
+
+/* The FP32 pair-kernel variant this context uses for N blobs with or
+ * without the wall: the fixed variant if one was set, else the autotuner's
+ * cached choice for that size class, else -1 (not tuned yet). */
+mb_status mb_context_pair_variant(const mb_context *ctx, int64_t n, int wall, int *variant);
+
+/*
  * Allocation-free variant of mb_mobility_matvec with MB_FP32_KAHAN.
  * The paper has no counterpart: this call exists for callers that cannot
  * allocate device memory — applications whose framework owns the whole

@@ -43,6 +43,8 @@ EXPORTED_SYMBOLS = [
     "mb_context_create",
     "mb_context_destroy",
     "mb_context_workspace_bytes",
+    "mb_context_set_pair_variant",
+    "mb_context_pair_variant",
     "mb_profile_enable",
     "mb_profile_read",
     "mb_mobility_matvec",
@@ -119,6 +121,8 @@ def load_library():
     L.mb_context_destroy.argtypes = [vp]
     L.mb_context_workspace_bytes.restype = ctypes.c_size_t
     L.mb_context_workspace_bytes.argtypes = [vp]
+    L.mb_context_set_pair_variant.argtypes = [vp, ci]
+    L.mb_context_pair_variant.argtypes = [vp, i64, ci, ctypes.POINTER(ci)]
     L.mb_profile_enable.argtypes = [vp, ci]
     L.mb_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64), ci]
@@ -223,6 +227,17 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.L.mb_context_workspace_bytes(self.handle))
+
+    def set_pair_variant(self, variant: int):
+        """-1 autotune (default), 0 scalar, 1 packed x2, 2 packed x4."""
+        self._check(self.L.mb_context_set_pair_variant(self.handle, int(variant)))
+
+    def pair_variant(self, n: int, wall: bool = True) -> int:
+        """Variant used for N blobs (-1 if the autotuner has not run yet)."""
+        v = ctypes.c_int()
+        self._check(self.L.mb_context_pair_variant(self.handle, int(n), int(bool(wall)),
+                                                    ctypes.byref(v)))
+        return v.value
 
     def profile_enable(self, on: bool = True):
         self._check(self.L.mb_profile_enable(self.handle, int(bool(on))))

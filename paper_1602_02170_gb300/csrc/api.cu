@@ -192,6 +192,27 @@ mb_status mb_context_destroy(mb_context *ctx)
 
 size_t mb_context_workspace_bytes(const mb_context *ctx) { return ctx ? ctx->held : 0; }
 
+mb_status mb_context_set_pair_variant(mb_context *ctx, int variant)
+{
+    MB_TRY(check_ctx(ctx));
+    if (variant < -1 || variant > 2) return set_err(ctx, MB_EINVAL, "pair variant must be -1..2");
+    ctx->pair_variant = variant;
+    ctx->tuned.clear();
+    return MB_OK;
+}
+
+mb_status mb_context_pair_variant(const mb_context *ctx, int64_t n, int wall, int *variant)
+{
+    if (!ctx || !variant) return MB_EINVAL;
+    if (ctx->pair_variant >= 0) {
+        *variant = ctx->pair_variant;
+        return MB_OK;
+    }
+    auto it = ctx->tuned.find(tune_key(n, wall));
+    *variant = it == ctx->tuned.end() ? -1 : it->second;
+    return MB_OK;
+}
+
 mb_status mb_profile_enable(mb_context *ctx, int on)
 {
     MB_TRY(check_ctx(ctx));

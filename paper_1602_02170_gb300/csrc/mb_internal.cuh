@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <map>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -51,6 +52,10 @@ struct mb_context {
     mb::DevBuf sol_dots;         // block partial sums for reductions
     void *host_small = nullptr;  // pinned host mirror of small scalars
 
+    // FP32 pair-kernel variant: -1 = autotune per (size class, wall), else fixed
+    int pair_variant = -1;
+    std::map<int, int> tuned;   // size-class key -> fastest variant
+
     // measurement: events around pair-kernel launches (mb_profile_*)
     int profiling = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -70,6 +75,8 @@ void release(mb_context *ctx, DevBuf &buf);
 // f_stride_blob lets the solver pass its packed vectors (stride 3 doubles).
 mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
                         double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
+// Autotuner size class of an FP32 matvec (pair_matvec.cu).
+int tune_key(int64_t n, int wall);
 // Pack positions once (FP32 path); the matvec then only reads f.
 mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s);
 mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,

@@ -135,6 +135,109 @@ __global__ void __launch_bounds__(kNT) pair_f32_kernel(
     }
 }
 
+// Packed FP32 kernel: each thread owns 2*NP targets, held as NP float2 pairs
+// (target t and t + NT*NP/2... see index map below), and every source is
+// staged once per tile as duplicated float2 operands:
+//   sP[5*s + 0] = (-x_hi, -x_hi, -y_hi, -y_hi)   sP[5*s + 1] = (-z_hi, -z_hi, z_hi, z_hi)
+//   sP[5*s + 2] = (-x_lo, -x_lo, -y_lo, -y_lo)   sP[5*s + 3] = (-z_lo, -z_lo, f_x, f_x)
+//   sP[5*s + 4] = (f_y, f_y, f_z, f_z)
+// Target of pair q, half h: tb*NT*2*NP + (2q + h)*NT + threadIdx.x.
+template <bool WALL, int NP>
+__global__ void __launch_bounds__(kNT) pair_f32x2_kernel(
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts2 k,
+    double *__restrict__ out, double scale, int direct)
+{
+    __shared__ float4 sP[5 * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        float2 xh[NP], yh[NP], zh[NP], xl[NP], yl[NP], zl[NP];
+        float sum[2 * NP][3], comp[2 * NP][3];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float4 h[2], l[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                int64_t i = (int64_t)tb * kNT * 2 * NP + (2 * q + hh) * kNT + threadIdx.x;
+                i = i < n ? i : n - 1;
+                h[hh] = hi[i];
+                l[hh] = lo[i];
+            }
+            xh[q] = make_float2(h[0].x, h[1].x); yh[q] = make_float2(h[0].y, h[1].y);
+            zh[q] = make_float2(h[0].z, h[1].z);
+            xl[q] = make_float2(l[0].x, l[1].x); yl[q] = make_float2(l[0].y, l[1].y);
+            zl[q] = make_float2(l[0].z, l[1].z);
+        }
+#pragma unroll
+        for (int t = 0; t < 2 * NP; ++t)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sum[t][c] = comp[t][c] = 0.f;
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
+        for (int64_t jt = j_begin; jt < j_end; jt += kNT) {
+            __syncthreads();
+            {
+                const int64_t j = jt + threadIdx.x;
+                const bool valid = j < j_end;
+                const int64_t jc = valid ? j : j_begin;
+                const float4 h = hi[jc], l = lo[jc];
+                const float fx = valid ? (float)f[3 * jc] : 0.f;
+                const float fy = valid ? (float)f[3 * jc + 1] : 0.f;
+                const float fz = valid ? (float)f[3 * jc + 2] : 0.f;
+                float4 *d = sP + 5 * threadIdx.x;
+                d[0] = make_float4(-h.x, -h.x, -h.y, -h.y);
+                d[1] = make_float4(-h.z, -h.z, h.z, h.z);
+                d[2] = make_float4(-l.x, -l.x, -l.y, -l.y);
+                d[3] = make_float4(-l.z, -l.z, fx, fx);
+                d[4] = make_float4(fy, fy, fz, fz);
+            }
+            __syncthreads();
+            float2 ax[NP], ay[NP], az[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) ax[q] = ay[q] = az[q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+            for (int s = 0; s < kNT; ++s) {
+                const float4 P0 = sP[5 * s + 0], P1 = sP[5 * s + 1], P2 = sP[5 * s + 2],
+                             P3 = sP[5 * s + 3], P4 = sP[5 * s + 4];
+                const float2 nxh = make_float2(P0.x, P0.y), nyh = make_float2(P0.z, P0.w);
+                const float2 nzh = make_float2(P1.x, P1.y), zj = make_float2(P1.z, P1.w);
+                const float2 nxl = make_float2(P2.x, P2.y), nyl = make_float2(P2.z, P2.w);
+                const float2 nzl = make_float2(P3.x, P3.y), fx = make_float2(P3.z, P3.w);
+                const float2 fy = make_float2(P4.x, P4.y), fz = make_float2(P4.z, P4.w);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const float2 dx = add2(add2(xh[q], nxh), add2(xl[q], nxl));
+                    const float2 dy = add2(add2(yh[q], nyh), add2(yl[q], nyl));
+                    const float2 dz = add2(add2(zh[q], nzh), add2(zl[q], nzl));
+                    const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
+                    pair_accumulate2<WALL>(dx, dy, dz, dxy2, zh[q], zj, fx, fy, fz, k, ax[q],
+                                           ay[q], az[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                kahan_add(sum[2 * q][0], comp[2 * q][0], ax[q].x);
+                kahan_add(sum[2 * q][1], comp[2 * q][1], ay[q].x);
+                kahan_add(sum[2 * q][2], comp[2 * q][2], az[q].x);
+                kahan_add(sum[2 * q + 1][0], comp[2 * q + 1][0], ax[q].y);
+                kahan_add(sum[2 * q + 1][1], comp[2 * q + 1][1], ay[q].y);
+                kahan_add(sum[2 * q + 1][2], comp[2 * q + 1][2], az[q].y);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 2 * NP; ++t) {
+            const int64_t i = (int64_t)tb * kNT * 2 * NP + t * kNT + threadIdx.x;
+            if (i < n) {
+                double *o = direct ? out + 3 * i : out + 3 * (sc * n + i);
+                const double m = direct ? scale : 1.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[c] = m * ((double)sum[t][c] - (double)comp[t][c]);
+            }
+        }
+    }
+}
+
 template <bool WALL>
 __global__ void __launch_bounds__(kNT) pair_f64_kernel(
     const double *__restrict__ r, const double *__restrict__ f, int64_t n, int64_t chunk,
@@ -244,6 +347,117 @@ constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// FP32 variants and their autotuner.
+//   0: scalar kernel, kTPT targets per thread
+//   1: packed f32x2 kernel, 2 targets per thread
+//   2: packed f32x2 kernel, 4 targets per thread
+constexpr int kF32Variants = 3;
+
+int f32_targets_per_cta(int v) { return v == 0 ? kNT * kTPT : (v == 1 ? 2 * kNT : 4 * kNT); }
+
+template <bool WALL>
+int f32_resident(mb_context *ctx, int v)
+{
+    if (v == 0) return resident_ctas(ctx, pair_f32_kernel<WALL, kTPT>);
+    if (v == 1) return resident_ctas(ctx, pair_f32x2_kernel<WALL, 1>);
+    return resident_ctas(ctx, pair_f32x2_kernel<WALL, 2>);
+}
+
+template <bool WALL>
+void f32_launch(int v, const Plan &p, cudaStream_t s, const float4 *hi, const float4 *lo,
+                const double *f, int64_t n, double a, double *out, double scale, int direct)
+{
+    if (v == 0) {
+        pair_f32_kernel<WALL, kTPT><<<p.grid, kNT, 0, s>>>(
+            hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts<float>::make(a), out, scale,
+            direct);
+    } else if (v == 1) {
+        pair_f32x2_kernel<WALL, 1><<<p.grid, kNT, 0, s>>>(
+            hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts2::make(a), out, scale, direct);
+    } else {
+        pair_f32x2_kernel<WALL, 2><<<p.grid, kNT, 0, s>>>(
+            hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts2::make(a), out, scale, direct);
+    }
+}
+
+// One FP32 matvec with variant v (pair kernel + chunk reduction).
+mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, int wall,
+                  double scale, double *u, cudaStream_t s, bool profile)
+{
+    const int res = wall ? f32_resident<true>(ctx, v) : f32_resident<false>(ctx, v);
+    const Plan p = make_plan(n, f32_targets_per_cta(v), res);
+    double *out = u;
+    const int direct = p.S == 1;
+    if (!direct) {
+        MB_TRY(ensure(ctx, ctx->partial, sizeof(double) * 3 * (size_t)n * p.S, "matvec partials"));
+        out = (double *)ctx->partial.ptr;
+    }
+    auto *ev = profile ? profile_begin(ctx, s) : nullptr;
+    const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+    const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+    if (wall)
+        f32_launch<true>(v, p, s, hi, lo, f, n, a, out, scale, direct);
+    else
+        f32_launch<false>(v, p, s, hi, lo, f, n, a, out, scale, direct);
+    profile_end(ev, s);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (!direct) {
+        const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
+        reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return MB_OK;
+}
+
+// Size class of a matvec for the autotuner: wall flag and half-octaves of N.
+int tune_key(int64_t n, int wall)
+{
+    int b = 0;
+    for (int64_t m = n; m > 1; m >>= 1) ++b;
+    const int half = (n >= 3 * ((int64_t)1 << (b > 0 ? b - 1 : 0))) ? 1 : 0;
+    return (2 * b + half) * 2 + (wall ? 1 : 0);
+}
+
+mb_status matvec_f32(mb_context *ctx, const double *f, int64_t n, double a, int wall,
+                     double scale, double *u, cudaStream_t s)
+{
+    int v = ctx->pair_variant;
+    if (v < 0) {
+        const int key = tune_key(n, wall);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            v = it->second;
+        } else if (n < 4096) {
+            v = 1;  // launch-bound: any variant is as fast
+            ctx->tuned[key] = v;
+        } else {
+            // time each variant once on this stream (each run is a full, valid matvec)
+            float best = 1e30f;
+            int best_v = 1;
+            cudaEvent_t e0, e1;
+            MB_CUDA_TRY(ctx, cudaEventCreate(&e0));
+            MB_CUDA_TRY(ctx, cudaEventCreate(&e1));
+            for (int c = 0; c < kF32Variants; ++c) {
+                MB_CUDA_TRY(ctx, cudaEventRecord(e0, s));
+                MB_TRY(f32_run(ctx, c, f, n, a, wall, scale, u, s, false));
+                MB_CUDA_TRY(ctx, cudaEventRecord(e1, s));
+                MB_CUDA_TRY(ctx, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                MB_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; best_v = c; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ctx->tuned[key] = best_v;
+            v = best_v;
+        }
+    }
+    return f32_run(ctx, v, f, n, a, wall, scale, u, s, true);
+}
+
 mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s)
 {
     MB_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * (size_t)n, "packed positions"));
@@ -260,15 +474,12 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
                         double eta, int wall, mb_precision prec, double *u, cudaStream_t s)
 {
     const double scale = 1.0 / (6.0 * kPi * eta * a);
+    if (prec != MB_FP64) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
     Plan p;
-    if (prec == MB_FP64) {
+    {
         const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
                              : resident_ctas(ctx, pair_f64_kernel<false>);
         p = make_plan(n, kNT, res);
-    } else {
-        const int res = wall ? resident_ctas(ctx, pair_f32_kernel<true, kTPT>)
-                             : resident_ctas(ctx, pair_f32_kernel<false, kTPT>);
-        p = make_plan(n, kNT * kTPT, res);
     }
     double *out = u;
     const int direct = p.S == 1;
@@ -277,25 +488,13 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         out = (double *)ctx->partial.ptr;
     }
     auto *ev = profile_begin(ctx, s);
-    if (prec == MB_FP64) {
-        const PairConsts<double> k = PairConsts<double>::make(a);
-        if (wall)
-            pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
-                                                         out, scale, direct);
-        else
-            pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items,
-                                                          k, out, scale, direct);
-    } else {
-        const PairConsts<float> k = PairConsts<float>::make(a);
-        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
-        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
-        if (wall)
-            pair_f32_kernel<true, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
-                                                               p.items, k, out, scale, direct);
-        else
-            pair_f32_kernel<false, kTPT><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
-                                                                p.items, k, out, scale, direct);
-    }
+    const PairConsts<double> k = PairConsts<double>::make(a);
+    if (wall)
+        pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k, out,
+                                                     scale, direct);
+    else
+        pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
+                                                      out, scale, direct);
     profile_end(ev, s);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());

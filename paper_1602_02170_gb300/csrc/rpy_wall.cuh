@@ -134,4 +134,104 @@ __device__ __forceinline__ void block_f64(const double *ri, const double *rj,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed variant: the same pair interaction for two targets at once, one in
+// each half of a float2, with Blackwell's paired FP32 instructions
+// (fma/add/mul .f32x2).  Every source operand arrives duplicated in both
+// halves; positions arrive negated so that separations are sums.
+struct PairConsts2 {
+    float2 a2, c1, c2, c3, c4, sw, tiny, one;
+    float four_a2, k1, k2;
+    // wall polynomial coefficients (see the f1..f5 formulas above)
+    float2 m1, m2, p2, m2o3, p2o3, m10o3, p6, m10, p70o3, p20, m4, p40o3, m140o3, m12, m20o3,
+        m8o3;
+
+    __host__ static PairConsts2 make(double a)
+    {
+        auto d = [](double v) { return make_float2((float)v, (float)v); };
+        PairConsts2 k;
+        k.a2 = d(a * a);
+        k.c1 = d(0.75 * a);
+        k.c2 = d(0.5 * a * a * a);
+        k.c3 = d(0.75 * a);
+        k.c4 = d(-1.5 * a * a * a);
+        k.sw = d(0.75 * a);
+        k.tiny = d(1e-30);
+        k.one = d(1.0);
+        k.four_a2 = (float)(4.0 * a * a);
+        k.k1 = (float)(9.0 / (32.0 * a));
+        k.k2 = (float)(3.0 / (32.0 * a));
+        k.m1 = d(-1.0); k.m2 = d(-2.0); k.p2 = d(2.0);
+        k.m2o3 = d(-2.0 / 3.0); k.p2o3 = d(2.0 / 3.0); k.m10o3 = d(-10.0 / 3.0);
+        k.p6 = d(6.0); k.m10 = d(-10.0); k.p70o3 = d(70.0 / 3.0); k.p20 = d(20.0);
+        k.m4 = d(-4.0); k.p40o3 = d(40.0 / 3.0); k.m140o3 = d(-140.0 / 3.0);
+        k.m12 = d(-12.0); k.m20o3 = d(-20.0 / 3.0); k.m8o3 = d(-8.0 / 3.0);
+        return k;
+    }
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// u += M_ij f_j for the two targets held in the halves of the float2s.
+// dxy2 must already include the tiny floor (it keeps r^2 > 0 for i = j).
+template <bool WALL>
+__device__ __forceinline__ void pair_accumulate2(float2 dx, float2 dy, float2 dz, float2 dxy2,
+                                                 float2 zt, float2 zj, float2 fx, float2 fy,
+                                                 float2 fz, const PairConsts2 &k, float2 &ux,
+                                                 float2 &uy, float2 &uz)
+{
+    const float2 r2 = fma2(dz, dz, dxy2);
+    const float2 inv = rsqrt2(r2);
+    const float2 inv2 = mul2(inv, inv);
+    float2 C = mul2(inv, fma2(k.c2, inv2, k.c1));
+    float2 D = mul2(mul2(inv, inv2), fma2(k.c4, inv2, k.c3));
+    if (__any_sync(0xffffffffu, (r2.x < k.four_a2) | (r2.y < k.four_a2))) {
+        // overlapping blobs (rare): regularised branch, lane by lane
+        if (r2.x < k.four_a2) { C.x = 1.f - k.k1 * (r2.x * inv.x); D.x = k.k2 * inv.x; }
+        if (r2.y < k.four_a2) { C.y = 1.f - k.k1 * (r2.y * inv.y); D.y = k.k2 * inv.y; }
+    }
+    const float2 rf_xy = fma2(dx, fx, mul2(dy, fy));
+    const float2 g = mul2(D, fma2(dz, fz, rf_xy));
+    if (!WALL) {
+        ux = fma2(C, fx, fma2(g, dx, ux));
+        uy = fma2(C, fy, fma2(g, dy, uy));
+        uz = fma2(C, fz, fma2(g, dz, uz));
+        return;
+    }
+    const float2 R3 = add2(zt, zj);
+    const float2 invR = rsqrt2(fma2(R3, R3, dxy2));
+    const float2 hs = mul2(zj, invR);
+    const float2 ht = mul2(zt, invR);
+    const float2 e3 = add2(hs, ht);
+    const float2 E = mul2(e3, e3);
+    const float2 t2 = mul2(k.a2, mul2(invR, invR));
+    const float2 t4 = mul2(t2, t2);
+    const float2 p = mul2(hs, ht);
+    const float2 T1 = mul2(E, t2);
+    const float2 T2 = mul2(E, t4);
+    // f1 = -1 - 2p + 2 T1 - 2/3 t2 + 2/3 t4 - 10/3 T2
+    const float2 f1 = fma2(k.m10o3, T2, fma2(k.p2o3, t4, fma2(k.m2o3, t2, fma2(k.p2, T1, fma2(k.m2, p, k.m1)))));
+    // f2 = -1 + 6p - 10 T1 + 2 t2 + 70/3 T2 - 10/3 t4
+    const float2 f2 = fma2(k.m10o3, t4, fma2(k.p70o3, T2, fma2(k.p2, t2, fma2(k.m10, T1, fma2(k.p6, p, k.m1)))));
+    // f3 = 2 hs + e3 (20 T1 - 4 t2 + 40/3 t4 - 140/3 T2 - 12 p)
+    const float2 in3 = fma2(k.m12, p, fma2(k.m140o3, T2, fma2(k.p40o3, t4, fma2(k.m4, t2, mul2(k.p20, T1)))));
+    const float2 f3 = fma2(k.p2, hs, mul2(e3, in3));
+    // f4 = 2 hs - 20/3 e3 t4
+    const float2 f4 = fma2(k.p2, hs, mul2(k.m20o3, mul2(e3, t4)));
+    // f5 = -4 hs^2 - 4 T1 + 20 T2 - 8/3 t4
+    const float2 f5 = fma2(k.m8o3, t4, fma2(k.p20, T2, fma2(k.m4, T1, mul2(k.m4, mul2(hs, hs)))));
+    const float2 eF = mul2(fma2(R3, fz, rf_xy), invR);
+    const float2 gw = mul2(fma2(f2, eF, mul2(f3, fz)), invR);
+    const float2 kz = fma2(f4, eF, mul2(f5, fz));
+    const float2 s = mul2(k.sw, invR);
+    const float2 Cx = fma2(s, f1, C);
+    const float2 Gx = fma2(s, gw, g);
+    ux = fma2(Cx, fx, fma2(Gx, dx, ux));
+    uy = fma2(Cx, fy, fma2(Gx, dy, uy));
+    uz = fma2(Cx, fz, fma2(g, dz, fma2(s, fma2(gw, R3, kz), uz)));
+}
+
 }  // namespace mb

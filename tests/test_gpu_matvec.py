@@ -67,6 +67,33 @@ def test_matvec_full_size_sampled(ctx, full_size_case, prec):
     assert np.abs(got[rows] - ref).max() <= TOL[prec] * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("n", [7, 513, 1537, 4100, 9000])
+def test_matvec_fp32_variants_elementwise(ctx, variant, n):
+    """Every FP32 kernel variant (scalar; packed with 2 or 4 targets per
+    thread) against the oracle, on sizes that leave ragged target blocks."""
+    r, f = I.blob_cloud(300 + n, n, 0.5, 3.0 * max(1.0, n ** 0.5 / 3), 0.5, 1.5)
+    ref = O.matvec(r, f, 0.5, 1.0, True)
+    ctx.set_pair_variant(variant)
+    try:
+        got = host(ctx.mobility_matvec(dev(r), dev(f), 0.5, 1.0, True, "fp32"))
+    finally:
+        ctx.set_pair_variant(-1)
+    assert np.abs(got - ref).max() <= TOL["fp32"] * np.abs(ref).max()
+    assert rel_l2(got, ref) <= TOL["fp32"]
+
+
+def test_autotuner_picks_a_variant_and_keeps_it(ctx):
+    r, f, a = I.config_matvec_cloud(5, n=20000)
+    assert ctx.pair_variant(20000, True) in (-1, 0, 1, 2)
+    u1 = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
+    v = ctx.pair_variant(20000, True)
+    assert v in (0, 1, 2)
+    u2 = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
+    np.testing.assert_array_equal(u1, u2)
+    assert ctx.pair_variant(20000, True) == v
+
+
 def test_matvec_translation_parallel_to_wall(ctx):
     """Property at any size: shifting every blob parallel to the wall by
     (+300, -200) leaves u unchanged (FP32 path keeps it thanks to hi/lo)."""
