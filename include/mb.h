@@ -267,6 +267,47 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
                             const mb_params *params, double *U, double *Omega, double *lambda,
                             mb_info *info, void *stream);
 
+/* One independent problem of a batch (all pointers device pointers; layout
+ * as for mb_solve_mobility; slip may be NULL). */
+typedef struct {
+    int64_t n_bodies;
+    int64_t n_blobs;
+    const double *q;
+    const double *theta;
+    const int64_t *blob_start;
+    const double *rho;
+    const double *F;
+    const double *T;
+    const double *slip;
+    double *U;
+    double *Omega;
+    double *lambda;
+} mb_problem;
+
+/*
+ * Solve many independent mobility problems (Eq. saddle_M, one per problem)
+ * together.  All problems share `params` (a, eta, wall, tolerance,
+ * iteration limits, precision).  The blob build, K, K^T and the block-
+ * diagonal preconditioner of Section 2.2.2 run over all bodies of all
+ * problems in one launch each; the pair kernel runs as one persistent launch
+ * over all problems' (target block, source chunk) work items, so problems of
+ * very different sizes share the GPU; each problem keeps its own GMRES
+ * state and stops consuming pair-kernel work once converged.  The first
+ * FP32 matvec times the packed kernel with 2 and 4 targets per thread and
+ * keeps the faster (autotuned tile shape).
+ *
+ * problems: host array of n_problems descriptors (pointing to device data);
+ * infos: host array of n_problems (may be NULL), filled per problem
+ * (setup_ms and solve_ms are the batch's).  Synchronises the stream.
+ * Returns MB_ENOTCONVERGED if any problem missed the tolerance (each
+ * problem's best iterate is written and its info says which), MB_ESINGULAR
+ * naming the problem and body whose block is not positive definite, and
+ * MB_EINVAL for a malformed descriptor (including blob_start[0] != 0 or
+ * blob_start[n_b] != N, detected on the device).
+ */
+mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *problems,
+                         const mb_params *params, mb_info *infos, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

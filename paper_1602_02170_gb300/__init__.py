@@ -55,6 +55,7 @@ EXPORTED_SYMBOLS = [
     "mb_precond_setup",
     "mb_precond_apply",
     "mb_solve_mobility",
+    "mb_solve_batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -80,6 +81,23 @@ class Params(ctypes.Structure):
         ("maxit", ctypes.c_int),
         ("restart", ctypes.c_int),
         ("prec", ctypes.c_int),
+    ]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("n_bodies", ctypes.c_int64),
+        ("n_blobs", ctypes.c_int64),
+        ("q", ctypes.c_void_p),
+        ("theta", ctypes.c_void_p),
+        ("blob_start", ctypes.c_void_p),
+        ("rho", ctypes.c_void_p),
+        ("F", ctypes.c_void_p),
+        ("T", ctypes.c_void_p),
+        ("slip", ctypes.c_void_p),
+        ("U", ctypes.c_void_p),
+        ("Omega", ctypes.c_void_p),
+        ("lam", ctypes.c_void_p),
     ]
 
 
@@ -137,6 +155,8 @@ def load_library():
         vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
         ctypes.POINTER(Info), vp,
     ]
+    L.mb_solve_batch.argtypes = [vp, ci, ctypes.POINTER(Problem), ctypes.POINTER(Params),
+                                 ctypes.POINTER(Info), vp]
     for name in EXPORTED_SYMBOLS:
         if name not in ("mb_status_string", "mb_last_error", "mb_context_workspace_bytes"):
             getattr(L, name).restype = ci  # mb_status
@@ -355,3 +375,43 @@ class Context:
             return U, Om, lam, info.as_dict()
         self._check(st)
         return U, Om, lam, info.as_dict()
+
+    def solve_batch(self, problems, a, eta=1.0, wall=True, tol=1e-10, maxit=200, restart=100,
+                    prec="mixed", stream=None, raise_on_nonconvergence=True):
+        """Solve independent problems together (mb_solve_batch).
+
+        problems: list of dicts with CUDA tensors q (n_b,3), theta (n_b,4),
+        blob_start (n_b+1, int64), rho (N,3), F, T (n_b,3) and optional slip
+        (N,3).  Returns a list of (U, Omega, lambda, info dict)."""
+        torch = self._torch
+        n = len(problems)
+        arr = (Problem * max(1, n))()
+        outs = []
+        keep = []
+        for k, P in enumerate(problems):
+            nb, nbl = int(P["q"].shape[0]), int(P["rho"].shape[0])
+            self._dev(P["q"], (nb, 3)); self._dev(P["theta"], (nb, 4)); self._dev(P["rho"], (nbl, 3))
+            self._dev(P["F"], (nb, 3)); self._dev(P["T"], (nb, 3))
+            self._dev(P["blob_start"], (nb + 1,), torch.int64)
+            slip = P.get("slip")
+            if slip is not None:
+                self._dev(slip, (nbl, 3))
+            dev = P["q"].device
+            U = torch.empty((nb, 3), dtype=torch.float64, device=dev)
+            Om = torch.empty((nb, 3), dtype=torch.float64, device=dev)
+            lam = torch.empty((nbl, 3), dtype=torch.float64, device=dev)
+            outs.append((U, Om, lam))
+            keep.append(P)
+            arr[k] = Problem(nb, nbl, P["q"].data_ptr(), P["theta"].data_ptr(),
+                             P["blob_start"].data_ptr(), P["rho"].data_ptr(), P["F"].data_ptr(),
+                             P["T"].data_ptr(), 0 if slip is None else slip.data_ptr(),
+                             U.data_ptr(), Om.data_ptr(), lam.data_ptr())
+        infos = (Info * max(1, n))()
+        p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
+                   _prec(prec))
+        st = self.L.mb_solve_batch(self.handle, n, arr, ctypes.byref(p), infos,
+                                   self._stream(stream))
+        if not (st == 4 and not raise_on_nonconvergence):
+            self._check(st)
+        return [(U, Om, lam, infos[k].as_dict()) for k, (U, Om, lam) in enumerate(outs)]
+

@@ -181,7 +181,8 @@ mb_status mb_context_destroy(mb_context *ctx)
     DevBuf *bufs[] = {&ctx->pos_hi, &ctx->pos_lo, &ctx->partial, &ctx->stage_r, &ctx->stage_f,
                       &ctx->stage_u, &ctx->pinv, &ctx->pinv_off, &ctx->blob_start_copy,
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
-                      &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots};
+                      &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
+                      &ctx->batch_ws};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);
     for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -355,6 +356,34 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
     if (n_blobs > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
     return solve_mobility(ctx, n_bodies, n_blobs, q, theta, blob_start, rho, F, T, slip, params, U,
                           Omega, lambda, info, (cudaStream_t)stream);
+}
+
+mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *problems,
+                         const mb_params *params, mb_info *infos, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (n_problems < 0 || (n_problems > 0 && !problems) || !params)
+        return set_err(ctx, MB_EINVAL, "bad problem list or null params");
+    if (n_problems == 0) return MB_OK;
+    if (bad_phys(params->a, params->eta))
+        return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
+    if (!(params->tol > 0.0) || params->maxit < 1 || params->restart < 1)
+        return set_err(ctx, MB_EINVAL, "tol > 0, maxit >= 1 and restart >= 1 required");
+    if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
+        params->prec != MB_MIXED_REFINE)
+        return set_err(ctx, MB_EINVAL, "unknown precision mode");
+    int64_t n_tot = 0;
+    for (int p = 0; p < n_problems; ++p) {
+        const mb_problem &P = problems[p];
+        if (P.n_bodies <= 0 || P.n_blobs <= 0)
+            return set_err(ctx, MB_EINVAL, "problem %d: needs at least one body and one blob", p);
+        if (!P.q || !P.theta || !P.blob_start || !P.rho || !P.F || !P.T || !P.U || !P.Omega ||
+            !P.lambda)
+            return set_err(ctx, MB_EINVAL, "problem %d: null array pointer", p);
+        n_tot += P.n_blobs;
+    }
+    if (n_tot > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "total N above 2^31");
+    return solve_batch(ctx, n_problems, problems, params, infos, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -49,7 +49,8 @@ struct mb_context {
     mb::DevBuf sol_V, sol_Z;     // Krylov bases (restart+1 and restart vectors)
     mb::DevBuf sol_b, sol_x, sol_w, sol_t; // rhs, iterate, scratch vectors
     mb::DevBuf sol_small;        // Hessenberg, Givens, dots (doubles)
-    mb::DevBuf sol_dots;         // block partial sums for reductions
+    mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
+    mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)
     void *host_small = nullptr;  // pinned host mirror of small scalars
 
     // FP32 pair-kernel variant: -1 = autotune per (size class, wall), else fixed
@@ -107,6 +108,10 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                          const double *F, const double *T, const double *slip,
                          const mb_params *p, double *U, double *Omega, double *lambda,
                          mb_info *info, cudaStream_t s);
+
+// Batched solves (batch.cu)
+mb_status solve_batch(mb_context *ctx, int np, const mb_problem *probs, const mb_params *prm,
+                      mb_info *infos, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

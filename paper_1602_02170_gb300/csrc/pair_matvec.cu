@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "mb_internal.cuh"
+#include "pair_tiles.cuh"
 #include "rpy_wall.cuh"
 
 namespace mb {
@@ -43,14 +44,6 @@ __global__ void pack_hilo_kernel(const double *__restrict__ r, int64_t n, float4
         lo[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh),
                             (float)(z - (double)zh), 0.f);
     }
-}
-
-__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
-{
-    const float y = x - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
 }
 
 template <bool WALL, int TPT>
@@ -135,106 +128,22 @@ __global__ void __launch_bounds__(kNT) pair_f32_kernel(
     }
 }
 
-// Packed FP32 kernel: each thread owns 2*NP targets, held as NP float2 pairs
-// (target t and t + NT*NP/2... see index map below), and every source is
-// staged once per tile as duplicated float2 operands:
-//   sP[5*s + 0] = (-x_hi, -x_hi, -y_hi, -y_hi)   sP[5*s + 1] = (-z_hi, -z_hi, z_hi, z_hi)
-//   sP[5*s + 2] = (-x_lo, -x_lo, -y_lo, -y_lo)   sP[5*s + 3] = (-z_lo, -z_lo, f_x, f_x)
-//   sP[5*s + 4] = (f_y, f_y, f_z, f_z)
-// Target of pair q, half h: tb*NT*2*NP + (2q + h)*NT + threadIdx.x.
+// Packed FP32 kernel (paired f32x2 arithmetic, 2*NP targets per thread): a
+// persistent loop over (target block, source chunk) items; see x2_item.
 template <bool WALL, int NP>
-__global__ void __launch_bounds__(kNT) pair_f32x2_kernel(
+__global__ void __launch_bounds__(kNT, NP == 1 ? 3 : 2) pair_f32x2_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
     int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts2 k,
     double *__restrict__ out, double scale, int direct)
 {
-    __shared__ float4 sP[5 * kNT];
+    __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int tb = (int)(item % n_tblocks);
         const int64_t sc = item / n_tblocks;
-        float2 xh[NP], yh[NP], zh[NP], xl[NP], yl[NP], zl[NP];
-        float sum[2 * NP][3], comp[2 * NP][3];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            float4 h[2], l[2];
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                int64_t i = (int64_t)tb * kNT * 2 * NP + (2 * q + hh) * kNT + threadIdx.x;
-                i = i < n ? i : n - 1;
-                h[hh] = hi[i];
-                l[hh] = lo[i];
-            }
-            xh[q] = make_float2(h[0].x, h[1].x); yh[q] = make_float2(h[0].y, h[1].y);
-            zh[q] = make_float2(h[0].z, h[1].z);
-            xl[q] = make_float2(l[0].x, l[1].x); yl[q] = make_float2(l[0].y, l[1].y);
-            zl[q] = make_float2(l[0].z, l[1].z);
-        }
-#pragma unroll
-        for (int t = 0; t < 2 * NP; ++t)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sum[t][c] = comp[t][c] = 0.f;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        for (int64_t jt = j_begin; jt < j_end; jt += kNT) {
-            __syncthreads();
-            {
-                const int64_t j = jt + threadIdx.x;
-                const bool valid = j < j_end;
-                const int64_t jc = valid ? j : j_begin;
-                const float4 h = hi[jc], l = lo[jc];
-                const float fx = valid ? (float)f[3 * jc] : 0.f;
-                const float fy = valid ? (float)f[3 * jc + 1] : 0.f;
-                const float fz = valid ? (float)f[3 * jc + 2] : 0.f;
-                float4 *d = sP + 5 * threadIdx.x;
-                d[0] = make_float4(-h.x, -h.x, -h.y, -h.y);
-                d[1] = make_float4(-h.z, -h.z, h.z, h.z);
-                d[2] = make_float4(-l.x, -l.x, -l.y, -l.y);
-                d[3] = make_float4(-l.z, -l.z, fx, fx);
-                d[4] = make_float4(fy, fy, fz, fz);
-            }
-            __syncthreads();
-            float2 ax[NP], ay[NP], az[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) ax[q] = ay[q] = az[q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-            for (int s = 0; s < kNT; ++s) {
-                const float4 P0 = sP[5 * s + 0], P1 = sP[5 * s + 1], P2 = sP[5 * s + 2],
-                             P3 = sP[5 * s + 3], P4 = sP[5 * s + 4];
-                const float2 nxh = make_float2(P0.x, P0.y), nyh = make_float2(P0.z, P0.w);
-                const float2 nzh = make_float2(P1.x, P1.y), zj = make_float2(P1.z, P1.w);
-                const float2 nxl = make_float2(P2.x, P2.y), nyl = make_float2(P2.z, P2.w);
-                const float2 nzl = make_float2(P3.x, P3.y), fx = make_float2(P3.z, P3.w);
-                const float2 fy = make_float2(P4.x, P4.y), fz = make_float2(P4.z, P4.w);
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const float2 dx = add2(add2(xh[q], nxh), add2(xl[q], nxl));
-                    const float2 dy = add2(add2(yh[q], nyh), add2(yl[q], nyl));
-                    const float2 dz = add2(add2(zh[q], nzh), add2(zl[q], nzl));
-                    const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
-                    pair_accumulate2<WALL>(dx, dy, dz, dxy2, zh[q], zj, fx, fy, fz, k, ax[q],
-                                           ay[q], az[q]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                kahan_add(sum[2 * q][0], comp[2 * q][0], ax[q].x);
-                kahan_add(sum[2 * q][1], comp[2 * q][1], ay[q].x);
-                kahan_add(sum[2 * q][2], comp[2 * q][2], az[q].x);
-                kahan_add(sum[2 * q + 1][0], comp[2 * q + 1][0], ax[q].y);
-                kahan_add(sum[2 * q + 1][1], comp[2 * q + 1][1], ay[q].y);
-                kahan_add(sum[2 * q + 1][2], comp[2 * q + 1][2], az[q].y);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < 2 * NP; ++t) {
-            const int64_t i = (int64_t)tb * kNT * 2 * NP + t * kNT + threadIdx.x;
-            if (i < n) {
-                double *o = direct ? out + 3 * i : out + 3 * (sc * n + i);
-                const double m = direct ? scale : 1.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) o[c] = m * ((double)sum[t][c] - (double)comp[t][c]);
-            }
-        }
+        x2_item<WALL, NP, kNT>(sP, hi, lo, f, n, tb, j_begin, j_end, k,
+                               direct ? out : out + 3 * sc * n, direct ? scale : 1.0);
     }
 }
 
@@ -244,43 +153,14 @@ __global__ void __launch_bounds__(kNT) pair_f64_kernel(
     int n_tblocks, int64_t n_items, PairConsts<double> k, double *__restrict__ out, double scale,
     int direct)
 {
-    __shared__ double sx[kNT], sy[kNT], sz[kNT], sfx[kNT], sfy[kNT], sfz[kNT];
+    __shared__ double sm[6 * kNT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int tb = (int)(item % n_tblocks);
         const int64_t sc = item / n_tblocks;
-        int64_t i = (int64_t)tb * kNT + threadIdx.x;
-        const int64_t ic = i < n ? i : n - 1;
-        const double xi = r[3 * ic], yi = r[3 * ic + 1], zi = r[3 * ic + 2];
-        double ux = 0.0, uy = 0.0, uz = 0.0;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        for (int64_t jt = j_begin; jt < j_end; jt += kNT) {
-            __syncthreads();
-            {
-                const int64_t j = jt + threadIdx.x;
-                const bool valid = j < j_end;
-                const int64_t jc = valid ? j : j_begin;
-                sx[threadIdx.x] = r[3 * jc];
-                sy[threadIdx.x] = r[3 * jc + 1];
-                sz[threadIdx.x] = r[3 * jc + 2];
-                sfx[threadIdx.x] = valid ? f[3 * jc] : 0.0;
-                sfy[threadIdx.x] = valid ? f[3 * jc + 1] : 0.0;
-                sfz[threadIdx.x] = valid ? f[3 * jc + 2] : 0.0;
-            }
-            __syncthreads();
-#pragma unroll 2
-            for (int s = 0; s < kNT; ++s) {
-                pair_accumulate<WALL, double>(xi - sx[s], yi - sy[s], zi - sz[s], zi, sz[s], sfx[s],
-                                              sfy[s], sfz[s], k, ux, uy, uz);
-            }
-        }
-        if (i < n) {
-            double *o = direct ? out + 3 * i : out + 3 * (sc * n + i);
-            const double m = direct ? scale : 1.0;
-            o[0] = m * ux;
-            o[1] = m * uy;
-            o[2] = m * uz;
-        }
+        f64_item<WALL, kNT>(sm, r, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
+                            direct ? scale : 1.0);
     }
 }
 
