@@ -53,9 +53,13 @@ typedef enum {
     MB_FP64 = 0,          /* pair kernel in FP64                               */
     MB_FP32_KAHAN = 1,    /* pair kernel in FP32 (hi/lo positions, Kahan-
                              compensated accumulation), result in FP64         */
-    MB_MIXED_REFINE = 2   /* solver only: FP32 pair kernel inside the Krylov
-                             iteration, FP64 pair kernel for the true residual
-                             of every restart (iterative refinement)           */
+    MB_MIXED_REFINE = 2,  /* solver only: FP32 pair kernel inside the Krylov
+                             iteration, double-float pair kernel for the true
+                             residual of every restart (iterative refinement)  */
+    MB_DF64 = 3           /* pair kernel in double-float: each value an
+                             unevaluated sum of two FP32 numbers (~46 bits),
+                             FP64-class accuracy (~1e-11 relative) on the FP32
+                             pipes, several times faster than MB_FP64 on GB300 */
 } mb_precision;
 
 typedef struct mb_context mb_context;
@@ -129,7 +133,7 @@ mb_status mb_profile_read(mb_context *ctx, double *pair_kernel_ms, int64_t *pair
  *
  *   r, f : N x 3 positions and forces (read only)
  *   u    : N x 3 velocities (written)
- *   prec : MB_FP64 or MB_FP32_KAHAN
+ *   prec : MB_FP64, MB_FP32_KAHAN or MB_DF64
  * r, f and u may all be device pointers (the call is asynchronous on
  * `stream`) or all host pointers (staged through the context's workspace
  * with copies on `stream`; the call returns after u is written; pinned host

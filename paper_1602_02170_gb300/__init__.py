@@ -17,6 +17,7 @@ __all__ = [
     "FP64",
     "FP32_KAHAN",
     "MIXED_REFINE",
+    "DF64",
     "library_path",
     "load_library",
     "EXPORTED_SYMBOLS",
@@ -24,8 +25,9 @@ __all__ = [
     "NOALLOC_MAX_BLOBS",
 ]
 
-FP64, FP32_KAHAN, MIXED_REFINE = 0, 1, 2
-_PREC = {"fp64": FP64, "fp32": FP32_KAHAN, "fp32_kahan": FP32_KAHAN, "mixed": MIXED_REFINE}
+FP64, FP32_KAHAN, MIXED_REFINE, DF64 = 0, 1, 2, 3
+_PREC = {"fp64": FP64, "fp32": FP32_KAHAN, "fp32_kahan": FP32_KAHAN, "mixed": MIXED_REFINE,
+         "df64": DF64}
 
 STATUS = {
     0: "MB_OK",

@@ -249,8 +249,8 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
     MB_TRY(check_ctx(ctx));
     if (n < 0) return set_err(ctx, MB_EINVAL, "N must be >= 0");
     if (bad_phys(a, eta)) return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
-    if (prec != MB_FP64 && prec != MB_FP32_KAHAN)
-        return set_err(ctx, MB_EINVAL, "matvec precision must be MB_FP64 or MB_FP32_KAHAN");
+    if (prec != MB_FP64 && prec != MB_FP32_KAHAN && prec != MB_DF64)
+        return set_err(ctx, MB_EINVAL, "matvec precision must be MB_FP64, MB_FP32_KAHAN or MB_DF64");
     if (n == 0) return MB_OK;
     if (!r || !f || !u) return set_err(ctx, MB_EINVAL, "null array pointer");
     if (n > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
@@ -349,7 +349,7 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
     if (!(params->tol > 0.0) || params->maxit < 1 || params->restart < 1)
         return set_err(ctx, MB_EINVAL, "tol > 0, maxit >= 1 and restart >= 1 required");
     if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
-        params->prec != MB_MIXED_REFINE)
+        params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
         return set_err(ctx, MB_EINVAL, "unknown precision mode");
     if (!q || !theta || !blob_start || !rho || !F || !T || !U || !Omega || !lambda)
         return set_err(ctx, MB_EINVAL, "null array pointer");
@@ -370,7 +370,7 @@ mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *prob
     if (!(params->tol > 0.0) || params->maxit < 1 || params->restart < 1)
         return set_err(ctx, MB_EINVAL, "tol > 0, maxit >= 1 and restart >= 1 required");
     if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
-        params->prec != MB_MIXED_REFINE)
+        params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
         return set_err(ctx, MB_EINVAL, "unknown precision mode");
     int64_t n_tot = 0;
     for (int p = 0; p < n_problems; ++p) {

@@ -154,6 +154,29 @@ __global__ void __launch_bounds__(kNT) batch_f64_kernel(
     }
 }
 
+template <bool WALL>
+__global__ void __launch_bounds__(kNT) batch_df_kernel(
+    const BPlan *__restrict__ plans, const int64_t *__restrict__ item_off, int np,
+    int64_t n_items, const int *__restrict__ mask, const float4 *__restrict__ hi,
+    const float4 *__restrict__ lo, const double *__restrict__ f, double *__restrict__ y,
+    double *__restrict__ partial, PairConsts<dfl> k, double scale)
+{
+    __shared__ float4 sD[3 * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int p = find_item_owner(item_off, np, item);
+        if (!mask[p]) continue;
+        const BPlan P = plans[p];
+        const int64_t local = item - P.item_off;
+        const int tb = (int)(local % P.n_tblocks);
+        const int64_t sc = local / P.n_tblocks;
+        const int64_t j_begin = sc * P.chunk;
+        const int64_t j_end = j_begin + P.chunk < P.n ? j_begin + P.chunk : P.n;
+        double *out = P.S == 1 ? y + 3 * P.blob_off : partial + P.part_off + 3 * sc * P.n;
+        df_item<WALL, kNT>(sD, hi + P.blob_off, lo + P.blob_off, f + 3 * P.blob_off, P.n, tb,
+                           j_begin, j_end, k, out, P.S == 1 ? scale : 1.0);
+    }
+}
+
 // y_i = scale * sum_s partial[s][i] for blobs of masked-in problems with S > 1
 __global__ void batch_reduce_kernel(const BPlan *__restrict__ plans, const int *__restrict__ blob_prob,
                                     const int *__restrict__ mask, int64_t n_tot,
@@ -472,7 +495,22 @@ struct Batch {
     mb_status matvec(const double *f, double *y, mb_precision prec, const int *mask)
     {
         const double scale = 1.0 / (6.0 * kPi * eta * a);
-        if (prec == MB_FP64) {
+        if (prec == MB_DF64) {
+            // the double-float kernel uses the FP64 kernel's plan (one target per thread)
+            const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+            const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+            const PairConsts<dfl> k = PairConsts<dfl>::make(a);
+            if (wall)
+                batch_df_kernel<true><<<grid64, kNT, 0, s>>>(plan64, item_off64, np, items64, mask, hi,
+                                                             lo, f, y, partial, k, scale);
+            else
+                batch_df_kernel<false><<<grid64, kNT, 0, s>>>(plan64, item_off64, np, items64, mask,
+                                                              hi, lo, f, y, partial, k, scale);
+            count_launch();
+            batch_reduce_kernel<<<vgrid(3 * n_tot), 256, 0, s>>>(plan64, blob_prob, mask, n_tot,
+                                                                 partial, scale, y);
+            count_launch();
+        } else if (prec == MB_FP64) {
             if (wall)
                 batch_f64_kernel<true><<<grid64, kNT, 0, s>>>(plan64, item_off64, np, items64, mask, r,
                                                               f, y, partial, PairConsts<double>::make(a), scale);
@@ -730,20 +768,20 @@ mb_status solve_batch(mb_context *ctx, int np, const mb_problem *probs, const mb
         }
         MB_TRY(st);
     }
-    const bool use32 = prm->prec != MB_FP64;
+    const bool use32 = prm->prec != MB_FP64;  // FP32 and double-float read packed positions
     if (use32) MB_TRY(matvec_pack_positions(ctx, bt.r, n_tot, s));
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const auto t1 = clk::now();
 
-    const mb_precision inner = prm->prec == MB_FP64 ? MB_FP64 : MB_FP32_KAHAN;
-    const mb_precision outer = prm->prec == MB_FP32_KAHAN ? MB_FP32_KAHAN : MB_FP64;
+    const mb_precision inner = inner_precision(prm->prec);
+    const mb_precision outer = outer_precision(prm->prec);
     const int vg = vgrid(L);
     const int pg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(np, 128), 1024));
     const BSmall &B = bt.B;
 
     // autotune the packed-kernel shape (2 or 4 targets per thread) on the
     // first inner matvec of the batch: time both on all problems
-    if (use32) {
+    if (inner == MB_FP32_KAHAN) {
         std::vector<int> ones(np, 1);
         MB_CUDA_TRY(ctx, cudaMemcpyAsync(bt.st.notdone, ones.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
         float best = 1e30f;

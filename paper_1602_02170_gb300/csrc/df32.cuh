@@ -1,0 +1,90 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi)/2, giving about 46 significant bits on
+// the FP32 pipes.  Built from the classic error-free transformations:
+// Knuth's two-sum (the exact rounding error of a + b), the fast two-sum of
+// Dekker for |a| >= |b|, and the exact product error of a * b obtained with a
+// fused multiply-add.  The reciprocal square root takes the FP32 estimate and
+// one Newton step y <- y + y (1 - x y^2) / 2 evaluated in double-float, which
+// doubles the number of correct bits.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate; the pair kernel in
+// double-float reaches FP64-class accuracy for the refinement residuals of
+// the mixed-precision solver at a fraction of the FP64 kernel's time.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mb {
+
+struct dfl {
+    float hi, lo;
+
+    __host__ __device__ constexpr dfl() : hi(0.f), lo(0.f) {}
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    // exact split of a double into hi + lo (constant-folded for literals)
+    __host__ __device__ constexpr dfl(double d)
+        : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr dfl(int i) : dfl((double)i) {}
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return dfl(s, e);
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return dfl(s, b - (s - a));
+}
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b)
+{
+    dfl s = two_sum(a.hi, b.hi);
+    const dfl t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+
+__device__ __forceinline__ dfl operator*(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b)
+{
+    a = a + b;
+    return a;
+}
+
+__device__ __forceinline__ bool operator<(dfl a, dfl b)
+{
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+__device__ __forceinline__ dfl mb_max(dfl a, dfl b) { return a < b ? b : a; }
+
+__device__ __forceinline__ dfl mb_rsqrt(dfl x)
+{
+    const float y0 = rsqrtf(x.hi);
+    const dfl y(y0, 0.f);
+    // r = 1 - x y0^2, small; y = y0 + y0 r / 2
+    const dfl r = dfl(1.0) - x * (y * y);
+    return y + dfl(0.5f * y0, 0.f) * r;
+}
+
+__device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace mb

@@ -298,8 +298,8 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     S.sm = (double *)ctx->sol_small.ptr; S.partial = S.sm + sl.total();
     S.hsm = (double *)ctx->host_small;
 
-    const mb_precision inner = p->prec == MB_FP64 ? MB_FP64 : MB_FP32_KAHAN;
-    const mb_precision outer = p->prec == MB_FP32_KAHAN ? MB_FP32_KAHAN : MB_FP64;
+    const mb_precision inner = inner_precision(p->prec);
+    const mb_precision outer = outer_precision(p->prec);
     const int vg = vec_grid(L);
 
     build_rhs_kernel<<<vg, 256, 0, s>>>(n, nb, slip, F, T, S.b);

@@ -115,6 +115,17 @@ mb_status solve_batch(mb_context *ctx, int np, const mb_problem *probs, const mb
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Pair-kernel precision inside the Krylov iteration and for the restart
+// residual of each solver precision mode.
+inline mb_precision inner_precision(mb_precision p)
+{
+    return p == MB_FP64 ? MB_FP64 : (p == MB_DF64 ? MB_DF64 : MB_FP32_KAHAN);
+}
+inline mb_precision outer_precision(mb_precision p)
+{
+    return p == MB_FP64 ? MB_FP64 : (p == MB_FP32_KAHAN ? MB_FP32_KAHAN : MB_DF64);
+}
+
 // Running count of kernels launched through the library (mb_profile_read).
 extern std::atomic<long long> g_launches;
 inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }

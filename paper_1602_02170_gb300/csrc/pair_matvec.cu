@@ -164,6 +164,23 @@ __global__ void __launch_bounds__(kNT) pair_f64_kernel(
     }
 }
 
+template <bool WALL>
+__global__ void __launch_bounds__(kNT) pair_df_kernel(
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts<dfl> k,
+    double *__restrict__ out, double scale, int direct)
+{
+    __shared__ float4 sD[3 * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
+        df_item<WALL, kNT>(sD, hi, lo, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
+                           direct ? scale : 1.0);
+    }
+}
+
 // u_i = scale * sum_s partial[s][i]  (fixed order)
 __global__ void reduce_partials_kernel(const double *__restrict__ partial, int64_t n, int S,
                                        double scale, double *__restrict__ u)
@@ -354,11 +371,14 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
                         double eta, int wall, mb_precision prec, double *u, cudaStream_t s)
 {
     const double scale = 1.0 / (6.0 * kPi * eta * a);
-    if (prec != MB_FP64) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
+    if (prec == MB_FP32_KAHAN) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
+    const bool df = prec == MB_DF64;
     Plan p;
     {
-        const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
-                             : resident_ctas(ctx, pair_f64_kernel<false>);
+        const int res = df ? (wall ? resident_ctas(ctx, pair_df_kernel<true>)
+                                   : resident_ctas(ctx, pair_df_kernel<false>))
+                           : (wall ? resident_ctas(ctx, pair_f64_kernel<true>)
+                                   : resident_ctas(ctx, pair_f64_kernel<false>));
         p = make_plan(n, kNT, res);
     }
     double *out = u;
@@ -368,13 +388,25 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         out = (double *)ctx->partial.ptr;
     }
     auto *ev = profile_begin(ctx, s);
-    const PairConsts<double> k = PairConsts<double>::make(a);
-    if (wall)
-        pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k, out,
-                                                     scale, direct);
-    else
-        pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
-                                                      out, scale, direct);
+    if (df) {
+        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+        const PairConsts<dfl> k = PairConsts<dfl>::make(a);
+        if (wall)
+            pair_df_kernel<true><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks, p.items,
+                                                        k, out, scale, direct);
+        else
+            pair_df_kernel<false><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
+                                                         p.items, k, out, scale, direct);
+    } else {
+        const PairConsts<double> k = PairConsts<double>::make(a);
+        if (wall)
+            pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
+                                                         out, scale, direct);
+        else
+            pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items,
+                                                          k, out, scale, direct);
+    }
     profile_end(ev, s);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());

@@ -7,6 +7,7 @@
 // out + 3 i (i = target index within the problem) multiplied by `m`.
 #pragma once
 
+#include "df32.cuh"
 #include "rpy_wall.cuh"
 
 namespace mb {
@@ -156,6 +157,54 @@ __device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *
         out[3 * i] = m * ux;
         out[3 * i + 1] = m * uy;
         out[3 * i + 2] = m * uz;
+    }
+}
+
+// Double-float item: one target per thread; the same pair formula as the
+// FP32 and FP64 kernels evaluated in double-float (df32.cuh).  Sources are
+// staged as three float4: (x_hi, x_lo, y_hi, y_lo), (z_hi, z_lo, fx_hi,
+// fx_lo), (fy_hi, fy_lo, fz_hi, fz_lo); positions come from the packed hi/lo
+// arrays, forces are split from FP64 on the fly.
+template <bool WALL, int NT>
+__device__ __forceinline__ void df_item(float4 *__restrict__ sD, const float4 *__restrict__ hi,
+                                        const float4 *__restrict__ lo,
+                                        const double *__restrict__ f, int64_t n, int tb,
+                                        int64_t j_begin, int64_t j_end, const PairConsts<dfl> &k,
+                                        double *__restrict__ out, double m)
+{
+    const int64_t i = (int64_t)tb * NT + threadIdx.x;
+    const int64_t ic = i < n ? i : n - 1;
+    const float4 th = hi[ic], tl = lo[ic];
+    const dfl xi(th.x, tl.x), yi(th.y, tl.y), zi(th.z, tl.z);
+    dfl ux, uy, uz;
+    for (int64_t jt = j_begin; jt < j_end; jt += NT) {
+        __syncthreads();
+        {
+            const int64_t j = jt + threadIdx.x;
+            const bool valid = j < j_end;
+            const int64_t jc = valid ? j : j_begin;
+            const float4 h = hi[jc], l = lo[jc];
+            const dfl fx = valid ? dfl(f[3 * jc]) : dfl();
+            const dfl fy = valid ? dfl(f[3 * jc + 1]) : dfl();
+            const dfl fz = valid ? dfl(f[3 * jc + 2]) : dfl();
+            float4 *d = sD + 3 * threadIdx.x;
+            d[0] = make_float4(h.x, l.x, h.y, l.y);
+            d[1] = make_float4(h.z, l.z, fx.hi, fx.lo);
+            d[2] = make_float4(fy.hi, fy.lo, fz.hi, fz.lo);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int s = 0; s < NT; ++s) {
+            const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
+            const dfl zj(B.x, B.y);
+            pair_accumulate<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                                       dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), k, ux, uy, uz);
+        }
+    }
+    if (i < n) {
+        out[3 * i] = m * to_double(ux);
+        out[3 * i + 1] = m * to_double(uy);
+        out[3 * i + 2] = m * to_double(uz);
     }
 }
 

@@ -28,6 +28,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace mb {
 
 // Per-call constants of the pair interaction (units of (6 pi eta a)^-1).
@@ -53,7 +55,7 @@ struct PairConsts {
         k.k1 = T(9.0 / (32.0 * a));
         k.k2 = T(3.0 / (32.0 * a));
         k.sw = T(0.75 * a);
-        k.tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
+        k.tiny = std::is_same<T, double>::value ? T(1e-300) : T(1e-30);
         return k;
     }
 };

@@ -2,7 +2,9 @@
 
 Tolerances: FP64 path 1e-12 (rounding order only); FP32+Kahan path 1e-5
 relative L2 and 1e-5 of max|u| element-wise — the matvec accuracy bar for the
-FP32 path (FP32 pair arithmetic with hi/lo positions; expected ~1e-7).
+FP32 path (FP32 pair arithmetic with hi/lo positions; expected ~1e-7);
+double-float path 1e-10 (about 46 significant bits per operation, positions
+carried as hi + lo FP32 pairs, i.e. to ~2^-48 of their magnitude).
 """
 import numpy as np
 import pytest
@@ -14,10 +16,10 @@ from tests.gpu_common import ctx, dev, host, rel_l2  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "df64": 1e-10}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df64"])
 @pytest.mark.parametrize("wall", [True, False])
 @pytest.mark.parametrize("n", [1, 7, 255, 256, 1537, 5000])
 def test_matvec_small_elementwise(ctx, prec, wall, n):
@@ -31,7 +33,7 @@ def test_matvec_small_elementwise(ctx, prec, wall, n):
     assert rel_l2(got, ref) <= tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df64"])
 def test_matvec_overlaps_coincident_and_contact(ctx, prec):
     """Degenerate pairs: coincident distinct blobs (r = 0), exact contact
     r = 2a, deep overlaps, and blobs at z = a touching the wall."""
@@ -56,7 +58,7 @@ def full_size_case():
     return r, f, a, rows, O.matvec(r, f, a, 1.0, True, targets=rows)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "df64"])
 def test_matvec_full_size_sampled(ctx, full_size_case, prec):
     """The 65,536-blob workload (a = 0.5, xy in [0,400]^2, z in [a,3a]) in
     the launch configuration the benchmark times, checked on 4,096 sampled

@@ -145,6 +145,30 @@ def test_solve_mixed_refinement_small_suspension(ctx):
     _solve_and_compare(ctx, I.config_small_suspension(1), "mixed", 1e-10, 1e-6)
 
 
+def test_solve_df64_small_suspension(ctx):
+    """Double-float pair kernel throughout: same answer as FP64."""
+    _solve_and_compare(ctx, I.config_small_suspension(3), "df64", 1e-10, 1e-6)
+
+
+def test_solve_mixed_monolayer_patch(ctx):
+    """162-blob shells (global-memory factorisation path): mixed precision
+    with double-float residuals reaches 1e-8; sampled residual rows checked
+    with the oracle."""
+    s = I.config_monolayer(2, n_bodies=24, box=14.0)
+    d = _dev_susp(s)
+    U, W, lam, info = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"],
+                                         d["T"], s.a, 1.0, True, tol=1e-8, prec="mixed")
+    assert info["converged"] == 1 and info["rel_residual"] <= 1e-8
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rows = np.random.default_rng(0).choice(s.n_blobs, 200, replace=False)
+    res = O.residual_rows(rows, r, s.q, s.blob_start, host(lam), host(U), host(W), s.a)
+    # ||b|| = ||(F, T)|| here (no slip); per-row residuals well below it
+    bnorm = np.linalg.norm(np.concatenate([s.F, s.T]))
+    assert np.abs(res).max() <= 1e-8 * bnorm
+    Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True)
+    assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
+
+
 def test_solve_fp32_small_suspension(ctx):
     _solve_and_compare(ctx, I.config_small_suspension(2), "fp32", 1e-6, 1e-5)
 
