@@ -290,7 +290,7 @@ typedef struct {
 
 /*
  * Solve many independent mobility problems (Eq. saddle_M, one per problem)
- * together.  All problems share `params` (a, eta, wall, tolerance,
+ * together, on the serving engine below with every problem admitted at once.  All problems share `params` (a, eta, wall, tolerance,
  * iteration limits, precision).  The blob build, K, K^T and the block-
  * diagonal preconditioner of Section 2.2.2 run over all bodies of all
  * problems in one launch each; the pair kernel runs as one persistent launch
@@ -298,7 +298,8 @@ typedef struct {
  * very different sizes share the GPU; each problem keeps its own GMRES
  * state and stops consuming pair-kernel work once converged.  The first
  * FP32 matvec times the packed kernel with 2 and 4 targets per thread and
- * keeps the faster (autotuned tile shape).
+ * keeps the faster (autotuned tile shape).  The arena is sized exactly for
+ * the batch.
  *
  * problems: host array of n_problems descriptors (pointing to device data);
  * infos: host array of n_problems (may be NULL), filled per problem
@@ -311,6 +312,51 @@ typedef struct {
  */
 mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *problems,
                          const mb_params *params, mb_info *infos, void *stream);
+
+/*
+ * Serving: a continuous-batching engine for mobility solves.
+ *
+ * The server owns one device arena, sized at creation by `limits` and
+ * charged to the context's HBM budget: blob and body slots, preconditioner
+ * storage and the Krylov basis of restart length params->restart.  Requests
+ * (mb_problem descriptors, device pointers that must stay valid until the
+ * request completes) are queued by mb_server_submit and admitted first-come
+ * first-served when their blobs, bodies and preconditioner blocks fit in the
+ * arena (admission by HBM footprint) and a request slot is free.  Each
+ * mb_server_step is one scheduling tick: it retires finished requests
+ * (writing U, Omega and lambda to the request's arrays and freeing its
+ * ranges), admits queued ones (blob build, preconditioner factorisation,
+ * right-hand side), computes the true residual of every request starting a
+ * restart cycle, and runs one Arnoldi step of the flexible GMRES of
+ * mb_solve_mobility for every active request — all requests share the same
+ * kernel launches whatever their size or iteration.  Requests submitted
+ * while others are in flight join at the next tick.  A request's result does
+ * not depend on which others share its ticks (up to the solver tolerance).
+ *
+ * mb_server_step synchronises `stream` once per tick and reports how many
+ * requests are running and queued.  mb_server_poll gives a request's state
+ * (0 queued, 1 running, 2 done, 3 failed), its info (setup_ms = time from
+ * submission to admission, solve_ms = admission to completion) and its
+ * status (MB_OK, MB_ENOTCONVERGED, MB_ESINGULAR, MB_EINVAL).  A request too
+ * large for the arena is refused at submission with MB_ENOMEM.
+ */
+typedef struct mb_server mb_server;
+
+typedef struct {
+    int64_t max_blobs;          /* blob slots in the arena                   */
+    int64_t max_bodies;         /* body slots                                */
+    int64_t max_precond_bytes;  /* storage for the bodies' preconditioner
+                                   blocks: (3 n_p + 6)^2 doubles per body    */
+    int max_requests;           /* requests in flight at once                */
+} mb_server_limits;
+
+mb_status mb_server_create(mb_context *ctx, const mb_params *params,
+                           const mb_server_limits *limits, mb_server **server);
+mb_status mb_server_destroy(mb_server *server);
+mb_status mb_server_submit(mb_server *server, const mb_problem *problem, int64_t *ticket);
+mb_status mb_server_step(mb_server *server, void *stream, int *n_running, int *n_queued);
+mb_status mb_server_poll(mb_server *server, int64_t ticket, int *state, mb_info *info,
+                         mb_status *result);
 
 #ifdef __cplusplus
 }

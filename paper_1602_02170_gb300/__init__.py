@@ -23,6 +23,7 @@ __all__ = [
     "EXPORTED_SYMBOLS",
     "mobility_matvec_noalloc",
     "NOALLOC_MAX_BLOBS",
+    "Server",
 ]
 
 FP64, FP32_KAHAN, MIXED_REFINE, DF64 = 0, 1, 2, 3
@@ -58,6 +59,11 @@ EXPORTED_SYMBOLS = [
     "mb_precond_apply",
     "mb_solve_mobility",
     "mb_solve_batch",
+    "mb_server_create",
+    "mb_server_destroy",
+    "mb_server_submit",
+    "mb_server_step",
+    "mb_server_poll",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +106,15 @@ class Problem(ctypes.Structure):
         ("U", ctypes.c_void_p),
         ("Omega", ctypes.c_void_p),
         ("lam", ctypes.c_void_p),
+    ]
+
+
+class ServerLimits(ctypes.Structure):
+    _fields_ = [
+        ("max_blobs", ctypes.c_int64),
+        ("max_bodies", ctypes.c_int64),
+        ("max_precond_bytes", ctypes.c_int64),
+        ("max_requests", ctypes.c_int),
     ]
 
 
@@ -159,6 +174,13 @@ def load_library():
     ]
     L.mb_solve_batch.argtypes = [vp, ci, ctypes.POINTER(Problem), ctypes.POINTER(Params),
                                  ctypes.POINTER(Info), vp]
+    L.mb_server_create.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(ServerLimits),
+                                   ctypes.POINTER(vp)]
+    L.mb_server_destroy.argtypes = [vp]
+    L.mb_server_submit.argtypes = [vp, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+    L.mb_server_step.argtypes = [vp, vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.mb_server_poll.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(Info),
+                                 ctypes.POINTER(ci)]
     for name in EXPORTED_SYMBOLS:
         if name not in ("mb_status_string", "mb_last_error", "mb_context_workspace_bytes"):
             getattr(L, name).restype = ci  # mb_status
@@ -416,4 +438,88 @@ class Context:
         if not (st == 4 and not raise_on_nonconvergence):
             self._check(st)
         return [(U, Om, lam, infos[k].as_dict()) for k, (U, Om, lam) in enumerate(outs)]
+
+
+class Server:
+    """Continuous-batching solver service on a context (mb_server_*).
+
+    submit() queues a problem (dict of CUDA tensors as for
+    Context.solve_batch) and returns a ticket; step() runs one scheduling
+    tick; poll() reports (state, info, status) with state 0 queued,
+    1 running, 2 done, 3 failed.  Results land in the tensors returned by
+    submit(); keep the inputs alive until the ticket is done."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, ctx, a, eta=1.0, wall=True, tol=1e-10, maxit=200, restart=60,
+                 prec="mixed", max_blobs=1 << 20, max_bodies=1 << 16,
+                 max_precond_bytes=4 << 30, max_requests=256):
+        self.ctx = ctx
+        self.L = ctx.L
+        self._torch = ctx._torch
+        p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
+                   _prec(prec))
+        lim = ServerLimits(int(max_blobs), int(max_bodies), int(max_precond_bytes),
+                           int(max_requests))
+        h = ctypes.c_void_p()
+        self._check(self.L.mb_server_create(ctx.handle, ctypes.byref(p), ctypes.byref(lim),
+                                            ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def _check(self, st):
+        if st != 0:
+            raise MBError(st, self.L.mb_last_error(self.ctx.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.L.mb_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, P):
+        """Queue a problem; returns (ticket, (U, Omega, lambda) output tensors)."""
+        torch = self._torch
+        nb, nbl = int(P["q"].shape[0]), int(P["rho"].shape[0])
+        dev = P["q"].device
+        U = torch.empty((nb, 3), dtype=torch.float64, device=dev)
+        Om = torch.empty((nb, 3), dtype=torch.float64, device=dev)
+        lam = torch.empty((nbl, 3), dtype=torch.float64, device=dev)
+        slip = P.get("slip")
+        pr = Problem(nb, nbl, P["q"].data_ptr(), P["theta"].data_ptr(), P["blob_start"].data_ptr(),
+                     P["rho"].data_ptr(), P["F"].data_ptr(), P["T"].data_ptr(),
+                     0 if slip is None else slip.data_ptr(), U.data_ptr(), Om.data_ptr(),
+                     lam.data_ptr())
+        t = ctypes.c_int64()
+        self._check(self.L.mb_server_submit(self.handle, ctypes.byref(pr), ctypes.byref(t)))
+        self._keep[t.value] = (P, U, Om, lam)
+        return t.value, (U, Om, lam)
+
+    def step(self, stream=None):
+        """One scheduling tick; returns (n_running, n_queued)."""
+        nr, nq = ctypes.c_int(), ctypes.c_int()
+        self._check(self.L.mb_server_step(self.handle, self.ctx._stream(stream), ctypes.byref(nr),
+                                          ctypes.byref(nq)))
+        return nr.value, nq.value
+
+    def poll(self, ticket):
+        st, res = ctypes.c_int(), ctypes.c_int()
+        info = Info()
+        self._check(self.L.mb_server_poll(self.handle, int(ticket), ctypes.byref(st),
+                                          ctypes.byref(info), ctypes.byref(res)))
+        if st.value in (self.DONE, self.FAILED):
+            self._keep.pop(int(ticket), None)
+        return st.value, info.as_dict(), STATUS.get(res.value, str(res.value))
+
+    def run_until_idle(self, stream=None, max_ticks=1_000_000):
+        for _ in range(max_ticks):
+            nr, nq = self.step(stream)
+            if nr == 0 and nq == 0:
+                return
+        raise RuntimeError("server did not drain")
 

@@ -99,6 +99,12 @@ void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                         const double *q, const int64_t *blob_start, double a, double eta,
                         int wall, cudaStream_t s);
+// Asynchronous setup of the blocks of nb bodies: start (nb+1, global blob
+// indices), poff (nb offsets into P); a failing body sets flags[flag_slot] = 2.
+mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, const double *q,
+                              const int64_t *start, const int64_t *poff, double *P, int max_np,
+                              double a, double eta, int wall, int *flags, int flag_slot,
+                              cudaStream_t s);
 // z = P^-1 v where v = [w (3N); g (6 n_b)] packed contiguously, same for z.
 void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s);
 
@@ -109,7 +115,7 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                          const mb_params *p, double *U, double *Omega, double *lambda,
                          mb_info *info, cudaStream_t s);
 
-// Batched solves (batch.cu)
+// Batched solves on the serving engine (server.cu)
 mb_status solve_batch(mb_context *ctx, int np, const mb_problem *probs, const mb_params *prm,
                       mb_info *infos, cudaStream_t s);
 

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
     const int64_t *__restrict__ start, const int64_t *__restrict__ poff, PairConsts<double> k,
     double scale, double *__restrict__ P, double *__restrict__ scratch, int64_t scratch_stride,
-    int *__restrict__ flag)
+    int *__restrict__ flag, int flag_slot)
 {
     extern __shared__ double sm[];
     for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
@@ -80,7 +80,10 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
             __syncthreads();
         }
         if (bad) {
-            if (threadIdx.x == 0) atomicMin(flag, (int)p);
+            if (threadIdx.x == 0) {
+                if (flag_slot >= 0) flag[flag_slot] = 2;
+                else atomicMin(flag, (int)p);
+            }
             __syncthreads();
             continue;
         }
@@ -167,7 +170,10 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
         }
         __syncthreads();
         if (bad) {
-            if (threadIdx.x == 0) atomicMin(flag, (int)p);
+            if (threadIdx.x == 0) {
+                if (flag_slot >= 0) flag[flag_slot] = 2;
+                else atomicMin(flag, (int)p);
+            }
             __syncthreads();
             continue;
         }
@@ -290,7 +296,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                                (const int64_t *)ctx->pinv_off.ptr, k, scale,
                                                (double *)ctx->pinv.ptr, scratch, stride,
-                                               (int *)ctx->flag.ptr);
+                                               (int *)ctx->flag.ptr, -1);
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
@@ -316,6 +322,42 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                        first_bad);
     }
     return MB_OK;
+}
+
+mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, const double *q,
+                              const int64_t *start, const int64_t *poff, double *P, int max_np,
+                              double a, double eta, int wall, int *flags, int flag_slot,
+                              cudaStream_t s)
+{
+    const int nmax = 3 * max_np;
+    const bool lsmem = nmax <= kSmemMaxRows;
+    const size_t small = sizeof(double) * (12 * (size_t)nmax + 72);
+    const size_t smem = small + (lsmem ? sizeof(double) * (size_t)nmax * nmax : 0);
+    const PairConsts<double> k = PairConsts<double>::make(a);
+    const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
+    int grid = (int)std::min<int64_t>(nb, 4 * (int64_t)ctx->sm_count);
+    double *scratch = nullptr;
+    int64_t stride = 0;
+    if (!lsmem) {
+        grid = (int)std::min<int64_t>(nb, ctx->sm_count);
+        stride = (int64_t)nmax * nmax;
+        MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
+        scratch = (double *)ctx->sol_dots.ptr;
+    }
+    auto launch = [&](auto kern) -> mb_status {
+        MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, start, poff, k, scale, P, scratch, stride,
+                                               flags, flag_slot);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    };
+    if (wall)
+        return lsmem ? launch(precond_setup_kernel<true, true>)
+                     : launch(precond_setup_kernel<true, false>);
+    return lsmem ? launch(precond_setup_kernel<false, true>)
+                 : launch(precond_setup_kernel<false, false>);
 }
 
 static void precond_apply_impl(mb_context *ctx, const double *w, const double *g, double *lam,

@@ -1,0 +1,116 @@
+"""Serving engine (mb_server_*): continuous batching, admission by footprint,
+and per-request results that do not depend on the other requests in flight.
+
+Bar: each request's body velocities within 1e-6 relative of the same problem
+solved alone (mb_solve_mobility) and of the oracle's direct solve.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1602_02170_gb300 as mb
+from oracle import oracle as O
+from paper_1602_02170_gb300 import inputs as I
+from tests.gpu_common import ctx, dev, host, rel_l2  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+A = 0.1625
+
+
+def _prob(s):
+    return dict(q=dev(s.q), theta=dev(s.theta), blob_start=dev(s.blob_start, torch.int64),
+                rho=dev(s.rho), F=dev(s.F), T=dev(s.T))
+
+
+def _alone(ctx, P):
+    U, W, lam, _ = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"], P["T"],
+                                      A, 1.0, True, tol=1e-10, prec="mixed")
+    return host(U), host(W)
+
+
+def test_server_requests_join_mid_flight(ctx):
+    first = [I.mixed_suspension(200 + k, nb) for k, nb in enumerate([12, 5])]
+    later = [I.mixed_suspension(300 + k, nb) for k, nb in enumerate([3, 9, 1])]
+    srv = mb.Server(ctx, A, tol=1e-10, prec="mixed", max_blobs=20000, max_bodies=500,
+                    max_requests=16)
+    probs, tickets, outs = [], [], []
+    for s in first:
+        P = _prob(s)
+        t, o = srv.submit(P)
+        probs.append((s, P)); tickets.append(t); outs.append(o)
+    srv.step()
+    srv.step()
+    assert srv.poll(tickets[0])[0] == mb.Server.RUNNING
+    for s in later:
+        P = _prob(s)
+        t, o = srv.submit(P)
+        probs.append((s, P)); tickets.append(t); outs.append(o)
+    nr, nq = srv.step()
+    # the late requests were admitted while the first ones were still running
+    assert nr == 5 and nq == 0
+    assert srv.poll(tickets[0])[0] == mb.Server.RUNNING
+    srv.run_until_idle()
+    for (s, P), t, (U, W, lam) in zip(probs, tickets, outs):
+        state, info, status = srv.poll(t)
+        assert state == mb.Server.DONE and status == "MB_OK", (state, status, info)
+        assert info["converged"] == 1 and info["rel_residual"] <= 1e-10
+        Ua, Wa = _alone(ctx, P)
+        assert rel_l2(host(U), Ua) <= 1e-6 and rel_l2(host(W), Wa) <= 1e-6
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        Ur, Wr, lr = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
+        assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
+        assert rel_l2(host(lam), lr) <= 1e-5
+    srv.close()
+
+
+def test_server_admission_by_footprint(ctx):
+    """An arena with room for one request at a time still serves them all,
+    one after the other; a request bigger than the arena is refused."""
+    susp = [I.mixed_suspension(400 + k, 6) for k in range(3)]
+    cap = max(s.n_blobs for s in susp) + 10
+    srv = mb.Server(ctx, A, tol=1e-10, prec="fp64", max_blobs=cap, max_bodies=64,
+                    max_requests=8)
+    tickets, outs = [], []
+    for s in susp:
+        t, o = srv.submit(_prob(s))
+        tickets.append(t); outs.append(o)
+    most = 0
+    for _ in range(10000):
+        nr, nq = srv.step()
+        most = max(most, nr)
+        if nr == 0 and nq == 0:
+            break
+    assert most == 1
+    for s, t, (U, W, lam) in zip(susp, tickets, outs):
+        assert srv.poll(t)[0] == mb.Server.DONE
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
+        assert rel_l2(host(U), Ur) <= 1e-6
+    big = I.mixed_suspension(9, 40)
+    with pytest.raises(mb.MBError) as ei:
+        srv.submit(_prob(big))
+    assert ei.value.name == "MB_ENOMEM"
+    srv.close()
+
+
+def test_server_isolates_a_failing_request(ctx):
+    good = [I.mixed_suspension(500 + k, 4) for k in range(2)]
+    s = I.mixed_suspension(510, 4)
+    q = s.q.copy()
+    r = O.blob_positions(q, s.theta, s.blob_start, s.rho)
+    q[0, 2] -= r[s.blob_start[0]:s.blob_start[1], 2].min() - 0.5 * A
+    badP = _prob(s)
+    badP["q"] = dev(q)
+    srv = mb.Server(ctx, A, tol=1e-10, prec="mixed", max_blobs=5000, max_bodies=100,
+                    max_requests=8)
+    t0, o0 = srv.submit(_prob(good[0]))
+    tb, _ = srv.submit(badP)
+    t1, o1 = srv.submit(_prob(good[1]))
+    srv.run_until_idle()
+    assert srv.poll(tb)[0] == mb.Server.FAILED and srv.poll(tb)[2] == "MB_ESINGULAR"
+    for g, t, (U, W, lam) in ((good[0], t0, o0), (good[1], t1, o1)):
+        assert srv.poll(t)[0] == mb.Server.DONE
+        rg = O.blob_positions(g.q, g.theta, g.blob_start, g.rho)
+        Ur, Wr, _ = O.solve_saddle(rg, g.q, g.blob_start, g.F, g.T, A, 1.0, True)
+        assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
+    srv.close()
