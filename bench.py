@@ -68,6 +68,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-solve", action="store_true")
     p.add_argument("--solves", type=int, default=30)
+    p.add_argument("--workload", choices=["matvec", "monolayer", "batch", "serve"],
+                   default="matvec",
+                   help="matvec: the benchmark line below; monolayer / batch / serve: the "
+                        "663,552-blob monolayer solve, 256 batched suspensions, and the "
+                        "serving stream, each printing its own JSON line")
+    p.add_argument("--serve-seconds", type=float, default=30.0)
+    p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--pool", type=int, default=40)
     return p.parse_args()
 
 
@@ -367,10 +375,228 @@ def bench_solves(ctx, count):
             "iters": infos[-1]["iters"], "rel_err_U": eU, "rel_err_Omega": eW}
 
 
+def _dev_problem(s):
+    import numpy as np
+    import torch
+
+    d = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x)).to("cuda", dt)
+    return dict(q=d(s.q), theta=d(s.theta), blob_start=d(s.blob_start, torch.int64), rho=d(s.rho),
+                F=d(s.F), T=d(s.T))
+
+
+def bench_monolayer(args):
+    """4,096 shells of 162 blobs (N = 663,552) above the wall, mixed precision
+    (FP32 pair kernel in the Krylov iteration, double-float restart
+    residuals) to a true relative residual of 1e-8."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from oracle import oracle as O
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    s = I.config_monolayer(1)
+    P = _dev_problem(s)
+    # size-class autotuning of the FP32 kernel happens on this first matvec
+    r = ctx.blob_positions(P["q"], P["theta"], P["blob_start"], P["rho"])
+    ctx.mobility_matvec(r, torch.ones_like(r), s.a, 1.0, True, "fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U, W, lam, info = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"],
+                                         P["T"], s.a, 1.0, True, tol=1e-8, maxit=300, restart=60,
+                                         prec="mixed")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rows = np.random.default_rng(3).choice(s.n_blobs, 128, replace=False)
+    rr = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    res = O.residual_rows(rows, rr, s.q, s.blob_start, lam.cpu().numpy(), U.cpu().numpy(),
+                          W.cpu().numpy(), s.a)
+    bnorm = float(np.linalg.norm(np.concatenate([s.F, s.T])))
+    line = {"metric": "mobility solves/s", "workload": "monolayer: 4096 x 162-blob shells, "
+            "N=663552, a=0.12, 200x200 patch, z in [1.2,1.6]", "value": 1.0 / dt,
+            "unit": "solves/s", "seconds": dt, "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)",
+            "info": info, "pairs_per_matvec": float(s.n_blobs) ** 2,
+            "oracle_sampled_residual_rows_max_over_bnorm": float(np.abs(res).max() / bnorm),
+            "oracle_rows": int(len(rows)), "n_gpus": 1}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def bench_batch(args):
+    """256 independent mixed suspensions (42-blob shells and 15-blob
+    boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
+    to 1e-8; compared on a random subset with the plain FP64 path solving one
+    problem at a time, at the same tolerance."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from oracle import oracle as O
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    t0 = time.perf_counter()
+    susp = I.config_batched(1)
+    gen_s = time.perf_counter() - t0
+    probs = [_dev_problem(s) for s in susp]
+    a = susp[0].a
+    ctx.solve_batch(probs[:4], a, tol=1e-8, prec="mixed")  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ctx.solve_batch(probs, a, tol=1e-8, maxit=300, restart=60, prec="mixed")
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    iters = [r[3]["iters"] for r in res]
+    rng = np.random.default_rng(5)
+    sub = sorted(rng.choice(len(susp), 8, replace=False).tolist())
+    t0 = time.perf_counter()
+    sub_batch = ctx.solve_batch([probs[k] for k in sub], a, tol=1e-8, prec="mixed")
+    torch.cuda.synchronize()
+    t_sub_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sub_fp64 = []
+    for k in sub:
+        P = probs[k]
+        sub_fp64.append(ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"],
+                                           P["T"], a, 1.0, True, tol=1e-8, maxit=300, restart=60,
+                                           prec="fp64"))
+    torch.cuda.synchronize()
+    t_sub_fp64 = time.perf_counter() - t0
+    diff = max(float(((x[0] - y[0]).norm() / y[0].norm()).item()) for x, y in zip(sub_batch, sub_fp64))
+    oracle_err = []
+    for k in sub:
+        s = susp[k]
+        if s.n_blobs <= 1500:
+            rr = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+            Ur, _, _ = O.solve_saddle(rr, s.q, s.blob_start, s.F, s.T, a, 1.0, True)
+            oracle_err.append(float(np.linalg.norm(res[k][0].cpu().numpy() - Ur) / np.linalg.norm(Ur)))
+    pairs = float(sum(s.n_blobs ** 2 for s in susp))
+    line = {"metric": "mobility solves/s", "workload": "batched: 256 mixed suspensions "
+            "(42-blob shells / 15-blob boomerangs, a=0.1625), bodies log-uniform 8..2048, "
+            "z in [1.2,3]", "value": len(susp) / t_batch, "unit": "solves/s", "seconds": t_batch,
+            "tol": 1e-8, "prec": "mixed (fp32 + df64 residual), one batched launch per kernel",
+            "n_blobs_total": int(sum(s.n_blobs for s in susp)),
+            "n_bodies_total": int(sum(s.n_bodies for s in susp)),
+            "pairs_per_batched_matvec": pairs, "iters_median": float(np.median(iters)),
+            "iters_max": int(max(iters)), "generation_s": gen_s,
+            "subset": {"problems": sub, "batched_mixed_solves_per_s": len(sub) / t_sub_batch,
+                       "fp64_one_at_a_time_solves_per_s": len(sub) / t_sub_fp64,
+                       "max_rel_diff_U_batched_vs_fp64": diff,
+                       "oracle_rel_err_U_small_problems": oracle_err},
+            "n_gpus": 1}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def bench_serve(args):
+    """Poisson stream of mobility solves (mean args.rate requests/s) with blob
+    counts log-uniform in [100, 2e5] (mixed shells and boomerangs), served
+    by the continuous-batching engine; then a sweep at 0.5x and 0.8x of the
+    measured capacity so that p99 latency is meaningful."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    t0 = time.perf_counter()
+    pool = [I.config_serving_request(1000 + k) for k in range(args.pool)]
+    gen_s = time.perf_counter() - t0
+    a = pool[0].a
+    dpool = [_dev_problem(s) for s in pool]
+    sizes = [s.n_blobs for s in pool]
+
+    def run(rate, seconds, seed, drain):
+        srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
+                        max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=512)
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 2) + 16))
+        arrivals = arrivals[arrivals < seconds]
+        picks = rng.integers(0, len(pool), len(arrivals))
+        inflight, lat, sizes_done = {}, [], []
+        nsub = 0
+        start = time.perf_counter()
+        ticks = 0
+        while True:
+            now = time.perf_counter() - start
+            while nsub < len(arrivals) and arrivals[nsub] <= now:
+                t, outs = srv.submit(dpool[picks[nsub]])
+                inflight[t] = (arrivals[nsub], picks[nsub], outs)
+                nsub += 1
+            nr, nq = srv.step()
+            ticks += 1
+            now = time.perf_counter() - start
+            for t in list(inflight):
+                st_, info, status = srv.poll(t)
+                if st_ in (mb.Server.DONE, mb.Server.FAILED):
+                    arr, k, _ = inflight.pop(t)
+                    if st_ == mb.Server.DONE and status == "MB_OK":
+                        lat.append(now - arr)
+                        sizes_done.append(sizes[k])
+            if now >= seconds and (not drain or (nr == 0 and nq == 0 and nsub == len(arrivals))):
+                break
+            if nr == 0 and nq == 0 and nsub < len(arrivals):
+                time.sleep(max(0.0, min(arrivals[nsub] - now, 0.01)))
+        wall = time.perf_counter() - start
+        srv.close()
+        lat_ms = sorted(1e3 * x for x in lat)
+        pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(math.ceil(q * len(lat_ms))) - 1)] if lat_ms else None
+        return {"rate_offered": rate, "window_s": seconds, "wall_s": wall, "offered": int(len(arrivals)),
+                "served": len(lat), "served_per_s": len(lat) / wall, "p50_ms": pct(0.5),
+                "p99_ms": pct(0.99), "unserved_at_end": int(len(arrivals) - len(lat)),
+                "ticks": ticks, "mean_served_blobs": float(np.mean(sizes_done)) if sizes_done else None}
+
+    # the same request alone vs in the mix
+    check = []
+    for k in np.argsort(sizes)[:3]:
+        P = dpool[k]
+        Ua = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"], P["T"], a,
+                                1.0, True, tol=1e-8, prec="mixed")[0]
+        check.append((k, Ua))
+    sat = run(args.rate, args.serve_seconds, 1, drain=False)
+    cap = max(sat["served_per_s"], 1e-3)
+    sub = [run(f * cap, max(10.0, args.serve_seconds * 0.6), 2 + i, drain=True)
+           for i, f in enumerate((0.5, 0.8))]
+    # mix check: serve the three small requests together with a large one
+    srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
+                    max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=64)
+    big = int(np.argmax(sizes))
+    tickets = [srv.submit(dpool[big])[0]] + [srv.submit(dpool[k]) for k, _ in check]
+    srv.run_until_idle()
+    mix_diff = max(float(((t[1][0] - Ua).norm() / Ua.norm()).item())
+                   for t, (k, Ua) in zip(tickets[1:], check))
+    srv.close()
+    line = {"metric": "mobility solves/s and p99 latency", "workload": "serving: Poisson "
+            f"{args.rate:g} req/s, blobs log-uniform 100..2e5 (mixed shells/boomerangs), "
+            f"pool of {len(pool)} seeded requests", "value": sat["served_per_s"], "unit": "solves/s",
+            "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)", "saturated": sat,
+            "sub_saturation": sub, "same_alone_and_in_mix_max_rel_diff_U": mix_diff,
+            "pool_generation_s": gen_s, "n_gpus": 1}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "monolayer":
+        return bench_monolayer(args)
+    if args.workload == "batch":
+        return bench_batch(args)
+    if args.workload == "serve":
+        return bench_serve(args)
     return run_ours(args)
 
 

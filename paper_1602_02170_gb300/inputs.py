@@ -305,13 +305,15 @@ def mixed_suspension(
 
     One blob radius serves the whole suspension (the mobility has a single
     a); it is the smaller of the two shape radii so that every body keeps its
-    blobs at a/s <= 1/2.  The patch side defaults to sqrt(n_b / 0.08), the
-    body area density of 8 bodies per 10 x 10.
+    blobs at a/s <= 1/2.  The patch side defaults to sqrt(n_b / 0.04): half
+    the body area density of 8 bodies per 10 x 10, because placement rejects
+    on bounding spheres (boomerang bounding radius 1.64) and jams at the full
+    density for hundreds of bodies.
     """
     rng = np.random.default_rng(seed)
     a = min(sphere_a, boomerang_a)
     if box is None:
-        box = math.sqrt(n_bodies / 0.08)
+        box = math.sqrt(n_bodies / 0.04)
     kinds = rng.integers(0, 2, n_bodies)  # 0 = sphere, 1 = boomerang
     sph = shell(42, 1.0)
     boo = boomerang15()
