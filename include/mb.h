@@ -154,7 +154,10 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
  *       calls — so make that first call before any stream capture;
  *    0  scalar FP32 kernel, one target per thread;
  *    1  packed FP32 kernel (paired f32x2 arithmetic), two targets per thread;
- *    2  packed FP32 kernel, four targets per thread.
+ *    2  packed FP32 kernel, four targets per thread;
+ *    3  symmetric packed FP32 kernel: each unordered pair evaluated once
+ *       for both blobs (M_ji = M_ij^T), partial sums added to u with FP64
+ *       atomics, so results may differ between calls in the last FP64 bits.
  * All variants compute the same product to FP32 rounding.  Other values are
  * MB_EINVAL.  Setting a variant clears the autotuner's cache.
  */

@@ -147,6 +147,29 @@ __global__ void __launch_bounds__(kNT, NP == 1 ? 3 : 2) pair_f32x2_kernel(
     }
 }
 
+// Symmetric packed kernel: persistent loop over the upper-triangular block
+// pairs (I <= J) of blocks of 2*kNT blobs, row by row; see x2sym_item.
+template <bool WALL>
+__global__ void __launch_bounds__(kNT, 2) pair_sym_kernel(
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t n, int64_t nb, int64_t n_items, PairConsts2 k, double *__restrict__ u, double scale)
+{
+    __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
+    __shared__ float sRev[3 * kNT * (kNT / 32)];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        // row I holds nb - I items; rowoff(I) = I*nb - I*(I-1)/2
+        int64_t lo_r = 0, hi_r = nb;
+        while (hi_r - lo_r > 1) {
+            const int64_t mid = (lo_r + hi_r) >> 1;
+            if (mid * nb - mid * (mid - 1) / 2 <= item) lo_r = mid;
+            else hi_r = mid;
+        }
+        const int64_t I = lo_r;
+        const int64_t J = I + (item - (I * nb - I * (I - 1) / 2));
+        x2sym_item<WALL, kNT>(sP, sRev, hi, lo, f, n, I, J, k, u, scale);
+    }
+}
+
 template <bool WALL>
 __global__ void __launch_bounds__(kNT) pair_f64_kernel(
     const double *__restrict__ r, const double *__restrict__ f, int64_t n, int64_t chunk,
@@ -249,15 +272,16 @@ constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 //   0: scalar kernel, kTPT targets per thread
 //   1: packed f32x2 kernel, 2 targets per thread
 //   2: packed f32x2 kernel, 4 targets per thread
-constexpr int kF32Variants = 3;
+constexpr int kF32Variants = 4;
 
-int f32_targets_per_cta(int v) { return v == 0 ? kNT * kTPT : (v == 1 ? 2 * kNT : 4 * kNT); }
+int f32_targets_per_cta(int v) { return v == 0 ? kNT * kTPT : (v == 2 ? 4 * kNT : 2 * kNT); }
 
 template <bool WALL>
 int f32_resident(mb_context *ctx, int v)
 {
     if (v == 0) return resident_ctas(ctx, pair_f32_kernel<WALL, kTPT>);
     if (v == 1) return resident_ctas(ctx, pair_f32x2_kernel<WALL, 1>);
+    if (v == 3) return resident_ctas(ctx, pair_sym_kernel<WALL>);
     return resident_ctas(ctx, pair_f32x2_kernel<WALL, 2>);
 }
 
@@ -283,6 +307,25 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
                   double scale, double *u, cudaStream_t s, bool profile)
 {
     const int res = wall ? f32_resident<true>(ctx, v) : f32_resident<false>(ctx, v);
+    if (v == 3) {
+        // symmetric: zero u, then one launch over the block-pair triangle
+        const int64_t nb = ceil_div(n, 2 * kNT);
+        const int64_t items = nb * (nb + 1) / 2;
+        const int grid = (int)std::min<int64_t>(items, res);
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        auto *ev = profile ? profile_begin(ctx, s) : nullptr;
+        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+        const PairConsts2 k = PairConsts2::make(a);
+        if (wall)
+            pair_sym_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        else
+            pair_sym_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        profile_end(ev, s);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    }
     const Plan p = make_plan(n, f32_targets_per_cta(v), res);
     double *out = u;
     const int direct = p.S == 1;

@@ -208,4 +208,126 @@ __device__ __forceinline__ void df_item(float4 *__restrict__ sD, const float4 *_
     }
 }
 
+// Symmetric packed item over block pair (I, J), I <= J, blocks of 2*NT blobs
+// (two targets per thread, as in x2_item with NP = 1).  Each unordered pair
+// is evaluated once: forward contributions accumulate in the thread's
+// registers (tile sums folded Kahan-style), reverse contributions to the
+// sources are warp-reduced per source, summed over the CTA's warps in
+// shared memory in a fixed order, and added to u with FP64 atomics.
+// Diagonal items (I == J) run forward only over all ordered pairs.
+// u must be zeroed beforehand and receives scale * M f.
+template <bool WALL, int NT>
+__device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__restrict__ sRev,
+                                           const float4 *__restrict__ hi,
+                                           const float4 *__restrict__ lo,
+                                           const double *__restrict__ f, int64_t n, int64_t I,
+                                           int64_t J, const PairConsts2 &k,
+                                           double *__restrict__ u, double scale)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool diag = I == J;
+    const int64_t ia = I * 2 * NT + threadIdx.x, ib = ia + NT;
+    float2 xh, yh, zh, xl, yl, zl, fix, fiy, fiz;
+    {
+        const int64_t ca = ia < n ? ia : n - 1, cb = ib < n ? ib : n - 1;
+        const float4 ha = hi[ca], hb = hi[cb], la = lo[ca], lb = lo[cb];
+        xh = make_float2(ha.x, hb.x); yh = make_float2(ha.y, hb.y); zh = make_float2(ha.z, hb.z);
+        xl = make_float2(la.x, lb.x); yl = make_float2(la.y, lb.y); zl = make_float2(la.z, lb.z);
+        // padding targets carry no force, so their reverse contributions vanish
+        fix = make_float2(ia < n ? (float)f[3 * ia] : 0.f, ib < n ? (float)f[3 * ib] : 0.f);
+        fiy = make_float2(ia < n ? (float)f[3 * ia + 1] : 0.f, ib < n ? (float)f[3 * ib + 1] : 0.f);
+        fiz = make_float2(ia < n ? (float)f[3 * ia + 2] : 0.f, ib < n ? (float)f[3 * ib + 2] : 0.f);
+    }
+    float sum[2][3], comp[2][3];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sum[t][c] = comp[t][c] = 0.f;
+    for (int sub = 0; sub < 2; ++sub) {
+        const int64_t j0 = J * 2 * NT + sub * NT;
+        if (j0 >= n) break;
+        __syncthreads();
+        {
+            const int64_t j = j0 + threadIdx.x;
+            const bool valid = j < n;
+            const int64_t jc = valid ? j : j0;
+            const float4 h = hi[jc], l = lo[jc];
+            const float fx = valid ? (float)f[3 * jc] : 0.f;
+            const float fy = valid ? (float)f[3 * jc + 1] : 0.f;
+            const float fz = valid ? (float)f[3 * jc + 2] : 0.f;
+            float4 *d = sP + kX2SmemFloat4PerSource * threadIdx.x;
+            d[0] = make_float4(-h.x, -h.x, -h.y, -h.y);
+            d[1] = make_float4(-h.z, -h.z, h.z, h.z);
+            d[2] = make_float4(-l.x, -l.x, -l.y, -l.y);
+            d[3] = make_float4(-l.z, -l.z, fx, fx);
+            d[4] = make_float4(fy, fy, fz, fz);
+        }
+        __syncthreads();
+        float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+#pragma unroll 2
+        for (int s = 0; s < NT; ++s) {
+            const float4 *P = sP + kX2SmemFloat4PerSource * s;
+            const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
+            const float2 dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
+            const float2 dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
+            const float2 dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
+            const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
+            const float2 zj = make_float2(P1.z, P1.w);
+            const float2 fx = make_float2(P3.z, P3.w), fy = make_float2(P4.x, P4.y),
+                         fz = make_float2(P4.z, P4.w);
+            if (diag) {
+                pair_accumulate2<WALL>(dx, dy, dz, dxy2, zh, zj, fx, fy, fz, k, ax, ay, az);
+            } else {
+                float2 rx, ry, rz;
+                pair_sym2<WALL>(dx, dy, dz, dxy2, zh, zj, fx, fy, fz, fix, fiy, fiz, k, ax, ay, az,
+                                rx, ry, rz);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    rx.x += __shfl_xor_sync(0xffffffffu, rx.x, o);
+                    rx.y += __shfl_xor_sync(0xffffffffu, rx.y, o);
+                    ry.x += __shfl_xor_sync(0xffffffffu, ry.x, o);
+                    ry.y += __shfl_xor_sync(0xffffffffu, ry.y, o);
+                    rz.x += __shfl_xor_sync(0xffffffffu, rz.x, o);
+                    rz.y += __shfl_xor_sync(0xffffffffu, rz.y, o);
+                }
+                if (lane == 0) {
+                    float *o3 = sRev + 3 * (warp * NT + s);
+                    o3[0] = rx.x + rx.y;
+                    o3[1] = ry.x + ry.y;
+                    o3[2] = rz.x + rz.y;
+                }
+            }
+        }
+        kahan_add(sum[0][0], comp[0][0], ax.x);
+        kahan_add(sum[0][1], comp[0][1], ay.x);
+        kahan_add(sum[0][2], comp[0][2], az.x);
+        kahan_add(sum[1][0], comp[1][0], ax.y);
+        kahan_add(sum[1][1], comp[1][1], ay.y);
+        kahan_add(sum[1][2], comp[1][2], az.y);
+        if (!diag) {
+            __syncthreads();
+            const int64_t j = j0 + threadIdx.x;
+            if (j < n) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) acc += sRev[3 * (w * NT + threadIdx.x) + c];
+                    atomicAdd(u + 3 * j + c, scale * (double)acc);
+                }
+            }
+        }
+    }
+    if (ia < n)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            atomicAdd(u + 3 * ia + c, scale * ((double)sum[0][c] - (double)comp[0][c]));
+    if (ib < n)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            atomicAdd(u + 3 * ib + c, scale * ((double)sum[1][c] - (double)comp[1][c]));
+}
+
 }  // namespace mb
+

@@ -236,4 +236,76 @@ __device__ __forceinline__ void pair_accumulate2(float2 dx, float2 dy, float2 dz
     uz = fma2(Cx, fz, fma2(g, dz, fma2(s, fma2(gw, R3, kz), uz)));
 }
 
+// Both directions of one unordered pair at once (M_ji = M_ij^T): forward
+// u_i += M_ij f_j into (ux, uy, uz) and reverse v_j = M_ij^T f_i into
+// (rx, ry, rz) (overwritten).  The transpose reuses every coefficient; only
+// the roles of f3 and f4 swap.  Packed over two targets i as in
+// pair_accumulate2; fi* are the targets' forces.
+template <bool WALL>
+__device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float2 dxy2, float2 zt,
+                                          float2 zj, float2 fx, float2 fy, float2 fz, float2 fix,
+                                          float2 fiy, float2 fiz, const PairConsts2 &k, float2 &ux,
+                                          float2 &uy, float2 &uz, float2 &rx, float2 &ry,
+                                          float2 &rz)
+{
+    const float2 r2 = fma2(dz, dz, dxy2);
+    const float2 inv = rsqrt2(r2);
+    const float2 inv2 = mul2(inv, inv);
+    float2 C = mul2(inv, fma2(k.c2, inv2, k.c1));
+    float2 D = mul2(mul2(inv, inv2), fma2(k.c4, inv2, k.c3));
+    if (__any_sync(0xffffffffu, (r2.x < k.four_a2) | (r2.y < k.four_a2))) {
+        if (r2.x < k.four_a2) { C.x = 1.f - k.k1 * (r2.x * inv.x); D.x = k.k2 * inv.x; }
+        if (r2.y < k.four_a2) { C.y = 1.f - k.k1 * (r2.y * inv.y); D.y = k.k2 * inv.y; }
+    }
+    const float2 rf_xy = fma2(dx, fx, mul2(dy, fy));
+    const float2 g = mul2(D, fma2(dz, fz, rf_xy));
+    const float2 rb_xy = fma2(dx, fix, mul2(dy, fiy));
+    const float2 gb = mul2(D, fma2(dz, fiz, rb_xy));
+    if (!WALL) {
+        ux = fma2(C, fx, fma2(g, dx, ux));
+        uy = fma2(C, fy, fma2(g, dy, uy));
+        uz = fma2(C, fz, fma2(g, dz, uz));
+        rx = fma2(C, fix, mul2(gb, dx));
+        ry = fma2(C, fiy, mul2(gb, dy));
+        rz = fma2(C, fiz, mul2(gb, dz));
+        return;
+    }
+    const float2 R3 = add2(zt, zj);
+    const float2 invR = rsqrt2(fma2(R3, R3, dxy2));
+    const float2 hs = mul2(zj, invR);
+    const float2 ht = mul2(zt, invR);
+    const float2 e3 = add2(hs, ht);
+    const float2 E = mul2(e3, e3);
+    const float2 t2 = mul2(k.a2, mul2(invR, invR));
+    const float2 t4 = mul2(t2, t2);
+    const float2 p = mul2(hs, ht);
+    const float2 T1 = mul2(E, t2);
+    const float2 T2 = mul2(E, t4);
+    const float2 f1 = fma2(k.m10o3, T2, fma2(k.p2o3, t4, fma2(k.m2o3, t2, fma2(k.p2, T1, fma2(k.m2, p, k.m1)))));
+    const float2 f2 = fma2(k.m10o3, t4, fma2(k.p70o3, T2, fma2(k.p2, t2, fma2(k.m10, T1, fma2(k.p6, p, k.m1)))));
+    const float2 in3 = fma2(k.m12, p, fma2(k.m140o3, T2, fma2(k.p40o3, t4, fma2(k.m4, t2, mul2(k.p20, T1)))));
+    const float2 f3 = fma2(k.p2, hs, mul2(e3, in3));
+    const float2 f4 = fma2(k.p2, hs, mul2(k.m20o3, mul2(e3, t4)));
+    const float2 f5 = fma2(k.m8o3, t4, fma2(k.p20, T2, fma2(k.m4, T1, mul2(k.m4, mul2(hs, hs)))));
+    const float2 s = mul2(k.sw, invR);
+    const float2 Cx = fma2(s, f1, C);
+    // forward: M_ij f_j
+    const float2 eF = mul2(fma2(R3, fz, rf_xy), invR);
+    const float2 gw = mul2(fma2(f2, eF, mul2(f3, fz)), invR);
+    const float2 kz = fma2(f4, eF, mul2(f5, fz));
+    const float2 Gx = fma2(s, gw, g);
+    ux = fma2(Cx, fx, fma2(Gx, dx, ux));
+    uy = fma2(Cx, fy, fma2(Gx, dy, uy));
+    uz = fma2(Cx, fz, fma2(g, dz, fma2(s, fma2(gw, R3, kz), uz)));
+    // reverse: M_ij^T f_i (f3 and f4 exchange roles)
+    const float2 eB = mul2(fma2(R3, fiz, rb_xy), invR);
+    const float2 gwb = mul2(fma2(f2, eB, mul2(f4, fiz)), invR);
+    const float2 kzb = fma2(f3, eB, mul2(f5, fiz));
+    const float2 Gb = fma2(s, gwb, gb);
+    rx = fma2(Cx, fix, mul2(Gb, dx));
+    ry = fma2(Cx, fiy, mul2(Gb, dy));
+    rz = fma2(Cx, fiz, fma2(gb, dz, mul2(s, fma2(gwb, R3, kzb))));
+}
+
 }  // namespace mb
+

@@ -69,11 +69,12 @@ def test_matvec_full_size_sampled(ctx, full_size_case, prec):
     assert np.abs(got[rows] - ref).max() <= TOL[prec] * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("n", [7, 513, 1537, 4100, 9000])
 def test_matvec_fp32_variants_elementwise(ctx, variant, n):
     """Every FP32 kernel variant (scalar; packed with 2 or 4 targets per
-    thread) against the oracle, on sizes that leave ragged target blocks."""
+    thread; symmetric over block pairs) against the oracle, on sizes that
+    leave ragged blocks (513 = one full block pair plus a single blob)."""
     r, f = I.blob_cloud(300 + n, n, 0.5, 3.0 * max(1.0, n ** 0.5 / 3), 0.5, 1.5)
     ref = O.matvec(r, f, 0.5, 1.0, True)
     ctx.set_pair_variant(variant)
@@ -90,10 +91,23 @@ def test_autotuner_picks_a_variant_and_keeps_it(ctx):
     assert ctx.pair_variant(20000, True) in (-1, 0, 1, 2)
     u1 = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
     v = ctx.pair_variant(20000, True)
-    assert v in (0, 1, 2)
+    assert v in (0, 1, 2, 3)
     u2 = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
-    np.testing.assert_array_equal(u1, u2)
+    # the symmetric variant adds partial sums with FP64 atomics: equal to FP64 rounding
+    np.testing.assert_allclose(u1, u2, rtol=1e-13, atol=1e-15 * np.abs(u1).max())
     assert ctx.pair_variant(20000, True) == v
+
+
+def test_symmetric_variant_full_size_sampled(ctx, full_size_case):
+    """The symmetric kernel on the 65,536-blob workload against the oracle."""
+    r, f, a, rows, ref = full_size_case
+    ctx.set_pair_variant(3)
+    try:
+        got = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
+    finally:
+        ctx.set_pair_variant(-1)
+    assert rel_l2(got[rows], ref) <= TOL["fp32"]
+    assert np.abs(got[rows] - ref).max() <= TOL["fp32"] * np.abs(ref).max()
 
 
 def test_matvec_translation_parallel_to_wall(ctx):
@@ -113,7 +127,7 @@ def test_matvec_host_pointers_match_device(ctx):
     rh = torch.from_numpy(r).pin_memory()
     fh = torch.from_numpy(f).pin_memory()
     uh = ctx.mobility_matvec(rh, fh, 0.5, 1.0, True, "fp32").numpy()
-    np.testing.assert_array_equal(uh, ud)
+    np.testing.assert_allclose(uh, ud, rtol=1e-13, atol=1e-15 * np.abs(ud).max())
 
 
 def test_matvec_empty_and_errors(ctx):
