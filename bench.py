@@ -50,7 +50,8 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 KERNEL_NAMES = {0: "pair_f32_kernel<wall> (scalar, 1 target/thread)",
                 1: "pair_f32x2_kernel<wall,1> (packed f32x2, 2 targets/thread)",
-                2: "pair_f32x2_kernel<wall,2> (packed f32x2, 4 targets/thread)"}
+                2: "pair_f32x2_kernel<wall,2> (packed f32x2, 4 targets/thread)",
+                3: "pair_sym_kernel<wall> (symmetric packed f32x2, each pair once for both blobs)"}
 WORKLOAD = "wall-RPY mobility matvec, N=65536 blobs, a=0.5, xy~U[0,400]^2, z~U[a,3a], f~N(0,1)"
 METRIC = "blob-pair interactions/s"
 UNIT = "pairs/s"
@@ -76,6 +77,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=30.0)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--pool", type=int, default=40)
+    p.add_argument("--pair-variant", type=int, default=-1,
+                   help="FP32 pair-kernel variant (-1 autotune; 0..3 pin one, e.g. for profiling)")
     return p.parse_args()
 
 
@@ -231,6 +234,8 @@ def run_ours(args):
     from paper_1602_02170_gb300 import inputs as I
 
     ctx = mb.Context(local)
+    if args.pair_variant >= 0:
+        ctx.set_pair_variant(args.pair_variant)
     r_np, f_np, a = I.config_matvec_cloud(1 + rank, n=args.n)
     n = args.n
     r = torch.from_numpy(r_np).to(device)

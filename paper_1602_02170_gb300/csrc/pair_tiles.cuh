@@ -210,12 +210,16 @@ __device__ __forceinline__ void df_item(float4 *__restrict__ sD, const float4 *_
 
 // Symmetric packed item over block pair (I, J), I <= J, blocks of 2*NT blobs
 // (two targets per thread, as in x2_item with NP = 1).  Each unordered pair
-// is evaluated once: forward contributions accumulate in the thread's
-// registers (tile sums folded Kahan-style), reverse contributions to the
-// sources are warp-reduced per source, summed over the CTA's warps in
-// shared memory in a fixed order, and added to u with FP64 atomics.
-// Diagonal items (I == J) run forward only over all ordered pairs.
-// u must be zeroed beforehand and receives scale * M f.
+// is evaluated once.  Forward contributions accumulate in the thread's
+// registers (tile sums folded Kahan-style).  Reverse contributions use a
+// rotating schedule inside each group of 32 staged sources: at step t lane l
+// pairs its targets with source (l + t) mod 32, adds the reverse term into a
+// packed accumulator, and passes that accumulator to lane l - 1; after 32
+// steps lane l holds source l's sum over the warp's 64 targets (no per-source
+// reduction).  The warps' sums are added in a fixed order in shared memory
+// and then to u with FP64 atomics.  Diagonal items (I == J) run forward only
+// over all ordered pairs.  u must be zeroed beforehand and receives
+// scale * M f.
 template <bool WALL, int NT>
 __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__restrict__ sRev,
                                            const float4 *__restrict__ hi,
@@ -265,38 +269,48 @@ __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__res
         }
         __syncthreads();
         float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+        if (diag) {
 #pragma unroll 2
-        for (int s = 0; s < NT; ++s) {
-            const float4 *P = sP + kX2SmemFloat4PerSource * s;
-            const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
-            const float2 dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
-            const float2 dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
-            const float2 dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
-            const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
-            const float2 zj = make_float2(P1.z, P1.w);
-            const float2 fx = make_float2(P3.z, P3.w), fy = make_float2(P4.x, P4.y),
-                         fz = make_float2(P4.z, P4.w);
-            if (diag) {
-                pair_accumulate2<WALL>(dx, dy, dz, dxy2, zh, zj, fx, fy, fz, k, ax, ay, az);
-            } else {
-                float2 rx, ry, rz;
-                pair_sym2<WALL>(dx, dy, dz, dxy2, zh, zj, fx, fy, fz, fix, fiy, fiz, k, ax, ay, az,
-                                rx, ry, rz);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    rx.x += __shfl_xor_sync(0xffffffffu, rx.x, o);
-                    rx.y += __shfl_xor_sync(0xffffffffu, rx.y, o);
-                    ry.x += __shfl_xor_sync(0xffffffffu, ry.x, o);
-                    ry.y += __shfl_xor_sync(0xffffffffu, ry.y, o);
-                    rz.x += __shfl_xor_sync(0xffffffffu, rz.x, o);
-                    rz.y += __shfl_xor_sync(0xffffffffu, rz.y, o);
+            for (int s = 0; s < NT; ++s) {
+                const float4 *P = sP + kX2SmemFloat4PerSource * s;
+                const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
+                const float2 dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
+                const float2 dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
+                const float2 dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
+                const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
+                pair_accumulate2<WALL>(dx, dy, dz, dxy2, zh, make_float2(P1.z, P1.w),
+                                       make_float2(P3.z, P3.w), make_float2(P4.x, P4.y),
+                                       make_float2(P4.z, P4.w), k, ax, ay, az);
+            }
+        } else {
+            for (int g = 0; g < NT / 32; ++g) {
+                float2 rx = make_float2(0.f, 0.f), ry = rx, rz = rx;
+#pragma unroll 2
+                for (int t = 0; t < 32; ++t) {
+                    const int s = g * 32 + ((lane + t) & 31);
+                    const float4 *P = sP + kX2SmemFloat4PerSource * s;
+                    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
+                    const float2 dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
+                    const float2 dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
+                    const float2 dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
+                    const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
+                    pair_sym2<WALL>(dx, dy, dz, dxy2, zh, make_float2(P1.z, P1.w),
+                                    make_float2(P3.z, P3.w), make_float2(P4.x, P4.y),
+                                    make_float2(P4.z, P4.w), fix, fiy, fiz, k, ax, ay, az, rx, ry,
+                                    rz);
+                    // hand the accumulator to lane - 1, which meets this source next step
+                    const int from = (lane + 1) & 31;
+                    rx.x = __shfl_sync(0xffffffffu, rx.x, from);
+                    rx.y = __shfl_sync(0xffffffffu, rx.y, from);
+                    ry.x = __shfl_sync(0xffffffffu, ry.x, from);
+                    ry.y = __shfl_sync(0xffffffffu, ry.y, from);
+                    rz.x = __shfl_sync(0xffffffffu, rz.x, from);
+                    rz.y = __shfl_sync(0xffffffffu, rz.y, from);
                 }
-                if (lane == 0) {
-                    float *o3 = sRev + 3 * (warp * NT + s);
-                    o3[0] = rx.x + rx.y;
-                    o3[1] = ry.x + ry.y;
-                    o3[2] = rz.x + rz.y;
-                }
+                float *o3 = sRev + 3 * (warp * NT + g * 32 + lane);
+                o3[0] = rx.x + rx.y;
+                o3[1] = ry.x + ry.y;
+                o3[2] = rz.x + rz.y;
             }
         }
         kahan_add(sum[0][0], comp[0][0], ax.x);
@@ -330,4 +344,3 @@ __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__res
 }
 
 }  // namespace mb
-

@@ -237,8 +237,8 @@ __device__ __forceinline__ void pair_accumulate2(float2 dx, float2 dy, float2 dz
 }
 
 // Both directions of one unordered pair at once (M_ji = M_ij^T): forward
-// u_i += M_ij f_j into (ux, uy, uz) and reverse v_j = M_ij^T f_i into
-// (rx, ry, rz) (overwritten).  The transpose reuses every coefficient; only
+// u_i += M_ij f_j into (ux, uy, uz) and reverse v_j += M_ij^T f_i into
+// (rx, ry, rz).  The transpose reuses every coefficient; only
 // the roles of f3 and f4 swap.  Packed over two targets i as in
 // pair_accumulate2; fi* are the targets' forces.
 template <bool WALL>
@@ -265,9 +265,9 @@ __device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float
         ux = fma2(C, fx, fma2(g, dx, ux));
         uy = fma2(C, fy, fma2(g, dy, uy));
         uz = fma2(C, fz, fma2(g, dz, uz));
-        rx = fma2(C, fix, mul2(gb, dx));
-        ry = fma2(C, fiy, mul2(gb, dy));
-        rz = fma2(C, fiz, mul2(gb, dz));
+        rx = fma2(C, fix, fma2(gb, dx, rx));
+        ry = fma2(C, fiy, fma2(gb, dy, ry));
+        rz = fma2(C, fiz, fma2(gb, dz, rz));
         return;
     }
     const float2 R3 = add2(zt, zj);
@@ -302,9 +302,9 @@ __device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float
     const float2 gwb = mul2(fma2(f2, eB, mul2(f4, fiz)), invR);
     const float2 kzb = fma2(f3, eB, mul2(f5, fiz));
     const float2 Gb = fma2(s, gwb, gb);
-    rx = fma2(Cx, fix, mul2(Gb, dx));
-    ry = fma2(Cx, fiy, mul2(Gb, dy));
-    rz = fma2(Cx, fiz, fma2(gb, dz, mul2(s, fma2(gwb, R3, kzb))));
+    rx = fma2(Cx, fix, fma2(Gb, dx, rx));
+    ry = fma2(Cx, fiy, fma2(Gb, dy, ry));
+    rz = fma2(Cx, fiz, fma2(gb, dz, fma2(s, fma2(gwb, R3, kzb), rz)));
 }
 
 }  // namespace mb
