@@ -159,7 +159,9 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
  *       for both blobs (M_ji = M_ij^T), partial sums added to u with FP64
  *       atomics, so results may differ between calls in the last FP64 bits.
  * All variants compute the same product to FP32 rounding.  Other values are
- * MB_EINVAL.  Setting a variant clears the autotuner's cache.
+ * MB_EINVAL.  Setting a variant clears the autotuner's cache.  Batched
+ * solves and servers created on the context use the pinned variant for
+ * their FP32 pair launches too (variant 0 runs as 1 there).
  */
 mb_status mb_context_set_pair_variant(mb_context *ctx, int variant);
 
@@ -301,7 +303,8 @@ typedef struct {
  * very different sizes share the GPU; each problem keeps its own GMRES
  * state and stops consuming pair-kernel work once converged.  The first
  * FP32 matvec times the packed kernel with 2 and 4 targets per thread and
- * keeps the faster (autotuned tile shape).  The arena is sized exactly for
+ * the symmetric kernel (each unordered pair once for both blobs) and keeps
+ * the fastest (autotuned tile shape).  The arena is sized exactly for
  * the batch.
  *
  * problems: host array of n_problems descriptors (pointing to device data);

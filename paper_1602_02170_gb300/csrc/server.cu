@@ -260,6 +260,45 @@ __global__ void __launch_bounds__(kNT, NP == 1 ? 3 : 2) eng_x2_kernel(
     }
 }
 
+// Symmetric packed pair kernel over every listed request's block-pair
+// triangle (blocks of 2*kNT blobs); item -> request -> (I, J); results are
+// added to y with FP64 atomics (y zeroed beforehand).  n_tblocks holds the
+// request's block count.
+template <bool WALL>
+__global__ void __launch_bounds__(kNT, 2) eng_sym_kernel(
+    const Work *__restrict__ W, const int64_t *__restrict__ item_off, int nw, int64_t n_items,
+    const int *__restrict__ mask, PairConsts2 k, double scale)
+{
+    __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
+    __shared__ float sRev[3 * kNT * (kNT / 32)];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const Work P = W[find_owner(item_off, nw, item)];
+        if (!mask[P.slot]) continue;
+        const int64_t local = item - P.item_off;
+        const int64_t nb = P.n_tblocks;
+        int64_t lo_r = 0, hi_r = nb;
+        while (hi_r - lo_r > 1) {
+            const int64_t mid = (lo_r + hi_r) >> 1;
+            if (mid * nb - mid * (mid - 1) / 2 <= local) lo_r = mid;
+            else hi_r = mid;
+        }
+        const int64_t I = lo_r, J = I + (local - (I * nb - I * (I - 1) / 2));
+        x2sym_item<WALL, kNT>(sP, sRev, P.hi, P.lo, P.f, P.n, I, J, k, P.y, scale);
+    }
+}
+
+// y = 0 on the listed rows (RSeg work index -> that entry's y)
+__global__ void eng_zero_kernel(const Work *__restrict__ W, const RSeg *__restrict__ rs, int nrs,
+                                const int *__restrict__ mask)
+{
+    for (int it = blockIdx.x; it < nrs; it += gridDim.x) {
+        const RSeg R = rs[it];
+        const Work P = W[R.work];
+        if (!mask[P.slot]) continue;
+        for (int64_t e = R.start + threadIdx.x; e < R.end; e += blockDim.x) P.y[e] = 0.0;
+    }
+}
+
 template <bool WALL>
 __global__ void __launch_bounds__(kNT) eng_df_kernel(const Work *__restrict__ W,
                                                      const int64_t *__restrict__ item_off, int nw,
@@ -719,7 +758,8 @@ struct Engine {
     int *hstate = nullptr;  // pinned mirror of per-slot ints (8 arrays)
     RangeAlloc blobs, bodies, pcs, starts;
     std::vector<int> free_slots;
-    int np_variant = 1;     // packed-kernel targets per thread / 2 (autotuned)
+    int np_variant = 1;     // FP32 tile shape: 1, 2 = packed with 2 or 4 targets per
+                            // thread, 3 = symmetric (autotuned)
     bool tuned = false;
 
     struct Req {
@@ -904,9 +944,12 @@ struct Engine {
         if (list.empty()) return MB_OK;
         const double scale = 1.0 / (6.0 * kPi * prm.eta * prm.a);
         const bool x2 = prec == MB_FP32_KAHAN;
-        const int tpc = x2 ? 2 * np_variant * kNT : kNT;
+        const bool sym = x2 && np_variant == 3;
+        const int tpc = x2 ? 2 * (sym ? 1 : np_variant) * kNT : kNT;
         int occ = 1;
-        if (prec == MB_FP32_KAHAN)
+        if (sym)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_sym_kernel<true>, kNT, 0);
+        else if (prec == MB_FP32_KAHAN)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_x2_kernel<true, 1>, kNT, 0);
         else if (prec == MB_DF64)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_df_kernel<true>, kNT, 0);
@@ -930,13 +973,24 @@ struct Engine {
             wk.r = r + 3 * rq->blob_off;
             wk.f = f_base + fk[li] * ld + 3 * rq->blob_off;
             wk.y = y_base + yk[li] * ld + 3 * rq->blob_off;
+            wk.slot = rq->slot;
+            wk.item_off = items;
+            ioff.push_back(items);
+            if (sym) {
+                const int64_t nb = ceil_div(wk.n, tpc);
+                wk.n_tblocks = (int)nb;
+                wk.S = 1;
+                wk.chunk = wk.n;
+                items += nb * (nb + 1) / 2;
+                for (int64_t a = 0; a < 3 * wk.n; a += kSeg)
+                    rs.push_back(RSeg{a, std::min<int64_t>(3 * wk.n, a + kSeg), (int)li, 0});
+                W.push_back(wk);
+                continue;
+            }
             wk.n_tblocks = (int)ceil_div(wk.n, tpc);
             int S = (int)std::max<int64_t>(1, ceil_div(wk.n, chunk));
             wk.chunk = ceil_div(ceil_div(wk.n, S), kNT) * kNT;
             wk.S = (int)ceil_div(wk.n, wk.chunk);
-            wk.slot = rq->slot;
-            wk.item_off = items;
-            ioff.push_back(items);
             items += (int64_t)wk.n_tblocks * wk.S;
             if (wk.S > 1) {
                 wk.part = (double *)0 + part;  // offset, fixed up below
@@ -959,7 +1013,13 @@ struct Engine {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, res));
         const bool wall = prm.wall != 0;
         auto *ev = profile_begin(ctx, s);
-        if (prec == MB_FP32_KAHAN) {
+        if (sym) {
+            eng_zero_kernel<<<grid_for((int64_t)rs.size(), 1), 256, 0, s>>>(dW, dR, (int)rs.size(), mask);
+            count_launch();
+            const PairConsts2 k = PairConsts2::make(prm.a);
+            if (wall) eng_sym_kernel<true><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
+            else eng_sym_kernel<false><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
+        } else if (prec == MB_FP32_KAHAN) {
             const PairConsts2 k = PairConsts2::make(prm.a);
             if (np_variant == 1) {
                 if (wall) eng_x2_kernel<true, 1><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
@@ -979,7 +1039,7 @@ struct Engine {
         }
         profile_end(ev, s);
         count_launch();
-        if (!rs.empty()) {
+        if (!rs.empty() && !sym) {
             eng_reduce_kernel<<<grid_for((int64_t)rs.size(), 1), 256, 0, s>>>(dW, dR, (int)rs.size(),
                                                                            mask, scale);
             count_launch();
@@ -1159,7 +1219,12 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         *n_queued = (int)queue.size();
         return MB_OK;
     }
-    // autotune the packed tile shape on the first inner FP32 matvec
+    // tile shape: the context's pinned pair variant if any (the scalar
+    // variant maps to packed x2), else autotuned on the first inner FP32 matvec
+    if (!tuned && inner == MB_FP32_KAHAN && ctx->pair_variant >= 0) {
+        np_variant = std::max(1, ctx->pair_variant);
+        tuned = true;
+    }
     if (!tuned && inner == MB_FP32_KAHAN) {
         float best = 1e30f;
         int best_v = 1;
@@ -1169,7 +1234,7 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         std::vector<int64_t> zk(arn.size(), 0);
         std::vector<int> ones(s_cap, 0);
         for (int sl : arn) ones[sl] = 1;
-        for (int cand = 1; cand <= 2; ++cand) {
+        for (int cand = 1; cand <= 3; ++cand) {
             np_variant = cand;
             size_t off2 = 0;
             int *dm = upload(ones, off2, s, &stt);

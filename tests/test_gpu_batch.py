@@ -49,6 +49,24 @@ def test_batch_matches_alone_and_oracle(ctx):
             assert rel_l2(host(lam), lr) <= 1e-5, k
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_batch_each_tile_shape(ctx, variant):
+    """The engine's FP32 tile shapes (packed with 2 or 4 targets per thread,
+    symmetric over block pairs) give the same answer; problems of 20-40
+    bodies span several 512-blob blocks."""
+    susp = [I.mixed_suspension(600 + k, nb) for k, nb in enumerate([20, 33, 7, 40])]
+    ctx.set_pair_variant(variant)
+    try:
+        res = ctx.solve_batch([_prob(s) for s in susp], A, tol=1e-10, prec="mixed")
+    finally:
+        ctx.set_pair_variant(-1)
+    for s, (U, W, lam, info) in zip(susp, res):
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
+        assert info["converged"] == 1
+        assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
+
+
 def test_batch_result_independent_of_companions(ctx):
     """The same problem solved in two different batches gives the same answer."""
     susp = _suspensions()
