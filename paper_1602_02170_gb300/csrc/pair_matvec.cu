@@ -187,20 +187,25 @@ __global__ void __launch_bounds__(kNT) pair_f64_kernel(
     }
 }
 
+// Double-float kernel: symmetric over the upper-triangular pairs of blocks
+// of kNT blobs (one target per thread); see dfsym_item.
 template <bool WALL>
 __global__ void __launch_bounds__(kNT) pair_df_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
-    int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts<dfl> k,
-    double *__restrict__ out, double scale, int direct)
+    int64_t n, int64_t nb, int64_t n_items, PairConsts<dfl> k, double *__restrict__ u,
+    double scale)
 {
     __shared__ float4 sD[3 * kNT];
+    __shared__ double sRev[3 * kNT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int tb = (int)(item % n_tblocks);
-        const int64_t sc = item / n_tblocks;
-        const int64_t j_begin = sc * chunk;
-        const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        df_item<WALL, kNT>(sD, hi, lo, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
-                           direct ? scale : 1.0);
+        int64_t lo_r = 0, hi_r = nb;
+        while (hi_r - lo_r > 1) {
+            const int64_t mid = (lo_r + hi_r) >> 1;
+            if (mid * nb - mid * (mid - 1) / 2 <= item) lo_r = mid;
+            else hi_r = mid;
+        }
+        const int64_t I = lo_r, J = I + (item - (I * nb - I * (I - 1) / 2));
+        dfsym_item<WALL, kNT>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
     }
 }
 
@@ -415,13 +420,31 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
 {
     const double scale = 1.0 / (6.0 * kPi * eta * a);
     if (prec == MB_FP32_KAHAN) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
-    const bool df = prec == MB_DF64;
+    if (prec == MB_DF64) {
+        // symmetric double-float kernel: zero u, one launch over the block-pair triangle
+        const int res = wall ? resident_ctas(ctx, pair_df_kernel<true>)
+                             : resident_ctas(ctx, pair_df_kernel<false>);
+        const int64_t nb = ceil_div(n, kNT);
+        const int64_t items = nb * (nb + 1) / 2;
+        const int grid = (int)std::min<int64_t>(items, res);
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        auto *ev = profile_begin(ctx, s);
+        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+        const PairConsts<dfl> k = PairConsts<dfl>::make(a);
+        if (wall)
+            pair_df_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        else
+            pair_df_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        profile_end(ev, s);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    }
     Plan p;
     {
-        const int res = df ? (wall ? resident_ctas(ctx, pair_df_kernel<true>)
-                                   : resident_ctas(ctx, pair_df_kernel<false>))
-                           : (wall ? resident_ctas(ctx, pair_f64_kernel<true>)
-                                   : resident_ctas(ctx, pair_f64_kernel<false>));
+        const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
+                             : resident_ctas(ctx, pair_f64_kernel<false>);
         p = make_plan(n, kNT, res);
     }
     double *out = u;
@@ -431,25 +454,13 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         out = (double *)ctx->partial.ptr;
     }
     auto *ev = profile_begin(ctx, s);
-    if (df) {
-        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
-        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
-        const PairConsts<dfl> k = PairConsts<dfl>::make(a);
-        if (wall)
-            pair_df_kernel<true><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks, p.items,
-                                                        k, out, scale, direct);
-        else
-            pair_df_kernel<false><<<p.grid, kNT, 0, s>>>(hi, lo, f, n, p.chunk, p.n_tblocks,
-                                                         p.items, k, out, scale, direct);
-    } else {
-        const PairConsts<double> k = PairConsts<double>::make(a);
-        if (wall)
-            pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
-                                                         out, scale, direct);
-        else
-            pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items,
-                                                          k, out, scale, direct);
-    }
+    const PairConsts<double> k = PairConsts<double>::make(a);
+    if (wall)
+        pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k, out,
+                                                     scale, direct);
+    else
+        pair_f64_kernel<false><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k,
+                                                      out, scale, direct);
     profile_end(ev, s);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());

@@ -160,54 +160,6 @@ __device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *
     }
 }
 
-// Double-float item: one target per thread; the same pair formula as the
-// FP32 and FP64 kernels evaluated in double-float (df32.cuh).  Sources are
-// staged as three float4: (x_hi, x_lo, y_hi, y_lo), (z_hi, z_lo, fx_hi,
-// fx_lo), (fy_hi, fy_lo, fz_hi, fz_lo); positions come from the packed hi/lo
-// arrays, forces are split from FP64 on the fly.
-template <bool WALL, int NT>
-__device__ __forceinline__ void df_item(float4 *__restrict__ sD, const float4 *__restrict__ hi,
-                                        const float4 *__restrict__ lo,
-                                        const double *__restrict__ f, int64_t n, int tb,
-                                        int64_t j_begin, int64_t j_end, const PairConsts<dfl> &k,
-                                        double *__restrict__ out, double m)
-{
-    const int64_t i = (int64_t)tb * NT + threadIdx.x;
-    const int64_t ic = i < n ? i : n - 1;
-    const float4 th = hi[ic], tl = lo[ic];
-    const dfl xi(th.x, tl.x), yi(th.y, tl.y), zi(th.z, tl.z);
-    dfl ux, uy, uz;
-    for (int64_t jt = j_begin; jt < j_end; jt += NT) {
-        __syncthreads();
-        {
-            const int64_t j = jt + threadIdx.x;
-            const bool valid = j < j_end;
-            const int64_t jc = valid ? j : j_begin;
-            const float4 h = hi[jc], l = lo[jc];
-            const dfl fx = valid ? dfl(f[3 * jc]) : dfl();
-            const dfl fy = valid ? dfl(f[3 * jc + 1]) : dfl();
-            const dfl fz = valid ? dfl(f[3 * jc + 2]) : dfl();
-            float4 *d = sD + 3 * threadIdx.x;
-            d[0] = make_float4(h.x, l.x, h.y, l.y);
-            d[1] = make_float4(h.z, l.z, fx.hi, fx.lo);
-            d[2] = make_float4(fy.hi, fy.lo, fz.hi, fz.lo);
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int s = 0; s < NT; ++s) {
-            const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
-            const dfl zj(B.x, B.y);
-            pair_accumulate<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
-                                       dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), k, ux, uy, uz);
-        }
-    }
-    if (i < n) {
-        out[3 * i] = m * to_double(ux);
-        out[3 * i + 1] = m * to_double(uy);
-        out[3 * i + 2] = m * to_double(uz);
-    }
-}
-
 // Symmetric packed item over block pair (I, J), I <= J, blocks of 2*NT blobs
 // (two targets per thread, as in x2_item with NP = 1).  Each unordered pair
 // is evaluated once.  Forward contributions accumulate in the thread's
@@ -343,4 +295,92 @@ __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__res
             atomicAdd(u + 3 * ib + c, scale * ((double)sum[1][c] - (double)comp[1][c]));
 }
 
+// Symmetric double-float item over block pair (I, J), I <= J, blocks of NT
+// blobs, one target per thread; the rotating reverse accumulators of
+// x2sym_item in double-float.  Sources are staged as three float4 (x_hi,
+// x_lo, y_hi, y_lo), (z_hi, z_lo, fx_hi, fx_lo), (fy_hi, fy_lo, fz_hi,
+// fz_lo): a 48-byte stride, so the rotated reads stay conflict-free.
+// sRev holds NT * 3 doubles: each warp adds its per-source sums with shared-
+// memory atomics.  u must be zeroed and receives scale * M f.
+template <bool WALL, int NT>
+__device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__restrict__ sRev,
+                                           const float4 *__restrict__ hi,
+                                           const float4 *__restrict__ lo,
+                                           const double *__restrict__ f, int64_t n, int64_t I,
+                                           int64_t J, const PairConsts<dfl> &k,
+                                           double *__restrict__ u, double scale)
+{
+    const int lane = threadIdx.x & 31;
+    const bool diag = I == J;
+    const int64_t i = I * NT + threadIdx.x;
+    const int64_t ic = i < n ? i : n - 1;
+    const float4 th = hi[ic], tl = lo[ic];
+    const dfl xi(th.x, tl.x), yi(th.y, tl.y), zi(th.z, tl.z);
+    const dfl gx = i < n ? dfl(f[3 * i]) : dfl(), gy = i < n ? dfl(f[3 * i + 1]) : dfl(),
+              gz = i < n ? dfl(f[3 * i + 2]) : dfl();
+    dfl ux, uy, uz;
+    const int64_t j0 = J * NT;
+    __syncthreads();
+    {
+        const int64_t j = j0 + threadIdx.x;
+        const bool valid = j < n;
+        const int64_t jc = valid ? j : j0;
+        const float4 h = hi[jc], l = lo[jc];
+        const dfl fx = valid ? dfl(f[3 * jc]) : dfl();
+        const dfl fy = valid ? dfl(f[3 * jc + 1]) : dfl();
+        const dfl fz = valid ? dfl(f[3 * jc + 2]) : dfl();
+        float4 *d = sD + 3 * threadIdx.x;
+        d[0] = make_float4(h.x, l.x, h.y, l.y);
+        d[1] = make_float4(h.z, l.z, fx.hi, fx.lo);
+        d[2] = make_float4(fy.hi, fy.lo, fz.hi, fz.lo);
+        sRev[3 * threadIdx.x] = sRev[3 * threadIdx.x + 1] = sRev[3 * threadIdx.x + 2] = 0.0;
+    }
+    __syncthreads();
+    if (diag) {
+#pragma unroll 1
+        for (int s = 0; s < NT; ++s) {
+            const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
+            const dfl zj(B.x, B.y);
+            pair_accumulate<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                                       dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), k, ux, uy, uz);
+        }
+    } else {
+        for (int g = 0; g < NT / 32; ++g) {
+            dfl vx, vy, vz;
+#pragma unroll 1
+            for (int t = 0; t < 32; ++t) {
+                const int s = g * 32 + ((lane + t) & 31);
+                const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
+                const dfl zj(B.x, B.y);
+                pair_sym<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                                    dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), gx, gy, gz, k, ux,
+                                    uy, uz, vx, vy, vz);
+                const int from = (lane + 1) & 31;
+                vx.hi = __shfl_sync(0xffffffffu, vx.hi, from);
+                vx.lo = __shfl_sync(0xffffffffu, vx.lo, from);
+                vy.hi = __shfl_sync(0xffffffffu, vy.hi, from);
+                vy.lo = __shfl_sync(0xffffffffu, vy.lo, from);
+                vz.hi = __shfl_sync(0xffffffffu, vz.hi, from);
+                vz.lo = __shfl_sync(0xffffffffu, vz.lo, from);
+            }
+            double *o3 = sRev + 3 * (g * 32 + lane);
+            atomicAdd(o3, to_double(vx));
+            atomicAdd(o3 + 1, to_double(vy));
+            atomicAdd(o3 + 2, to_double(vz));
+        }
+        __syncthreads();
+        const int64_t j = j0 + threadIdx.x;
+        if (j < n) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(u + 3 * j + c, scale * sRev[3 * threadIdx.x + c]);
+        }
+    }
+    if (i < n) {
+        atomicAdd(u + 3 * i, scale * to_double(ux));
+        atomicAdd(u + 3 * i + 1, scale * to_double(uy));
+        atomicAdd(u + 3 * i + 2, scale * to_double(uz));
+    }
+}
+
 }  // namespace mb
+

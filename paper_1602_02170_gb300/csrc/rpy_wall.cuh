@@ -115,6 +115,69 @@ __device__ __forceinline__ void pair_accumulate(T dx, T dy, T dz, T zi, T zj, T 
     uz += Cx * fz + g * dz + s * (gw * R3 + kz);
 }
 
+// Both directions of one unordered pair (scalar types: FP64, double-float):
+// u_i += M_ij f_j and v_j += M_ij^T f_i (f3 and f4 exchange roles in the
+// transpose).
+template <bool WALL, typename T>
+__device__ __forceinline__ void pair_sym(T dx, T dy, T dz, T zi, T zj, T fx, T fy, T fz, T gx,
+                                         T gy, T gz, const PairConsts<T> &k, T &ux, T &uy, T &uz,
+                                         T &vx, T &vy, T &vz)
+{
+    const T dxy2 = dx * dx + dy * dy;
+    const T r2 = mb_max(dz * dz + dxy2, k.tiny);
+    const T inv = mb_rsqrt(r2);
+    const T inv2 = inv * inv;
+    T C = inv * (k.c1 + k.c2 * inv2);
+    T D = inv * inv2 * (k.c3 + k.c4 * inv2);
+    if (r2 < k.four_a2) {
+        C = T(1) - k.k1 * (r2 * inv);
+        D = k.k2 * inv;
+    }
+    const T rf_xy = dx * fx + dy * fy;
+    const T g = D * (rf_xy + dz * fz);
+    const T rb_xy = dx * gx + dy * gy;
+    const T gb = D * (rb_xy + dz * gz);
+    if (!WALL) {
+        ux += C * fx + g * dx;
+        uy += C * fy + g * dy;
+        uz += C * fz + g * dz;
+        vx += C * gx + gb * dx;
+        vy += C * gy + gb * dy;
+        vz += C * gz + gb * dz;
+        return;
+    }
+    const T R3 = zi + zj;
+    const T invR = mb_rsqrt(R3 * R3 + dxy2);
+    const T hs = zj * invR;
+    const T ht = zi * invR;
+    const T e3 = hs + ht;
+    const T E = e3 * e3;
+    const T t2 = k.a2 * (invR * invR);
+    const T t4 = t2 * t2;
+    const T p = hs * ht;
+    const T f1 = T(-1) - T(2) * p + t2 * (T(2) * E - T(2.0 / 3.0)) + t4 * (T(2.0 / 3.0) - T(10.0 / 3.0) * E);
+    const T f2 = T(-1) + T(6) * p + t2 * (T(2) - T(10) * E) + t4 * (T(70.0 / 3.0) * E - T(10.0 / 3.0));
+    const T f3 = T(2) * hs + e3 * (t2 * (T(20) * E - T(4)) + t4 * (T(40.0 / 3.0) - T(140.0 / 3.0) * E) - T(12) * p);
+    const T f4 = T(2) * hs - T(20.0 / 3.0) * e3 * t4;
+    const T f5 = T(-4) * hs * hs - T(4) * E * t2 + t4 * (T(20) * E - T(8.0 / 3.0));
+    const T s = k.sw * invR;
+    const T Cx = C + s * f1;
+    const T eF = (rf_xy + R3 * fz) * invR;
+    const T gw = (f2 * eF + f3 * fz) * invR;
+    const T kz = f4 * eF + f5 * fz;
+    const T Gx = g + s * gw;
+    ux += Cx * fx + Gx * dx;
+    uy += Cx * fy + Gx * dy;
+    uz += Cx * fz + g * dz + s * (gw * R3 + kz);
+    const T eB = (rb_xy + R3 * gz) * invR;
+    const T gwb = (f2 * eB + f4 * gz) * invR;
+    const T kzb = f3 * eB + f5 * gz;
+    const T Gb = gb + s * gwb;
+    vx += Cx * gx + Gb * dx;
+    vy += Cx * gy + Gb * dy;
+    vz += Cx * gz + gb * dz + s * (gwb * R3 + kzb);
+}
+
 // Full 3x3 block M_ij in FP64, units of (6 pi eta a)^-1, row-major
 // m[3*alpha + beta] (alpha = velocity component of i, beta = force
 // component of j).  Used to assemble the per-body blocks of the

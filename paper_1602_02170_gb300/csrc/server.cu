@@ -299,6 +299,9 @@ __global__ void eng_zero_kernel(const Work *__restrict__ W, const RSeg *__restri
     }
 }
 
+// Symmetric double-float kernel over every listed request's block-pair
+// triangle (blocks of kNT blobs); y zeroed beforehand; n_tblocks holds the
+// request's block count.
 template <bool WALL>
 __global__ void __launch_bounds__(kNT) eng_df_kernel(const Work *__restrict__ W,
                                                      const int64_t *__restrict__ item_off, int nw,
@@ -306,15 +309,20 @@ __global__ void __launch_bounds__(kNT) eng_df_kernel(const Work *__restrict__ W,
                                                      PairConsts<dfl> k, double scale)
 {
     __shared__ float4 sD[3 * kNT];
+    __shared__ double sRev[3 * kNT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const Work P = W[find_owner(item_off, nw, item)];
         if (!mask[P.slot]) continue;
         const int64_t local = item - P.item_off;
-        const int tb = (int)(local % P.n_tblocks);
-        const int64_t sc = local / P.n_tblocks;
-        const int64_t j0 = sc * P.chunk, j1 = j0 + P.chunk < P.n ? j0 + P.chunk : P.n;
-        df_item<WALL, kNT>(sD, P.hi, P.lo, P.f, P.n, tb, j0, j1, k,
-                           P.S == 1 ? P.y : P.part + 3 * sc * P.n, P.S == 1 ? scale : 1.0);
+        const int64_t nb = P.n_tblocks;
+        int64_t lo_r = 0, hi_r = nb;
+        while (hi_r - lo_r > 1) {
+            const int64_t mid = (lo_r + hi_r) >> 1;
+            if (mid * nb - mid * (mid - 1) / 2 <= local) lo_r = mid;
+            else hi_r = mid;
+        }
+        const int64_t I = lo_r, J = I + (local - (I * nb - I * (I - 1) / 2));
+        dfsym_item<WALL, kNT>(sD, sRev, P.hi, P.lo, P.f, P.n, I, J, k, P.y, scale);
     }
 }
 
@@ -944,10 +952,13 @@ struct Engine {
         if (list.empty()) return MB_OK;
         const double scale = 1.0 / (6.0 * kPi * prm.eta * prm.a);
         const bool x2 = prec == MB_FP32_KAHAN;
-        const bool sym = x2 && np_variant == 3;
-        const int tpc = x2 ? 2 * (sym ? 1 : np_variant) * kNT : kNT;
+        const bool dfs = prec == MB_DF64;          // symmetric double-float
+        const bool sym = (x2 && np_variant == 3) || dfs;
+        const int tpc = x2 ? 2 * (np_variant == 3 ? 1 : np_variant) * kNT : kNT;
         int occ = 1;
-        if (sym)
+        if (dfs)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_df_kernel<true>, kNT, 0);
+        else if (sym)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_sym_kernel<true>, kNT, 0);
         else if (prec == MB_FP32_KAHAN)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_x2_kernel<true, 1>, kNT, 0);
@@ -1016,6 +1027,12 @@ struct Engine {
         if (sym) {
             eng_zero_kernel<<<grid_for((int64_t)rs.size(), 1), 256, 0, s>>>(dW, dR, (int)rs.size(), mask);
             count_launch();
+        }
+        if (dfs) {
+            const PairConsts<dfl> k = PairConsts<dfl>::make(prm.a);
+            if (wall) eng_df_kernel<true><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
+            else eng_df_kernel<false><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
+        } else if (sym) {
             const PairConsts2 k = PairConsts2::make(prm.a);
             if (wall) eng_sym_kernel<true><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
             else eng_sym_kernel<false><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
@@ -1028,10 +1045,6 @@ struct Engine {
                 if (wall) eng_x2_kernel<true, 2><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
                 else eng_x2_kernel<false, 2><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
             }
-        } else if (prec == MB_DF64) {
-            const PairConsts<dfl> k = PairConsts<dfl>::make(prm.a);
-            if (wall) eng_df_kernel<true><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
-            else eng_df_kernel<false><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
         } else {
             const PairConsts<double> k = PairConsts<double>::make(prm.a);
             if (wall) eng_f64_kernel<true><<<grid, kNT, 0, s>>>(dW, dI, nw, items, mask, k, scale);
