@@ -51,7 +51,8 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 KERNEL_NAMES = {0: "pair_f32_kernel<wall> (scalar, 1 target/thread)",
                 1: "pair_f32x2_kernel<wall,1> (packed f32x2, 2 targets/thread)",
                 2: "pair_f32x2_kernel<wall,2> (packed f32x2, 4 targets/thread)",
-                3: "pair_sym_kernel<wall> (symmetric packed f32x2, each pair once for both blobs)"}
+                3: "pair_sym_kernel<wall> (symmetric packed f32x2, each pair once for both blobs)",
+                4: "pair_f32x2_kernel<wall,1,32> (packed f32x2, 32-thread CTAs, small problems)"}
 WORKLOAD = "wall-RPY mobility matvec, N=65536 blobs, a=0.5, xy~U[0,400]^2, z~U[a,3a], f~N(0,1)"
 METRIC = "blob-pair interactions/s"
 UNIT = "pairs/s"

@@ -157,11 +157,14 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
  *    2  packed FP32 kernel, four targets per thread;
  *    3  symmetric packed FP32 kernel: each unordered pair evaluated once
  *       for both blobs (M_ji = M_ij^T), partial sums added to u with FP64
- *       atomics, so results may differ between calls in the last FP64 bits.
+ *       atomics, so results may differ between calls in the last FP64 bits;
+ *    4  packed FP32 kernel in 32-thread CTAs (64 targets, source chunks of
+ *       32 or more), which spreads small problems over many SMs; the
+ *       autotuner's choice below 4,096 blobs.
  * All variants compute the same product to FP32 rounding.  Other values are
  * MB_EINVAL.  Setting a variant clears the autotuner's cache.  Batched
  * solves and servers created on the context use the pinned variant for
- * their FP32 pair launches too (variant 0 runs as 1 there).
+ * their FP32 pair launches too (variant 0 runs as 1 there, 4 as 3).
  */
 mb_status mb_context_set_pair_variant(mb_context *ctx, int variant);
 

@@ -273,7 +273,8 @@ class Context:
         return int(self.L.mb_context_workspace_bytes(self.handle))
 
     def set_pair_variant(self, variant: int):
-        """-1 autotune (default), 0 scalar, 1 packed x2, 2 packed x4, 3 symmetric."""
+        """-1 autotune (default), 0 scalar, 1 packed x2, 2 packed x4, 3 symmetric,
+        4 packed in 32-thread CTAs (small problems)."""
         self._check(self.L.mb_context_set_pair_variant(self.handle, int(variant)))
 
     def pair_variant(self, n: int, wall: bool = True) -> int:

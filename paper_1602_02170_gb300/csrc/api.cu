@@ -196,7 +196,7 @@ size_t mb_context_workspace_bytes(const mb_context *ctx) { return ctx ? ctx->hel
 mb_status mb_context_set_pair_variant(mb_context *ctx, int variant)
 {
     MB_TRY(check_ctx(ctx));
-    if (variant < -1 || variant > 3) return set_err(ctx, MB_EINVAL, "pair variant must be -1..3");
+    if (variant < -1 || variant > 4) return set_err(ctx, MB_EINVAL, "pair variant must be -1..4");
     ctx->pair_variant = variant;
     ctx->tuned.clear();
     return MB_OK;

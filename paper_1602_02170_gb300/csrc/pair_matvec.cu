@@ -130,20 +130,20 @@ __global__ void __launch_bounds__(kNT) pair_f32_kernel(
 
 // Packed FP32 kernel (paired f32x2 arithmetic, 2*NP targets per thread): a
 // persistent loop over (target block, source chunk) items; see x2_item.
-template <bool WALL, int NP>
-__global__ void __launch_bounds__(kNT, NP == 1 ? 3 : 2) pair_f32x2_kernel(
+template <bool WALL, int NP, int NT = kNT>
+__global__ void __launch_bounds__(NT, NT == kNT ? (NP == 1 ? 3 : 2) : 16) pair_f32x2_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
     int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts2 k,
     double *__restrict__ out, double scale, int direct)
 {
-    __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
+    __shared__ float4 sP[kX2SmemFloat4PerSource * NT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int tb = (int)(item % n_tblocks);
         const int64_t sc = item / n_tblocks;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        x2_item<WALL, NP, kNT>(sP, hi, lo, f, n, tb, j_begin, j_end, k,
-                               direct ? out : out + 3 * sc * n, direct ? scale : 1.0);
+        x2_item<WALL, NP, NT>(sP, hi, lo, f, n, tb, j_begin, j_end, k,
+                              direct ? out : out + 3 * sc * n, direct ? scale : 1.0);
     }
 }
 
@@ -170,33 +170,33 @@ __global__ void __launch_bounds__(kNT, 2) pair_sym_kernel(
     }
 }
 
-template <bool WALL>
-__global__ void __launch_bounds__(kNT) pair_f64_kernel(
+template <bool WALL, int NT = kNT>
+__global__ void __launch_bounds__(NT) pair_f64_kernel(
     const double *__restrict__ r, const double *__restrict__ f, int64_t n, int64_t chunk,
     int n_tblocks, int64_t n_items, PairConsts<double> k, double *__restrict__ out, double scale,
     int direct)
 {
-    __shared__ double sm[6 * kNT];
+    __shared__ double sm[6 * NT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int tb = (int)(item % n_tblocks);
         const int64_t sc = item / n_tblocks;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        f64_item<WALL, kNT>(sm, r, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
-                            direct ? scale : 1.0);
+        f64_item<WALL, NT>(sm, r, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
+                           direct ? scale : 1.0);
     }
 }
 
 // Double-float kernel: symmetric over the upper-triangular pairs of blocks
 // of kNT blobs (one target per thread); see dfsym_item.
-template <bool WALL>
-__global__ void __launch_bounds__(kNT) pair_df_kernel(
+template <bool WALL, int NT = kNT>
+__global__ void __launch_bounds__(NT) pair_df_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
     int64_t n, int64_t nb, int64_t n_items, PairConsts<dfl> k, double *__restrict__ u,
     double scale)
 {
-    __shared__ float4 sD[3 * kNT];
-    __shared__ double sRev[3 * kNT];
+    __shared__ float4 sD[3 * NT];
+    __shared__ double sRev[3 * NT];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         int64_t lo_r = 0, hi_r = nb;
         while (hi_r - lo_r > 1) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kNT) pair_df_kernel(
             else hi_r = mid;
         }
         const int64_t I = lo_r, J = I + (item - (I * nb - I * (I - 1) / 2));
-        dfsym_item<WALL, kNT>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
+        dfsym_item<WALL, NT>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
     }
 }
 
@@ -232,14 +232,15 @@ struct Plan {
 
 // Split sources into S chunks so that the items fill whole waves of the
 // resident grid as evenly as possible, with chunks of at least two tiles.
-Plan make_plan(int64_t n, int targets_per_cta, int resident, int64_t s_cap = 64)
+Plan make_plan(int64_t n, int targets_per_cta, int resident, int64_t s_cap = 64, int tile = kNT,
+               int64_t min_chunk = 2 * kNT)
 {
     Plan p;
     p.n_tblocks = (int)ceil_div(n, targets_per_cta);
-    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(s_cap, ceil_div(n, 2 * kNT)));
+    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(s_cap, ceil_div(n, min_chunk)));
     double best = -1.0;
     for (int64_t s = 1; s <= max_s; ++s) {
-        const int64_t chunk = ceil_div(ceil_div(n, s), kNT) * kNT;
+        const int64_t chunk = ceil_div(ceil_div(n, s), tile) * tile;
         const int64_t s_eff = ceil_div(n, chunk);
         const int64_t items = (int64_t)p.n_tblocks * s_eff;
         const int64_t waves = ceil_div(items, resident);
@@ -259,10 +260,10 @@ Plan make_plan(int64_t n, int targets_per_cta, int resident, int64_t s_cap = 64)
 }
 
 template <typename K>
-int resident_ctas(mb_context *ctx, K kernel)
+int resident_ctas(mb_context *ctx, K kernel, int threads = kNT)
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kNT, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess ||
         occ < 1)
         occ = 1;
     return occ * ctx->sm_count;
@@ -277,9 +278,14 @@ constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 //   0: scalar kernel, kTPT targets per thread
 //   1: packed f32x2 kernel, 2 targets per thread
 //   2: packed f32x2 kernel, 4 targets per thread
-constexpr int kF32Variants = 4;
+constexpr int kF32Variants = 5;
+constexpr int kSmallNT = 32;        // CTA size of the small-problem kernels
+constexpr int64_t kSmallN = 8192;   // below this the FP64 and double-float paths use them
 
-int f32_targets_per_cta(int v) { return v == 0 ? kNT * kTPT : (v == 2 ? 4 * kNT : 2 * kNT); }
+int f32_targets_per_cta(int v)
+{
+    return v == 0 ? kNT * kTPT : (v == 2 ? 4 * kNT : (v == 4 ? 2 * kSmallNT : 2 * kNT));
+}
 
 template <bool WALL>
 int f32_resident(mb_context *ctx, int v)
@@ -287,6 +293,7 @@ int f32_resident(mb_context *ctx, int v)
     if (v == 0) return resident_ctas(ctx, pair_f32_kernel<WALL, kTPT>);
     if (v == 1) return resident_ctas(ctx, pair_f32x2_kernel<WALL, 1>);
     if (v == 3) return resident_ctas(ctx, pair_sym_kernel<WALL>);
+    if (v == 4) return resident_ctas(ctx, pair_f32x2_kernel<WALL, 1, kSmallNT>, kSmallNT);
     return resident_ctas(ctx, pair_f32x2_kernel<WALL, 2>);
 }
 
@@ -301,6 +308,9 @@ void f32_launch(int v, const Plan &p, cudaStream_t s, const float4 *hi, const fl
     } else if (v == 1) {
         pair_f32x2_kernel<WALL, 1><<<p.grid, kNT, 0, s>>>(
             hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts2::make(a), out, scale, direct);
+    } else if (v == 4) {
+        pair_f32x2_kernel<WALL, 1, kSmallNT><<<p.grid, kSmallNT, 0, s>>>(
+            hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts2::make(a), out, scale, direct);
     } else {
         pair_f32x2_kernel<WALL, 2><<<p.grid, kNT, 0, s>>>(
             hi, lo, f, n, p.chunk, p.n_tblocks, p.items, PairConsts2::make(a), out, scale, direct);
@@ -312,6 +322,33 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
                   double scale, double *u, cudaStream_t s, bool profile)
 {
     const int res = wall ? f32_resident<true>(ctx, v) : f32_resident<false>(ctx, v);
+    if (v == 4) {
+        // small problems: 64-target blocks, source chunks of 32 or more, many CTAs
+        const Plan p = make_plan(n, f32_targets_per_cta(4), res, 1024, kSmallNT, kSmallNT);
+        double *out = u;
+        const int direct = p.S == 1;
+        if (!direct) {
+            MB_TRY(ensure(ctx, ctx->partial, sizeof(double) * 3 * (size_t)n * p.S, "matvec partials"));
+            out = (double *)ctx->partial.ptr;
+        }
+        auto *ev = profile ? profile_begin(ctx, s) : nullptr;
+        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
+        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
+        if (wall)
+            f32_launch<true>(4, p, s, hi, lo, f, n, a, out, scale, direct);
+        else
+            f32_launch<false>(4, p, s, hi, lo, f, n, a, out, scale, direct);
+        profile_end(ev, s);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        if (!direct) {
+            const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
+            reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);
+            count_launch();
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+        }
+        return MB_OK;
+    }
     if (v == 3) {
         // symmetric: zero u, then one launch over the block-pair triangle
         const int64_t nb = ceil_div(n, 2 * kNT);
@@ -376,7 +413,7 @@ mb_status matvec_f32(mb_context *ctx, const double *f, int64_t n, double a, int 
         if (it != ctx->tuned.end()) {
             v = it->second;
         } else if (n < 4096) {
-            v = 1;  // launch-bound: any variant is as fast
+            v = 4;  // small: spread over many SMs in 64-target, 32-source items
             ctx->tuned[key] = v;
         } else {
             // time each variant once on this stream (each run is a full, valid matvec)
@@ -421,10 +458,15 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
     const double scale = 1.0 / (6.0 * kPi * eta * a);
     if (prec == MB_FP32_KAHAN) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
     if (prec == MB_DF64) {
-        // symmetric double-float kernel: zero u, one launch over the block-pair triangle
-        const int res = wall ? resident_ctas(ctx, pair_df_kernel<true>)
-                             : resident_ctas(ctx, pair_df_kernel<false>);
-        const int64_t nb = ceil_div(n, kNT);
+        // symmetric double-float kernel: zero u, one launch over the block-pair
+        // triangle (32-blob blocks for small problems, so that they spread)
+        const bool small = n < kSmallN;
+        const int nt = small ? kSmallNT : kNT;
+        const int res = small ? (wall ? resident_ctas(ctx, pair_df_kernel<true, kSmallNT>, kSmallNT)
+                                      : resident_ctas(ctx, pair_df_kernel<false, kSmallNT>, kSmallNT))
+                              : (wall ? resident_ctas(ctx, pair_df_kernel<true>)
+                                      : resident_ctas(ctx, pair_df_kernel<false>));
+        const int64_t nb = ceil_div(n, nt);
         const int64_t items = nb * (nb + 1) / 2;
         const int grid = (int)std::min<int64_t>(items, res);
         MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
@@ -432,7 +474,11 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
         const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
         const PairConsts<dfl> k = PairConsts<dfl>::make(a);
-        if (wall)
+        if (small && wall)
+            pair_df_kernel<true, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        else if (small)
+            pair_df_kernel<false, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+        else if (wall)
             pair_df_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
         else
             pair_df_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
@@ -441,8 +487,13 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
     }
+    const bool small = n < kSmallN;
     Plan p;
-    {
+    if (small) {
+        const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true, kSmallNT>, kSmallNT)
+                             : resident_ctas(ctx, pair_f64_kernel<false, kSmallNT>, kSmallNT);
+        p = make_plan(n, kSmallNT, res, 1024, kSmallNT, kSmallNT);
+    } else {
         const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
                              : resident_ctas(ctx, pair_f64_kernel<false>);
         p = make_plan(n, kNT, res);
@@ -455,7 +506,13 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
     }
     auto *ev = profile_begin(ctx, s);
     const PairConsts<double> k = PairConsts<double>::make(a);
-    if (wall)
+    if (small && wall)
+        pair_f64_kernel<true, kSmallNT><<<p.grid, kSmallNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks,
+                                                                   p.items, k, out, scale, direct);
+    else if (small)
+        pair_f64_kernel<false, kSmallNT><<<p.grid, kSmallNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks,
+                                                                    p.items, k, out, scale, direct);
+    else if (wall)
         pair_f64_kernel<true><<<p.grid, kNT, 0, s>>>(r, f, n, p.chunk, p.n_tblocks, p.items, k, out,
                                                      scale, direct);
     else

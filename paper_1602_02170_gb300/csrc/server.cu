@@ -1235,7 +1235,7 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
     // tile shape: the context's pinned pair variant if any (the scalar
     // variant maps to packed x2), else autotuned on the first inner FP32 matvec
     if (!tuned && inner == MB_FP32_KAHAN && ctx->pair_variant >= 0) {
-        np_variant = std::max(1, ctx->pair_variant);
+        np_variant = std::min(3, std::max(1, ctx->pair_variant));
         tuned = true;
     }
     if (!tuned && inner == MB_FP32_KAHAN) {
