@@ -182,6 +182,7 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->stage_u, &ctx->pinv, &ctx->pinv_off, &ctx->blob_start_copy,
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
+                      &ctx->sol_dx, &ctx->sol_ym,
                       &ctx->batch_ws};
     for (DevBuf *b : bufs) release(ctx, *b);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);

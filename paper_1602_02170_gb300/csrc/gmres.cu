@@ -8,10 +8,20 @@
 // device.  The preconditioned vectors z_j are kept (flexible variant), so the
 // update x += Z y is exact even when P^-1 or the inner matvec are inexact.
 // Every restart recomputes the true residual b - A x; with MB_MIXED_REFINE
-// the Arnoldi matvecs use the FP32 pair kernel and the restart residual the
-// FP64 one, which turns restarts into iterative refinement (the inexact-
-// Krylov remark of Section 2.2.1).  Termination is on the true residual,
-// as right preconditioning allows (Section 3, preconditioner discussion).
+// the Arnoldi matvecs use the FP32 pair kernel and the restart residual a
+// higher-precision one, which turns restarts into iterative refinement (the
+// inexact-Krylov remark of Section 2.2.1).  Termination is on the true
+// residual, as right preconditioning allows (Section 3, preconditioner
+// discussion).
+//
+// Mixed precision keeps M lambda as an FP64 running sum y_M: each cycle's
+// correction dx = Z y adds M dlambda to it, and A x = [y_M - K U; -K^T lambda]
+// is rebuilt from y_M with the exact K / K^T kernels.  The correction of a
+// cycle that started from a residual beta is about beta in size, so the FP32
+// pair kernel's error on it (below ~1e-5 relative) is ~1e-5 beta: once
+// beta <= kFineRel * tol * |b| that is under a tenth of the target and the
+// increment runs in FP32; larger corrections (always the first one, which is
+// the whole solution) run in double-float.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -24,6 +34,11 @@ namespace {
 
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
+// mixed precision: FP32 increments of y_M once the cycle's starting residual
+// is below kFineRel * tol * |b| (see the header)
+constexpr double kFineRel = 1e4;
+
+int vec_grid(int64_t L) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 2048)); }
 
 // partial[k * nblk + b] = sum over block b's slice of V[k] . w, for k < nk
 __global__ void multidot_kernel(const double *__restrict__ V, int64_t ld, int nk,
@@ -92,6 +107,31 @@ __global__ void sub_kernel(const double *__restrict__ a, const double *__restric
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
          e += (int64_t)gridDim.x * blockDim.x)
         z[e] = a[e] - b[e];
+}
+
+// dx = sum_k Z[k] y[k]; x += dx
+__global__ void update_span_kernel(const double *__restrict__ Z, int64_t ld, int nk,
+                                   const double *__restrict__ y, double *__restrict__ x,
+                                   double *__restrict__ dx, int64_t L)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < nk; ++k) acc += Z[(int64_t)k * ld + e] * y[k];
+        dx[e] = acc;
+        x[e] += acc;
+    }
+}
+
+// y_M += t; t = y_M (first n3 entries)
+__global__ void accumulate_kernel(double *__restrict__ t, double *__restrict__ ym, int64_t n3)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n3;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = ym[e] + t[e];
+        ym[e] = v;
+        t[e] = v;
+    }
 }
 
 // x += sum_k Z[k] y[k]
@@ -211,8 +251,6 @@ __global__ void unpack_solution_kernel(int64_t n, int64_t nb, const double *__re
     }
 }
 
-int vec_grid(int64_t L) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 2048)); }
-
 struct Solver {
     mb_context *ctx;
     cudaStream_t s;
@@ -230,6 +268,19 @@ struct Solver {
     mb_status apply_A(const double *xin, double *y, mb_precision prec)
     {
         MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s));
+        launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
+        launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    }
+
+    // y = A x from the running sum y_M += M dx_lambda (pair kernel in `prec`)
+    mb_status apply_A_incremental(const double *xin, const double *dx, double *ym, double *y,
+                                  mb_precision prec)
+    {
+        MB_TRY(matvec_packed(ctx, r, dx, n, a, eta, wall, prec, y, s));
+        accumulate_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, ym, 3 * n);
+        count_launch();
         launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
         launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
         MB_CUDA_TRY(ctx, cudaGetLastError());
@@ -277,6 +328,11 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     MB_TRY(ensure(ctx, ctx->sol_x, sizeof(double) * L, "iterate"));
     MB_TRY(ensure(ctx, ctx->sol_w, sizeof(double) * L, "work vector"));
     MB_TRY(ensure(ctx, ctx->sol_t, sizeof(double) * L, "work vector"));
+    const bool mixed = p->prec == MB_MIXED_REFINE;
+    if (mixed) {
+        MB_TRY(ensure(ctx, ctx->sol_dx, sizeof(double) * L, "cycle correction"));
+        MB_TRY(ensure(ctx, ctx->sol_ym, sizeof(double) * 3 * n, "running M lambda"));
+    }
     MB_TRY(ensure(ctx, ctx->sol_small, sizeof(double) * (sl.total() + (m + 1) * kRedBlocks),
                   "Krylov scalars"));
     if (!ctx->host_small) MB_CUDA_TRY(ctx, cudaMallocHost(&ctx->host_small, 64));
@@ -305,6 +361,9 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     build_rhs_kernel<<<vg, 256, 0, s>>>(n, nb, slip, F, T, S.b);
     count_launch();
     MB_CUDA_TRY(ctx, cudaMemsetAsync(S.x, 0, sizeof(double) * L, s));
+    double *dx = mixed ? (double *)ctx->sol_dx.ptr : nullptr;
+    double *ym = mixed ? (double *)ctx->sol_ym.ptr : nullptr;
+    if (mixed) MB_CUDA_TRY(ctx, cudaMemsetAsync(ym, 0, sizeof(double) * 3 * n, s));
     S.dots(S.b, 1, S.b, S.sm + sl.nrm2(), 0);
     MB_CUDA_TRY(ctx, cudaGetLastError());
     double bnorm2 = 0.0;
@@ -325,7 +384,13 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                 MB_CUDA_TRY(ctx, cudaMemcpyAsync(S.w, S.b, sizeof(double) * L,
                                                  cudaMemcpyDeviceToDevice, s));
             } else {
-                MB_TRY(S.apply_A(S.x, S.t, outer));
+                if (mixed) {
+                    // rel still holds the residual this cycle started from
+                    const bool fine = rel <= kFineRel * p->tol;
+                    MB_TRY(S.apply_A_incremental(S.x, dx, ym, S.t, fine ? inner : outer));
+                } else {
+                    MB_TRY(S.apply_A(S.x, S.t, outer));
+                }
                 sub_kernel<<<vg, 256, 0, s>>>(S.b, S.t, S.w, L);
                 count_launch();
             }
@@ -378,7 +443,10 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
             }
             solve_triangle_kernel<<<1, 1, 0, s>>>(S.sm, sl, k);
             count_launch();
-            add_span_kernel<<<vg, 256, 0, s>>>(S.Z, L, k, S.sm + sl.y(), S.x, L);
+            if (mixed)
+                update_span_kernel<<<vg, 256, 0, s>>>(S.Z, L, k, S.sm + sl.y(), S.x, dx, L);
+            else
+                add_span_kernel<<<vg, 256, 0, s>>>(S.Z, L, k, S.sm + sl.y(), S.x, L);
             count_launch();
             MB_CUDA_TRY(ctx, cudaGetLastError());
             ++restarts;

@@ -48,6 +48,7 @@ struct mb_context {
     mb::DevBuf sol_r;            // blob positions
     mb::DevBuf sol_V, sol_Z;     // Krylov bases (restart+1 and restart vectors)
     mb::DevBuf sol_b, sol_x, sol_w, sol_t; // rhs, iterate, scratch vectors
+    mb::DevBuf sol_dx, sol_ym;   // mixed precision: cycle correction, running M lambda
     mb::DevBuf sol_small;        // Hessenberg, Givens, dots (doubles)
     mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
     mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)

@@ -11,7 +11,11 @@
 //      ranges freed) and admits queued ones (blob build, preconditioner setup
 //      of Section 2.2.2, right-hand side);
 //   2. computes the true residual b - A x for every request starting a
-//      restart cycle (one batched matvec in the outer precision);
+//      restart cycle (one batched matvec in the outer precision; in mixed
+//      precision a batched product of the last cycle's correction, added to
+//      each request's FP64 running sum of M lambda, in FP32 once the
+//      correction is small enough for its error to stay under a tenth of the
+//      tolerance, as in the single-problem solver);
 //   3. runs one Arnoldi step of right-preconditioned flexible GMRES for every
 //      active request, whatever its step index: one batched preconditioner
 //      apply, one batched pair-kernel launch over all requests' (target
@@ -103,7 +107,12 @@ struct SlotState {    // per-slot device integers
     int *restarts;    // completed cycles
     int *park;        // cycle ended this tick
     int *bad;         // set at admission: 1 malformed descriptor, 2 singular block
+    int *fine;        // mixed: the running cycle's correction may be multiplied in FP32
 };
+
+constexpr int kSlotInts = 9;  // int arrays in SlotState
+// mixed precision: FP32 increments once a cycle starts below kFineRel * tol * |b|
+constexpr double kFineRel = 1e4;
 
 __device__ __forceinline__ int find_owner(const int64_t *__restrict__ off, int n, int64_t item)
 {
@@ -221,17 +230,18 @@ __global__ void eng_pack_kernel(const double *__restrict__ r, int64_t b_lo, int6
     }
 }
 
-// b = [slip ; -(F, T)] and x = 0 on the segments of admitted slots
+// b = [slip ; -(F, T)], x = 0 and y_M = 0 on the segments of admitted slots
 __global__ void eng_rhs_kernel(const Seg *__restrict__ segs, int nseg, int64_t n_cap,
                                const double *__restrict__ slip, const double *__restrict__ F,
                                const double *__restrict__ T, double *__restrict__ b,
-                               double *__restrict__ x)
+                               double *__restrict__ x, double *__restrict__ ym)
 {
     for (int it = blockIdx.x; it < nseg; it += gridDim.x) {
         const Seg sg = segs[it];
         for (int64_t e = sg.start + threadIdx.x; e < sg.end; e += blockDim.x) {
             if (e < 3 * n_cap) {
                 b[e] = slip[e];
+                ym[e] = 0.0;
             } else {
                 const int64_t k = e - 3 * n_cap, p = k / 6, c = k % 6;
                 b[e] = c < 3 ? -F[3 * p + c] : -T[3 * p + c - 3];
@@ -578,11 +588,13 @@ __global__ void eng_residual_kernel(const double *__restrict__ b, const double *
     }
 }
 
-// x += sum_{k < kstep_s} Z_k y_s[k] for slots that ended their cycle
+// dx = sum_{k < kstep_s} Z_k y_s[k] and x += dx for slots that ended their
+// cycle (dx may be null: x only)
 __global__ void eng_update_kernel(const double *__restrict__ Z, int64_t ld,
                                   const double *__restrict__ sm, int64_t stride, int64_t y_off,
                                   const int *__restrict__ jidx, const Seg *__restrict__ segs,
-                                  int nseg, const int *__restrict__ park, double *__restrict__ x)
+                                  int nseg, const int *__restrict__ park, double *__restrict__ x,
+                                  double *__restrict__ dx)
 {
     for (int it = blockIdx.x; it < nseg; it += gridDim.x) {
         const Seg sg = segs[it];
@@ -591,9 +603,26 @@ __global__ void eng_update_kernel(const double *__restrict__ Z, int64_t ld,
         const int nk = jidx[s];
         const double *y = sm + (int64_t)s * stride + y_off;
         for (int64_t e = sg.start + threadIdx.x; e < sg.end; e += blockDim.x) {
-            double acc = x[e];
+            double acc = 0.0;
             for (int k = 0; k < nk; ++k) acc += Z[(int64_t)k * ld + e] * y[k];
-            x[e] = acc;
+            x[e] += acc;
+            if (dx) dx[e] = acc;
+        }
+    }
+}
+
+// y_M += t and t = y_M on the blob segments of masked slots
+__global__ void eng_accumulate_kernel(double *__restrict__ t, double *__restrict__ ym,
+                                      const Seg *__restrict__ segs, int nseg,
+                                      const int *__restrict__ mask)
+{
+    for (int it = blockIdx.x; it < nseg; it += gridDim.x) {
+        const Seg sg = segs[it];
+        if (!mask[sg.slot]) continue;
+        for (int64_t e = sg.start + threadIdx.x; e < sg.end; e += blockDim.x) {
+            const double v = ym[e] + t[e];
+            ym[e] = v;
+            t[e] = v;
         }
     }
 }
@@ -614,6 +643,7 @@ __global__ void eng_init_kernel(const int *__restrict__ list, int nlist, double 
         st.iters[s] = 0;
         st.restarts[s] = 0;
         st.park[s] = 0;
+        st.fine[s] = 0;
         q[L.rel()] = 0.0;
     }
 }
@@ -632,6 +662,7 @@ __global__ void eng_cycle_start_kernel(const int *__restrict__ list, int nlist, 
         const double beta = sqrt(q[L.nrm2()]);
         const double rel = beta / q[L.bnorm()];
         q[L.rel()] = rel;
+        st.fine[s] = mixed && rel <= kFineRel * tol;
         if (rel <= tol) {
             st.conv[s] = 1;
             st.live[s] = 0;
@@ -761,11 +792,13 @@ struct Engine {
     int64_t *bstart, *body_b0, *body_b1, *blob_body, *poff;
     int *blob_slot, *body_slot;
     double *V, *Z, *b, *x, *w, *t, *sm, *dpart;
+    double *dx = nullptr, *ym = nullptr;  // mixed: cycle correction, running M lambda
     SlotState st{};
     int *flag = nullptr;
-    int *hstate = nullptr;  // pinned mirror of per-slot ints (8 arrays)
+    int *hstate = nullptr;  // pinned mirror of per-slot ints (kSlotInts arrays)
     RangeAlloc blobs, bodies, pcs, starts;
     std::vector<int> free_slots;
+    bool mixed = false;
     int np_variant = 1;     // FP32 tile shape: 1, 2 = packed with 2 or 4 targets per
                             // thread, 3 = symmetric (autotuned)
     bool tuned = false;
@@ -813,6 +846,7 @@ struct Engine {
         s_cap = max_requests;
         start_cap = max_bodies + max_requests;
         ld = 3 * n_cap + 6 * b_cap;
+        mixed = p->prec == MB_MIXED_REFINE;
         size_t need = 0;
         auto add = [&](size_t bytes) { need += ((bytes + 255) & ~(size_t)255); };
         add(sizeof(double) * 3 * n_cap * 3);                       // rho, r, slip
@@ -822,8 +856,9 @@ struct Engine {
         add(sizeof(int64_t) * (start_cap + 3 * b_cap + n_cap));    // bstart, b0, b1, poff, blob_body
         add(sizeof(int) * (n_cap + b_cap));                        // slots of blobs/bodies
         add(sizeof(double) * ld * (2 * m + 1 + 4));                // V, Z, b, x, w, t
+        if (mixed) add(sizeof(double) * (ld + 3 * n_cap));         // dx, y_M
         add(sizeof(double) * L.total() * s_cap);                   // per-slot scalars
-        add(sizeof(int) * 8 * s_cap + 64);                         // slot state, flag
+        add(sizeof(int) * kSlotInts * s_cap + 64);                 // slot state, flag
         MB_TRY(ensure(ctx, arena, need + 4096, "server arena"));
         char *base = (char *)arena.ptr;
         size_t off = 0;
@@ -856,16 +891,20 @@ struct Engine {
         x = (double *)take(sizeof(double) * ld);
         w = (double *)take(sizeof(double) * ld);
         t = (double *)take(sizeof(double) * ld);
+        if (mixed) {
+            dx = (double *)take(sizeof(double) * ld);
+            ym = (double *)take(sizeof(double) * 3 * n_cap);
+        }
         sm = (double *)take(sizeof(double) * L.total() * s_cap);
-        int *ints = (int *)take(sizeof(int) * 8 * s_cap);
+        int *ints = (int *)take(sizeof(int) * kSlotInts * s_cap);
         flag = (int *)take(sizeof(int) * 16);
-        st = SlotState{ints, ints + s_cap, ints + 2 * s_cap, ints + 3 * s_cap,
-                       ints + 4 * s_cap, ints + 5 * s_cap, ints + 6 * s_cap, ints + 7 * s_cap};
+        st = SlotState{ints, ints + s_cap, ints + 2 * s_cap, ints + 3 * s_cap, ints + 4 * s_cap,
+                       ints + 5 * s_cap, ints + 6 * s_cap, ints + 7 * s_cap, ints + 8 * s_cap};
         MB_CUDA_TRY(ctx, cudaMemset(blob_slot, 0xff, sizeof(int) * n_cap));
         MB_CUDA_TRY(ctx, cudaMemset(body_slot, 0xff, sizeof(int) * b_cap));
         MB_CUDA_TRY(ctx, cudaMemset(blob_body, 0xff, sizeof(int64_t) * n_cap));
-        MB_CUDA_TRY(ctx, cudaMemset(ints, 0, sizeof(int) * 8 * s_cap));
-        MB_CUDA_TRY(ctx, cudaMallocHost(&hstate, sizeof(int) * 8 * s_cap + 64));
+        MB_CUDA_TRY(ctx, cudaMemset(ints, 0, sizeof(int) * kSlotInts * s_cap));
+        MB_CUDA_TRY(ctx, cudaMallocHost(&hstate, sizeof(int) * kSlotInts * s_cap + 64));
         blobs.init(n_cap);
         bodies.init(b_cap);
         pcs.init(pc_cap);
@@ -1105,7 +1144,6 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
     const bool wall = prm.wall != 0;
     const mb_precision inner = inner_precision(prm.prec);
     const mb_precision outer = outer_precision(prm.prec);
-    const int mixed = prm.prec == MB_MIXED_REFINE;
 
     // ---- 1. admission (first come, first served while ranges fit)
     std::vector<Req *> admitted;
@@ -1186,7 +1224,7 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         Seg *dS = upload(segs, toff, s, &stt);
         MB_TRY(stt);
         eng_rhs_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(dS, (int)segs.size(), n_cap,
-                                                                         slip, F, T, b, x);
+                                                                         slip, F, T, b, x, ym ? ym : t);
         count_launch();
         // b.b per admitted slot, then initial state; the admitted slots act
         // as the mask (live is not set yet): use a temporary all-ones mask
@@ -1273,9 +1311,32 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         for (int sl : resid_list) rmask[sl] = 1;
         int *dR = upload(rmask, toff, s, &stt);
         MB_TRY(stt);
-        if (!resid_list.empty()) {
+        if (!resid_list.empty() && mixed) {
+            // t = y_M += M dx, the product in FP32 for slots whose cycle
+            // started small enough (fine), else in the outer precision
+            std::vector<int> lf, lc, mf(s_cap, 0), mc(s_cap, 0);
+            for (int sl : resid_list) {
+                if (hstate[8 * s_cap + sl]) { lf.push_back(sl); mf[sl] = 1; }
+                else { lc.push_back(sl); mc[sl] = 1; }
+            }
+            int *dMf = upload(mf, toff, s, &stt);
+            int *dMc = upload(mc, toff, s, &stt);
+            MB_TRY(stt);
+            std::vector<int64_t> zf(lf.size(), 0), zc(lc.size(), 0);
+            MB_TRY(matvec(lf, dx, zf, t, zf, inner, dMf, s, toff));
+            MB_TRY(matvec(lc, dx, zc, t, zc, outer, dMc, s, toff));
+            std::vector<Seg> bsegs;
+            for (int sl : resid_list) segs_of(running[sl], bsegs, true, false);
+            Seg *dB = upload(bsegs, toff, s, &stt);
+            MB_TRY(stt);
+            eng_accumulate_kernel<<<grid_for((int64_t)bsegs.size(), 1), 256, 0, s>>>(
+                t, ym, dB, (int)bsegs.size(), dR);
+            count_launch();
+        } else if (!resid_list.empty()) {
             std::vector<int64_t> zero(resid_list.size(), 0);
             MB_TRY(matvec(resid_list, x, zero, t, zero, outer, dR, s, toff));
+        }
+        if (!resid_list.empty()) {
             eng_K_kernel<<<grid_for(n_cap, 256), 256, 0, s>>>(blob_body, blob_slot, 0, n_cap, r, q, x,
                                                               nullptr, t, nullptr, ld, n_cap, dR,
                                                               -1.0, 1.0);
@@ -1366,14 +1427,15 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         eng_givens_kernel<<<1, 128, 0, s>>>(dA, (int)arn.size(), sm, L, st, prm.maxit);
         count_launch();
         eng_update_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(
-            Z, ld, sm, L.total(), L.y(), st.j, dS, (int)segs.size(), st.park, x);
+            Z, ld, sm, L.total(), L.y(), st.j, dS, (int)segs.size(), st.park, x, dx);
         count_launch();
         (void)dA;
     }
     MB_CUDA_TRY(ctx, cudaGetLastError());
 
     // ---- 4. read the slot state back; retire finished requests
-    MB_CUDA_TRY(ctx, cudaMemcpyAsync(hstate, st.act, sizeof(int) * 8 * s_cap, cudaMemcpyDeviceToHost, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(hstate, st.act, sizeof(int) * kSlotInts * s_cap,
+                                     cudaMemcpyDeviceToHost, s));
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const int *h_act = hstate, *h_live = hstate + s_cap, *h_park = hstate + 6 * s_cap,
               *h_j = hstate + 3 * s_cap;

@@ -169,6 +169,30 @@ def test_solve_mixed_monolayer_patch(ctx):
     assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
 
 
+@pytest.mark.parametrize("restart", [60, 8])
+def test_mixed_running_product_matches_fresh_residual(ctx, restart):
+    """Mixed precision rebuilds A x from an FP64 running sum of M lambda whose
+    small late increments come from the FP32 kernel.  The residual it reports
+    must agree with a fresh FP64 product of the returned solution; restart = 8
+    forces many short cycles and so many FP32 increments."""
+    s = I.config_monolayer(3, n_bodies=16, box=12.0)
+    d = _dev_susp(s)
+    tol = 1e-8
+    U, W, lam, info = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"],
+                                         d["T"], s.a, 1.0, True, tol=tol, maxit=400,
+                                         restart=restart, prec="mixed")
+    assert info["converged"] == 1
+    r = ctx.blob_positions(d["q"], d["theta"], d["blob_start"], d["rho"])
+    Ml = ctx.mobility_matvec(r, lam, s.a, 1.0, True, "fp64")
+    UO = torch.cat([U, W], 1).contiguous()
+    rb = ctx.K_apply(r, d["q"], d["blob_start"], UO) - Ml
+    rB = ctx.KT_apply(r, d["q"], d["blob_start"], lam) - torch.cat([d["F"], d["T"]], 1)
+    bnorm = float(np.linalg.norm(np.concatenate([s.F, s.T])))
+    fresh = float(torch.sqrt((rb * rb).sum() + (rB * rB).sum()).item()) / bnorm
+    assert fresh <= 1.2 * tol
+    assert abs(fresh - info["rel_residual"]) <= 0.2 * tol
+
+
 def test_solve_fp32_small_suspension(ctx):
     _solve_and_compare(ctx, I.config_small_suspension(2), "fp32", 1e-6, 1e-5)
 
