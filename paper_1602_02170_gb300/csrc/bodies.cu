@@ -106,6 +106,49 @@ __global__ void KT_apply_kernel(int64_t nb, const double *__restrict__ r, const 
     }
 }
 
+// The same sum with one CTA per body, for few bodies (the warp-per-body form
+// would leave most SMs idle and run each body's blobs serially in one warp).
+constexpr int64_t kKTBlockBodies = 256;
+
+__global__ void __launch_bounds__(256) KT_apply_block_kernel(
+    int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
+    const int64_t *__restrict__ start, const double *__restrict__ lam, double *__restrict__ FT,
+    double alpha)
+{
+    __shared__ double red[8][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        for (int64_t i = start[p] + threadIdx.x; i < start[p + 1]; i += blockDim.x) {
+            const double lx = lam[3 * i], ly = lam[3 * i + 1], lz = lam[3 * i + 2];
+            const double dx = r[3 * i] - qx, dy = r[3 * i + 1] - qy, dz = r[3 * i + 2] - qz;
+            acc[0] += lx;
+            acc[1] += ly;
+            acc[2] += lz;
+            acc[3] += dy * lz - dz * ly;
+            acc[4] += dz * lx - dx * lz;
+            acc[5] += dx * ly - dy * lx;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) red[warp][c] = acc[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double v = 0.0;
+            for (int w8 = 0; w8 < 8; ++w8) v += red[w8][threadIdx.x];
+            FT[6 * p + threadIdx.x] = alpha * v;
+        }
+    }
+}
+
 int grid_for(int64_t work, int threads)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), 4096));
@@ -137,7 +180,11 @@ void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t
                      const double *lambda, double *FT, double alpha, cudaStream_t s)
 {
     if (nb == 0) return;
-    KT_apply_kernel<<<grid_for(nb * 32, 256), 256, 0, s>>>(nb, r, q, blob_start, lambda, FT, alpha);
+    if (nb <= kKTBlockBodies)
+        KT_apply_block_kernel<<<(int)nb, 256, 0, s>>>(nb, r, q, blob_start, lambda, FT, alpha);
+    else
+        KT_apply_kernel<<<grid_for(nb * 32, 256), 256, 0, s>>>(nb, r, q, blob_start, lambda, FT,
+                                                               alpha);
     count_launch();
 }
 

@@ -173,7 +173,7 @@ __global__ void cycle_start_kernel(double *__restrict__ sm, Small L)
 
 // Column j of H is h[0..j] with H[j+1, j] = sqrt(nrm2); apply the previous
 // rotations, form the new one and update g.  est = |g[j+1]|.
-__global__ void givens_kernel(double *__restrict__ sm, Small L, int j)
+__device__ void givens_column(double *__restrict__ sm, Small L, int j)
 {
     double col[2];
     for (int i = 0; i <= j; ++i) sm[L.H(i, j)] = sm[L.h() + i];
@@ -198,6 +198,92 @@ __global__ void givens_kernel(double *__restrict__ sm, Small L, int j)
     sm[L.g() + j] = c * gj;
     sm[L.g() + j + 1] = -s * gj;
     sm[L.est()] = fabs(-s * gj);
+}
+
+__global__ void givens_kernel(double *__restrict__ sm, Small L, int j) { givens_column(sm, L, j); }
+
+// One CTA does the whole orthogonalisation of w = V_{j+1} for small systems:
+// both classical Gram-Schmidt passes (h = V^T w, w -= V h), their merged
+// coefficients as column j of H, |w|, the Givens update and w /= |w|.  The
+// same steps as the multi-kernel sequence, without its 9 launches.
+constexpr int kOrthThreads = 1024;
+constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one CTA
+
+__global__ void __launch_bounds__(kOrthThreads) orth_small_kernel(double *__restrict__ V,
+                                                                  int64_t L, int j,
+                                                                  double *__restrict__ sm,
+                                                                  Small S)
+{
+    // shared: hs[m + 1] pass coefficients, hc[m + 2] merged column j of H,
+    // cs[m], sn[m] previous rotations, red[32] partial sums
+    extern __shared__ double hs[];
+    double *hc = hs + S.m + 1;
+    double *cs = hc + S.m + 2;
+    double *sn = cs + S.m;
+    double *red = sn + S.m;
+    double *w = V + (int64_t)(j + 1) * L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        cs[i] = sm[S.cs() + i];
+        sn[i] = sm[S.sn() + i];
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i <= j; i += nw) {
+            const double *v = V + (int64_t)i * L;
+            double acc = 0.0;
+            for (int64_t e = lane; e < L; e += 32) acc += v[e] * w[e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) hs[i] = acc;
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < L; e += blockDim.x) {
+            double acc = w[e];
+            for (int i = 0; i <= j; ++i) acc -= V[(int64_t)i * L + e] * hs[i];
+            w[e] = acc;
+        }
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = pass == 0 ? hs[i] : hc[i] + hs[i];
+        __syncthreads();
+    }
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < L; e += blockDim.x) acc += w[e] * w[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) {
+            // Givens update of column j on the shared copy (as givens_column)
+            hc[j + 1] = sqrt(acc);
+            for (int i = 0; i < j; ++i) {
+                const double a = hc[i], b = hc[i + 1];
+                hc[i] = cs[i] * a + sn[i] * b;
+                hc[i + 1] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = hc[j], b = hc[j + 1];
+            const double rr = hypot(a, b);
+            const double c = rr > 0.0 ? a / rr : 1.0;
+            const double sg = rr > 0.0 ? b / rr : 0.0;
+            hc[j] = rr;
+            hc[j + 1] = 0.0;
+            const double gj = sm[S.g() + j];
+            sm[S.cs() + j] = c;
+            sm[S.sn() + j] = sg;
+            sm[S.g() + j] = c * gj;
+            sm[S.g() + j + 1] = -sg * gj;
+            sm[S.est()] = fabs(-sg * gj);
+            sm[S.nrm2()] = acc;
+            red[0] = acc;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
+    const double d = sqrt(red[0]);
+    const double inv = d > 0.0 ? 1.0 / d : 0.0;
+    for (int64_t e = threadIdx.x; e < L; e += blockDim.x) w[e] *= inv;
 }
 
 // h[i] += y[i] for i <= j: the second CGS pass's coefficients (held in y)
@@ -419,6 +505,18 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                 double *vn = S.V + (int64_t)(j + 1) * L;
                 precond_apply_packed(ctx, vj, zj, s);
                 MB_TRY(S.apply_A(zj, vn, inner));
+                ++iters;
+                k = j + 1;
+                if ((int64_t)(j + 1) * L <= kOrthSmallMax) {
+                    orth_small_kernel<<<1, kOrthThreads, sizeof(double) * (4 * m + 3 + 32), s>>>(
+                        S.V, L, j, S.sm, sl);
+                    count_launch();
+                    MB_CUDA_TRY(ctx, cudaGetLastError());
+                    double est = 0.0;
+                    MB_TRY(S.read_est(&est));
+                    if (!(est > inner_abs)) break;
+                    continue;
+                }
                 // CGS2
                 S.dots(S.V, j + 1, vn, S.sm + sl.h(), 0);
                 subtract_span_kernel<<<vg, 256, 0, s>>>(S.V, L, j + 1, S.sm + sl.h(), vn, L);
@@ -431,8 +529,6 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                 merge_passes_kernel<<<1, 32, 0, s>>>(S.sm, sl, j);
                 count_launch();
                 MB_CUDA_TRY(ctx, cudaGetLastError());
-                ++iters;
-                k = j + 1;
                 givens_kernel<<<1, 1, 0, s>>>(S.sm, sl, j);
                 count_launch();
                 scale_kernel<<<vg, 256, 0, s>>>(vn, vn, L, S.sm + sl.nrm2(), 1);

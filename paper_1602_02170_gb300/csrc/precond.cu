@@ -7,7 +7,8 @@
 // whose solution is U_p = -N_p (g_p + Q_p^T w_p), lambda_p = M_p^-1 w_p + Q_p U_p
 // with Q_p = M_p^-1 K_p and N_p = (K_p^T M_p^-1 K_p)^-1, the body mobility of
 // body p alone.  The setup kernel (one CTA per body) assembles M_p in FP64,
-// factors it by Cholesky, forms M_p^-1 by column solves, Q_p, the 6 x 6
+// factors it by Cholesky M_p = L L^T, inverts the factor (W = L^-1, kept
+// transposed in the free upper triangle), forms M_p^-1 = W^T W, Q_p, the 6 x 6
 // Schur complement and N_p, and stores the explicit (n+6) x (n+6) inverse
 //     P_p^-1 = [[M_p^-1 - Q_p N_p Q_p^T, -Q_p N_p], [-N_p Q_p^T, -N_p]],
 // so that one application is one batched FP64 GEMV per body.
@@ -23,7 +24,18 @@ namespace {
 constexpr int kSetupThreads = 256;
 constexpr int kSmemMaxRows = 160;   // n = 3 n_p rows held in shared memory up to this
 
-// Shared-memory layout of the setup kernel: [L (n*n, only if in smem) | Q (n*6) | QN (n*6) | S (36) | N (36)]
+// Row and column of entry e of a lower triangle enumerated row by row
+// (e = i (i + 1) / 2 + j, j <= i).
+__device__ __forceinline__ void tri_index(int e, int &i, int &j)
+{
+    i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (i > 0 && i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    j = e - i * (i + 1) / 2;
+}
+
+// Shared-memory layout of the setup kernel:
+//   [L (n*n, only if in smem) | Q (n*6) | QN (n*6) | S (36) | N (36) | dW (n)]
 template <bool WALL, bool L_SMEM>
 __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
@@ -42,6 +54,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
         double *QN = Q + 6 * n;
         double *S = QN + 6 * n;
         double *Nm = S + 36;
+        double *dW = Nm + 36;  // diagonal of W = L^-1
         __shared__ int bad;
         double *Pp = P + poff[p];
         const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
@@ -73,9 +86,12 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
             for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) L[i * n + c] *= dinv;
             __syncthreads();
             const int w = n - c - 1;
-            for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-                const int i = c + 1 + e / w, j = c + 1 + e % w;
-                if (j <= i) L[i * n + j] -= L[i * n + c] * L[j * n + c];
+            for (int e = threadIdx.x; e < w * (w + 1) / 2; e += blockDim.x) {
+                int i, j;
+                tri_index(e, i, j);
+                i += c + 1;
+                j += c + 1;
+                L[i * n + j] -= L[i * n + c] * L[j * n + c];
             }
             __syncthreads();
         }
@@ -88,20 +104,43 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
             continue;
         }
 
-        // 3. X = M_p^-1 by column solves L y = e_c, L^T x = y; column c lives in
-        //    P_p[:, c] (row stride m), one thread per column
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            for (int i = 0; i < c; ++i) Pp[(size_t)i * m + c] = 0.0;
-            for (int i = c; i < n; ++i) {
-                double acc = (i == c) ? 1.0 : 0.0;
-                for (int kk = c; kk < i; ++kk) acc -= L[i * n + kk] * Pp[(size_t)kk * m + c];
-                Pp[(size_t)i * m + c] = acc / L[i * n + i];
+        // 3. W = L^-1 (lower triangular), row by row: row k of W is
+        //    (e_k - sum_{j<k} L[k][j] W[j][:]) / L[k][k].  Right-looking: once
+        //    row k is complete, subtract its multiples from every later row, so
+        //    each step is one parallel sweep.  W[i][c] (i > c) is stored at
+        //    L[c][i], the free upper triangle; the diagonal in dW.  Rows are
+        //    kept unscaled until the end (W[k][c] = stored * dW[k]).
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dW[i] = 1.0 / L[i * n + i];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int c = e / n, i = e % n;
+            if (i > c) L[c * n + i] = 0.0;
+        }
+        __syncthreads();
+        for (int kk = 0; kk + 1 < n; ++kk) {
+            const int rows = n - kk - 1, cols = kk + 1;
+            const double dk = dW[kk];
+            for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+                const int c = e / rows, i = kk + 1 + e % rows;
+                const double wkc = c < kk ? L[c * n + kk] * dk : dk;  // W[k][c]
+                L[c * n + i] -= L[i * n + kk] * wkc;
             }
-            for (int i = n - 1; i >= 0; --i) {
-                double acc = Pp[(size_t)i * m + c];
-                for (int kk = i + 1; kk < n; ++kk) acc -= L[kk * n + i] * Pp[(size_t)kk * m + c];
-                Pp[(size_t)i * m + c] = acc / L[i * n + i];
-            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int c = e / n, i = e % n;
+            if (i > c) L[c * n + i] *= dW[i];
+        }
+        __syncthreads();
+
+        // 3b. X = M_p^-1 = W^T W: X[i][j] = sum_{k >= max(i,j)} W[k][i] W[k][j],
+        //     written to P_p[:n, :n] (row stride m), both triangles
+        for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
+            int i, j;
+            tri_index(e, i, j);  // j <= i
+            double acc = dW[i] * (j < i ? L[j * n + i] : dW[i]);
+            for (int kk = i + 1; kk < n; ++kk) acc += L[i * n + kk] * L[j * n + kk];
+            Pp[(size_t)i * m + j] = acc;
+            Pp[(size_t)j * m + i] = acc;
         }
         __syncthreads();
 
@@ -210,25 +249,31 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
     }
 }
 
-// z_p = P_p^-1 [w_p; g_p] for every body; one CTA per body (grid-stride),
-// one warp per output row, lanes across the row.
+// z_p = P_p^-1 [w_p; g_p] for every body.  Work items are (body, row chunk)
+// with `chunks` chunks of `rows` rows per body (one chunk when bodies are
+// plentiful, several when few bodies would leave SMs idle); one warp per
+// output row, lanes across the row.
 __global__ void __launch_bounds__(256) precond_apply_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     const double *__restrict__ P, const double *__restrict__ w, const double *__restrict__ g,
-    double *__restrict__ lam, double *__restrict__ UO)
+    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows)
 {
     extern __shared__ double xs[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
+    for (int64_t item = blockIdx.x; item < nb * chunks; item += gridDim.x) {
+        const int64_t p = item / chunks;
+        const int r0 = (int)(item % chunks) * rows;
         const int64_t b0 = start[p];
         const int n = 3 * (int)(start[p + 1] - b0);
         const int m = n + 6;
+        const int r1 = min(m, r0 + rows);
+        if (r0 >= m) continue;  // uniform over the CTA
         __syncthreads();
         for (int e = threadIdx.x; e < m; e += blockDim.x)
             xs[e] = e < n ? w[3 * b0 + e] : g[6 * p + (e - n)];
         __syncthreads();
         const double *Pp = P + poff[p];
-        for (int row = warp; row < m; row += nw) {
+        for (int row = r0 + warp; row < r1; row += nw) {
             const double *pr = Pp + (size_t)row * m;
             double acc = 0.0;
             for (int c = lane; c < m; c += 32) acc += pr[c] * xs[c];
@@ -240,6 +285,386 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Split setup for bodies with 3 n_p <= kSplitMaxRows.  The single kernel
+// above runs every step of a body on one SM; here only the Cholesky does,
+// and the O(n^3) rest is spread over many CTAs:
+//   S1 pc_assemble_kernel  M_p written into P_p's n x n block (warp per blob row);
+//   S2 pc_factor_kernel    one CTA per body: Cholesky M_p = L L^T carried out
+//                          together with G = L^-1 K_p (the six K columns are
+//                          eliminated alongside), then S = G^T G = K^T M^-1 K,
+//                          N = S^-1; stores L^T in P_p's upper triangle;
+//   S3 pc_trinv_kernel     one warp per column c of W = L^-1 (forward
+//                          substitution in registers), with row c of
+//                          Q = M^-1 K = W^T G and of Q N, and P_p's border;
+//   S4 pc_product_kernel   P_p's n x n block = W^T W - (Q N) Q^T in 32 x 32
+//                          tiles through shared memory.
+// Per-body scratch (stride kept uniform within a group of bodies):
+//   [W (nmax^2, row-major, zero above the diagonal near it) | G (6 nmax) |
+//    Q (6 nmax) | QN (6 nmax) | dW (nmax) | N (36)].
+constexpr int kSplitMaxRows = 512;
+constexpr int kTile = 32;
+
+__device__ __forceinline__ int64_t owner_body(const int64_t *__restrict__ start, int64_t nb,
+                                              int64_t b)
+{
+    int64_t lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct SplitScratch {
+    double *base;
+    int64_t stride;  // doubles per body
+    int nmax;
+    __device__ double *W(int64_t p) const { return base + p * stride; }
+    __device__ double *G(int64_t p) const { return W(p) + (int64_t)nmax * nmax; }
+    __device__ double *Q(int64_t p) const { return G(p) + 6 * nmax; }
+    __device__ double *QN(int64_t p) const { return Q(p) + 6 * nmax; }
+    __device__ double *dW(int64_t p) const { return QN(p) + 6 * nmax; }
+    __device__ double *N(int64_t p) const { return dW(p) + nmax; }
+};
+
+int64_t split_stride(int nmax) { return (int64_t)nmax * nmax + 19 * (int64_t)nmax + 36; }
+
+// S1: M_p (scaled) into P_p[0:n, 0:n], row stride m = n + 6.
+template <bool WALL>
+__global__ void __launch_bounds__(256) pc_assemble_kernel(
+    int64_t nb, const double *__restrict__ r, const int64_t *__restrict__ start,
+    const int64_t *__restrict__ poff, PairConsts<double> k, double scale, double *__restrict__ P)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s0 = start[0], rows = start[nb] - s0;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); it < rows;
+         it += warps) {
+        const int64_t b = s0 + it;
+        const int64_t p = owner_body(start, nb, b);
+        const int64_t b0 = start[p];
+        const int np = (int)(start[p + 1] - b0), bi = (int)(b - b0);
+        const int m = 3 * np + 6;
+        double *Pp = P + poff[p];
+        for (int bj = lane; bj < np; bj += 32) {
+            double blk[9];
+            block_f64<WALL>(r + 3 * b, r + 3 * (b0 + bj), k, blk);
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be)
+                    Pp[(size_t)(3 * bi + al) * m + 3 * bj + be] = scale * blk[3 * al + be];
+        }
+    }
+}
+
+// S2: one CTA per body.  Right-looking Cholesky on the lower triangle with
+// the six columns B = K_p appended (so that B ends as G = L^-1 K_p): step c
+// scales column c by 1/sqrt(d_c), then subtracts its outer product from the
+// trailing triangle and its multiples of row c from the rows of B below,
+// one FP64 FMA per entry (FP64 issue is the bound on this chip).
+template <bool L_SMEM>
+__global__ void __launch_bounds__(256) pc_factor_kernel(
+    int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
+    const int64_t *__restrict__ start, const int64_t *__restrict__ poff, double *__restrict__ P,
+    SplitScratch scr, int *__restrict__ flag, int flag_slot, int64_t p_base)
+{
+    extern __shared__ double sm[];
+    __shared__ int bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
+        const int64_t b0 = start[p];
+        const int np = (int)(start[p + 1] - b0);
+        const int n = 3 * np, m = n + 6;
+        double *Pp = P + poff[p];
+        double *L = L_SMEM ? sm : Pp;
+        const int ld = L_SMEM ? n : m;
+        double *B = L_SMEM ? sm + (size_t)n * n : scr.G(p);
+        double *ils = L_SMEM ? B + 6 * n : sm;  // 1 / sqrt(d_c)
+        double *S = ils + n;
+        double *Nm = S + 36;
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        __syncthreads();
+        if (threadIdx.x == 0) bad = 0;
+        if (L_SMEM)
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                const int i = e / n, j = e % n;
+                if (j <= i) L[e] = Pp[(size_t)i * m + j];
+            }
+        // B = K_p: rows of blob i are [I, -[d_i]x]
+        for (int e = threadIdx.x; e < 6 * n; e += blockDim.x) {
+            const int row = e / 6, col = e % 6, i = row / 3, al = row % 3;
+            double v;
+            if (col < 3) {
+                v = al == col ? 1.0 : 0.0;
+            } else {
+                const double dx = r[3 * (b0 + i)] - qx, dy = r[3 * (b0 + i) + 1] - qy,
+                             dz = r[3 * (b0 + i) + 2] - qz;
+                // -[d]x = [[0, dz, -dy], [-dz, 0, dx], [dy, -dx, 0]]
+                const int e3 = 3 * al + col - 3;
+                v = e3 == 1 ? dz : e3 == 2 ? -dy : e3 == 3 ? -dz : e3 == 5 ? dx
+                  : e3 == 6 ? dy : e3 == 7 ? -dx : 0.0;
+            }
+            B[e] = v;
+        }
+        int fail = 0;
+        for (int c = 0; c < n; ++c) {
+            __syncthreads();
+            const double d = L[(size_t)c * ld + c];
+            if (!(d > 0.0)) {  // every thread reads the same pivot
+                fail = 1;
+                break;
+            }
+            double il = 0.0;
+            if (lane == 0) il = 1.0 / sqrt(d);
+            il = __shfl_sync(0xffffffffu, il, 0);
+            if (threadIdx.x == 0) ils[c] = il;
+            // scale column c (L[c][c] becomes sqrt(d)) and row c of B
+            for (int i = c + threadIdx.x; i < n; i += blockDim.x) L[(size_t)i * ld + c] *= il;
+            if (threadIdx.x >= 32 && threadIdx.x < 38) B[6 * c + threadIdx.x - 32] *= il;
+            __syncthreads();
+            // trailing update with the scaled column: one FMA per entry
+            const int w = n - c - 1;
+            for (int e = threadIdx.x; e < w * (w + 1) / 2; e += blockDim.x) {
+                int i, j;
+                tri_index(e, i, j);
+                i += c + 1;
+                j += c + 1;
+                L[(size_t)i * ld + j] -= L[(size_t)i * ld + c] * L[(size_t)j * ld + c];
+            }
+            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
+                const int i = c + 1 + e / 6, bcol = e % 6;
+                B[6 * i + bcol] -= L[(size_t)i * ld + c] * B[6 * c + bcol];
+            }
+        }
+        __syncthreads();
+        if (fail) {  // uniform: a pivot was not positive
+            if (threadIdx.x == 0) {
+                if (flag_slot >= 0) flag[flag_slot] = 2;
+                else atomicMin(flag, (int)(p_base + p));
+            }
+            continue;
+        }
+        // dW, G to scratch; L^T into P_p's upper triangle (row k holds column k of L)
+        double *dW = scr.dW(p), *G = scr.G(p);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dW[i] = ils[i];
+        if (L_SMEM)
+            for (int e = threadIdx.x; e < 6 * n; e += blockDim.x) G[e] = B[e];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int kk = e / n, i = e % n;
+            if (i > kk) Pp[(size_t)kk * m + i] = L[(size_t)i * ld + kk];
+            else if (L_SMEM && i == kk) Pp[(size_t)kk * m + kk] = L[(size_t)kk * ld + kk];
+        }
+        __syncthreads();
+        // S = G^T G (symmetric 6 x 6), one warp per entry
+        for (int ab = warp; ab < 36; ab += nw) {
+            const int a = ab / 6, bb = ab % 6;
+            double acc = 0.0;
+            for (int i = lane; i < n; i += 32) acc += B[6 * i + a] * B[6 * i + bb];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) S[ab] = acc;
+        }
+        __syncthreads();
+        // N = S^-1 by Gauss-Jordan (one thread)
+        if (threadIdx.x == 0) {
+            double A[6][12];
+            for (int a = 0; a < 6; ++a)
+                for (int bb = 0; bb < 6; ++bb) {
+                    A[a][bb] = 0.5 * (S[a * 6 + bb] + S[bb * 6 + a]);
+                    A[a][6 + bb] = (a == bb) ? 1.0 : 0.0;
+                }
+            for (int c = 0; c < 6 && !bad; ++c) {
+                const double dd = A[c][c];
+                if (!(dd > 0.0)) { bad = 1; break; }
+                for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
+                for (int a = 0; a < 6; ++a)
+                    if (a != c) {
+                        const double f = A[a][c];
+                        for (int bb = 0; bb < 12; ++bb) A[a][bb] -= f * A[c][bb];
+                    }
+            }
+            for (int a = 0; a < 6; ++a)
+                for (int bb = 0; bb < 6; ++bb) Nm[a * 6 + bb] = A[a][6 + bb];
+        }
+        __syncthreads();
+        if (bad) {
+            if (threadIdx.x == 0) {
+                if (flag_slot >= 0) flag[flag_slot] = 2;
+                else atomicMin(flag, (int)(p_base + p));
+            }
+            continue;
+        }
+        double *Ns = scr.N(p);
+        if (threadIdx.x < 36) {
+            Ns[threadIdx.x] = Nm[threadIdx.x];
+            Pp[(size_t)(n + threadIdx.x / 6) * m + n + threadIdx.x % 6] = -Nm[threadIdx.x];
+        }
+    }
+}
+
+// S3: warp per column c of W = L^-1.  Lane l holds rows 32 t + l of the
+// column (t < R).  Step k: W[k][c] = (current value of row k) / L[k][k],
+// then rows i > k lose L[i][k] W[k][c].  L[i][k] is read from P_p's upper
+// triangle (contiguous in i).  Along the way the warp forms
+// Q[c][:] = sum_k W[k][c] G[k][:] and QN[c][:] = Q[c][:] N, and writes P_p's
+// border entries -QN[c][b] (column n + b of row c and its transpose).
+template <int R>
+__global__ void __launch_bounds__(256) pc_trinv_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int col_groups)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
+        const int64_t p = item / col_groups;
+        const int c = (int)(item % col_groups) * nw + warp;
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        if (c >= n) continue;  // warp-uniform
+        const double *Lt = P + poff[p];
+        double *W = scr.W(p);
+        const double *G = scr.G(p), *dW = scr.dW(p), *Nm = scr.N(p);
+        const int ldw = scr.nmax;
+        double w[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) w[t] = (32 * t + lane == c) ? 1.0 : 0.0;
+        // zero the rows of column c that the tiled product reads above the diagonal
+        for (int kk = (c & ~(kTile - 1)) + lane; kk < c; kk += 32) W[(size_t)kk * ldw + c] = 0.0;
+        double qa = 0.0;  // lane b < 6: Q[c][b]
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (32 * t + 31 < c) continue;
+            if (32 * t >= n) break;
+            for (int l = 0; l < 32; ++l) {
+                const int k = 32 * t + l;
+                if (k < c) continue;
+                if (k >= n) break;
+                const double wk = __shfl_sync(0xffffffffu, w[t], l) * dW[k];
+                if (lane == l) W[(size_t)k * ldw + c] = wk;
+                if (lane < 6) qa += wk * G[6 * k + lane];
+                const double *lk = Lt + (size_t)k * m;
+#pragma unroll
+                for (int t2 = t; t2 < R; ++t2) {
+                    const int i = 32 * t2 + lane;
+                    if (i > k && i < n) w[t2] -= lk[i] * wk;
+                }
+            }
+        }
+        // QN[c][b] = sum_a Q[c][a] N[a][b]
+        double qn = 0.0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const double qv = __shfl_sync(0xffffffffu, qa, a);
+            if (lane < 6) qn += qv * Nm[a * 6 + lane];
+        }
+        if (lane < 6) {
+            scr.Q(p)[6 * c + lane] = qa;
+            scr.QN(p)[6 * c + lane] = qn;
+            P[poff[p] + (size_t)c * m + n + lane] = -qn;
+            P[poff[p] + (size_t)(n + lane) * m + c] = -qn;
+        }
+    }
+}
+
+// S4: P_p[i][j] = sum_k W[k][i] W[k][j] - sum_b QN[i][b] Q[j][b] on the
+// lower 32 x 32 tiles (I >= J) of the n x n block, mirrored to the upper.
+__global__ void __launch_bounds__(256) pc_product_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int tiles_per_body)
+{
+    __shared__ double Wi[kTile][kTile + 1], Wj[kTile][kTile + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of threads
+    for (int64_t item = blockIdx.x; item < nb * tiles_per_body; item += gridDim.x) {
+        const int64_t p = item / tiles_per_body;
+        int I, J;
+        tri_index((int)(item % tiles_per_body), I, J);
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        const int i0 = I * kTile, j0 = J * kTile;
+        if (i0 >= n) continue;  // CTA-uniform
+        const double *W = scr.W(p);
+        const int ldw = scr.nmax;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k0 = i0; k0 < n; k0 += kTile) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+                const int kk = e / kTile, cc = e % kTile;
+                const int k = k0 + kk;
+                Wi[kk][cc] = (k < n && i0 + cc < n) ? W[(size_t)k * ldw + i0 + cc] : 0.0;
+                Wj[kk][cc] = (k < n && j0 + cc < n) ? W[(size_t)k * ldw + j0 + cc] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < kTile; ++kk) {
+                const double wj = Wj[kk][tx];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) acc[rr] += Wi[kk][ty + 8 * rr] * wj;
+            }
+        }
+        const double *Qs = scr.Q(p), *QN = scr.QN(p);
+        double *Pp = P + poff[p];
+        const int j = j0 + tx;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int i = i0 + ty + 8 * rr;
+            if (i >= n || j >= n || (I == J && j > i)) continue;
+            double v = acc[rr];
+#pragma unroll
+            for (int bb = 0; bb < 6; ++bb) v -= QN[6 * i + bb] * Qs[6 * j + bb];
+            Pp[(size_t)i * m + j] = v;
+            Pp[(size_t)j * m + i] = v;
+        }
+    }
+}
+
+// Runs S1..S4 over groups of bodies whose scratch fits the cap.
+mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double *q,
+                      const int64_t *start, const int64_t *poff, double *P, int max_np, double a,
+                      double eta, int wall, int *flag, int flag_slot, cudaStream_t s)
+{
+    const int nmax = 3 * max_np;
+    const int64_t stride = split_stride(nmax);
+    const int64_t cap_bytes = (int64_t)256 << 20;
+    const int64_t group = std::max<int64_t>(1, std::min<int64_t>(nb, cap_bytes / (8 * stride)));
+    MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * group, "preconditioner scratch"));
+    SplitScratch scr{(double *)ctx->sol_dots.ptr, stride, nmax};
+    const PairConsts<double> k = PairConsts<double>::make(a);
+    const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
+    const bool lsmem = nmax <= kSmemMaxRows;
+    const size_t fsmem =
+        sizeof(double) * ((lsmem ? (size_t)nmax * nmax + 6 * (size_t)nmax : 0) + nmax + 72);
+    const int col_groups = (int)ceil_div(nmax, 8);
+    const int T = (int)ceil_div(nmax, kTile);
+    const int tiles = T * (T + 1) / 2;
+    for (int64_t g0 = 0; g0 < nb; g0 += group) {
+        const int64_t ng = std::min(group, nb - g0);
+        const int64_t *st = start + g0;
+        const int64_t *po = poff + g0;
+        const int ga = (int)std::min<int64_t>(ceil_div(ng * max_np, 8), 8 * (int64_t)ctx->sm_count);
+        if (wall)
+            pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P);
+        else
+            pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P);
+        auto factor = lsmem ? pc_factor_kernel<true> : pc_factor_kernel<false>;
+        MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)fsmem));
+        factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
+            ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0);
+        const int gt = (int)std::min<int64_t>(ng * col_groups, 16 * (int64_t)ctx->sm_count);
+        if (nmax <= 128)
+            pc_trinv_kernel<4><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+        else if (nmax <= 256)
+            pc_trinv_kernel<8><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+        else
+            pc_trinv_kernel<16><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+        const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
+        pc_product_kernel<<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles);
+        count_launch(4);
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return MB_OK;
 }
 
 }  // namespace
@@ -277,20 +702,24 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
 
     const int nmax = 3 * max_np;
     const bool lsmem = nmax <= kSmemMaxRows;
-    const size_t small = sizeof(double) * (12 * (size_t)nmax + 72);
+    const size_t small = sizeof(double) * (13 * (size_t)nmax + 72);
     const size_t smem = small + (lsmem ? sizeof(double) * (size_t)nmax * nmax : 0);
     const PairConsts<double> k = PairConsts<double>::make(a);
     const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
     int grid = (int)std::min<int64_t>(nb, 4 * (int64_t)ctx->sm_count);
     double *scratch = nullptr;
     int64_t stride = 0;
-    if (!lsmem) {
+    if (!lsmem && nmax > kSplitMaxRows) {
         grid = (int)std::min<int64_t>(nb, ctx->sm_count);
         stride = (int64_t)nmax * nmax;
         MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
         scratch = (double *)ctx->sol_dots.ptr;
     }
     auto launch = [&](auto kern) -> mb_status {
+        if (nmax <= kSplitMaxRows)
+            return setup_split(ctx, nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
+                               (const int64_t *)ctx->pinv_off.ptr, (double *)ctx->pinv.ptr, max_np,
+                               a, eta, wall, (int *)ctx->flag.ptr, -1, s);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
@@ -331,20 +760,23 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
 {
     const int nmax = 3 * max_np;
     const bool lsmem = nmax <= kSmemMaxRows;
-    const size_t small = sizeof(double) * (12 * (size_t)nmax + 72);
+    const size_t small = sizeof(double) * (13 * (size_t)nmax + 72);
     const size_t smem = small + (lsmem ? sizeof(double) * (size_t)nmax * nmax : 0);
     const PairConsts<double> k = PairConsts<double>::make(a);
     const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
     int grid = (int)std::min<int64_t>(nb, 4 * (int64_t)ctx->sm_count);
     double *scratch = nullptr;
     int64_t stride = 0;
-    if (!lsmem) {
+    if (!lsmem && nmax > kSplitMaxRows) {
         grid = (int)std::min<int64_t>(nb, ctx->sm_count);
         stride = (int64_t)nmax * nmax;
         MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
         scratch = (double *)ctx->sol_dots.ptr;
     }
     auto launch = [&](auto kern) -> mb_status {
+        if (nmax <= kSplitMaxRows)
+            return setup_split(ctx, nb, r, q, start, poff, P, max_np, a, eta, wall, flags,
+                               flag_slot, s);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, start, poff, k, scale, P, scratch, stride,
@@ -364,10 +796,14 @@ static void precond_apply_impl(mb_context *ctx, const double *w, const double *g
                                double *UO, cudaStream_t s)
 {
     const int m = 3 * ctx->pc_max_np + 6;
-    const int grid = (int)std::min<int64_t>(ctx->pc_nb, 8 * (int64_t)ctx->sm_count);
+    // few bodies: split each body's rows so that about two CTAs per SM have work
+    const int64_t want = ceil_div(2 * (int64_t)ctx->sm_count, ctx->pc_nb);
+    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ceil_div(m, 8)));
+    const int rows = (int)ceil_div(m, chunks);
+    const int grid = (int)std::min<int64_t>(ctx->pc_nb * chunks, 8 * (int64_t)ctx->sm_count);
     precond_apply_kernel<<<grid, 256, sizeof(double) * m, s>>>(
         ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int64_t *)ctx->pinv_off.ptr,
-        (const double *)ctx->pinv.ptr, w, g, lam, UO);
+        (const double *)ctx->pinv.ptr, w, g, lam, UO, chunks, rows);
     count_launch();
 }
 

@@ -104,6 +104,30 @@ def test_preconditioner_large_bodies_global_path(ctx):
     assert rel_l2(host(UO), UO_ref) <= 1e-8
 
 
+def test_preconditioner_very_large_bodies_single_kernel_path(ctx):
+    """Bodies of 180 blobs (540 rows) exceed the split setup's register
+    column limit and take the one-kernel-per-body setup."""
+    g = np.stack(np.meshgrid(np.arange(6), np.arange(6), np.arange(5), indexing="ij"), -1)
+    a = 0.1
+    rho1 = (g.reshape(-1, 3) - np.array([2.5, 2.5, 2.0])) * (2.2 * a)
+    rng = np.random.default_rng(6)
+    rho = np.concatenate([rho1 + 0.01 * a * rng.standard_normal(rho1.shape) for _ in range(2)])
+    s = I.Suspension(q=np.array([[0.0, 0.0, 1.5], [2.0, 0.5, 1.7]]),
+                     theta=I.random_unit_quaternions(rng, 2),
+                     blob_start=np.array([0, 180, 360], dtype=np.int64), rho=rho,
+                     F=np.zeros((2, 3)), T=np.zeros((2, 3)), a=a)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    assert r[:, 2].min() > a
+    w = rng.standard_normal((s.n_blobs, 3))
+    gg = rng.standard_normal((s.n_bodies, 6))
+    d = _dev_susp(s)
+    ctx.precond_setup(dev(r), d["q"], d["blob_start"], s.a, 1.0, True)
+    lam, UO = ctx.precond_apply(dev(w), dev(gg))
+    lam_ref, UO_ref = O.precond_apply(r, s.q, s.blob_start, s.a, 1.0, True, w, gg)
+    assert rel_l2(host(lam), lam_ref) <= 1e-8
+    assert rel_l2(host(UO), UO_ref) <= 1e-8
+
+
 def test_preconditioner_singular_block_reported(ctx):
     """A blob at z = a/2 makes its body's wall-corrected block indefinite: the
     setup reports MB_ESINGULAR instead of producing NaNs."""
