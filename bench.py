@@ -70,7 +70,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-solve", action="store_true")
     p.add_argument("--solves", type=int, default=30)
-    p.add_argument("--workload", choices=["matvec", "monolayer", "batch", "serve"],
+    p.add_argument("--solve-prec", default="mixed", choices=["mixed", "fp32", "fp64", "df64"],
+                   help="precision of the --workload small solves")
+    p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve"],
                    default="matvec",
                    help="matvec: the benchmark line below; monolayer / batch / serve: the "
                         "663,552-blob monolayer solve, 256 batched suspensions, and the "
@@ -348,8 +350,8 @@ def run_ours(args):
     return 0
 
 
-def bench_solves(ctx, count):
-    """Mixed-precision mobility solves of the 8 x 42-blob suspension."""
+def bench_solves(ctx, count, prec="mixed"):
+    """Mobility solves of the 8 x 42-blob suspension (tol 1e-10; 1e-6 for fp32)."""
     import numpy as np
     import torch
 
@@ -360,13 +362,14 @@ def bench_solves(ctx, count):
     d = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x)).to("cuda", dt)
     args = (d(s.q), d(s.theta), d(s.blob_start, torch.int64), d(s.rho), d(s.F), d(s.T), s.a,
             s.eta, True)
+    tol = 1e-6 if prec == "fp32" else 1e-10
     for _ in range(3):
-        ctx.solve_mobility(*args, tol=1e-10, prec="mixed")
+        ctx.solve_mobility(*args, tol=tol, prec=prec)
     lat = []
     infos = []
     for _ in range(count):
         t0 = time.perf_counter()
-        U, W, lam, info = ctx.solve_mobility(*args, tol=1e-10, prec="mixed")
+        U, W, lam, info = ctx.solve_mobility(*args, tol=tol, prec=prec)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0)
         infos.append(info)
@@ -375,10 +378,28 @@ def bench_solves(ctx, count):
     eU = float(np.linalg.norm(U.cpu().numpy() - Ur) / np.linalg.norm(Ur))
     eW = float(np.linalg.norm(W.cpu().numpy() - Wr) / np.linalg.norm(Wr))
     lat_ms = sorted(1e3 * x for x in lat)
-    return {"workload": "8 x 42-blob shells above the wall (N=336), GMRES tol 1e-10, mixed precision",
+    return {"workload": f"8 x 42-blob shells above the wall (N=336), GMRES tol {tol:g}, {prec}",
             "solves_per_s": count / sum(lat), "p50_ms": lat_ms[len(lat_ms) // 2],
             "p99_ms": lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)],
-            "iters": infos[-1]["iters"], "rel_err_U": eU, "rel_err_Omega": eW}
+            "iters": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
+            "setup_ms": infos[-1]["setup_ms"], "solve_ms": infos[-1]["solve_ms"],
+            "rel_err_U": eU, "rel_err_Omega": eW}
+
+
+def bench_small(args):
+    """The 8 x 42-blob suspension alone: solves/s, p50/p99 and the setup /
+    iteration split of one solve (the command the small-solve launch list
+    in profiles/ is taken from)."""
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+
+    B.build()
+    ctx = mb.Context(0)
+    line = bench_solves(ctx, args.solves, args.solve_prec)
+    line.update({"metric": "mobility solves/s", "unit": "solves/s", "n_gpus": 1})
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
 
 
 def _dev_problem(s):
@@ -604,6 +625,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "small":
+        return bench_small(args)
     if args.workload == "monolayer":
         return bench_monolayer(args)
     if args.workload == "batch":
