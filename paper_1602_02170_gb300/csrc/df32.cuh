@@ -41,33 +41,51 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b)
     return dfl(s, b - (s - a));
 }
 
-// Addition in the "sloppy" form of Bailey's QD library: an exact two-sum of
-// the high parts, the low parts added in FP32, one renormalisation (11 FP32
-// operations instead of 20 for the form that also two-sums the low parts).
-// Its absolute error is within a few 2^-48 (|a| + |b|): relative accuracy is
-// lost only where a and b nearly cancel, and then only relative to the
-// operands, which is what the pair sums need (about 1e-13 of each term).
+// Addition in the "sloppy" form of Bailey's QD library (an exact two-sum of
+// the high parts, the low parts added in FP32), here without the closing
+// renormalisation: 8 FP32 operations instead of 20 for the form that also
+// two-sums the low parts and renormalises twice.  The result hi + lo is not
+// normalised (lo may exceed half an ulp of hi); every operation here accepts
+// such operands, and subtraction, accumulation (+=) and the reciprocal square
+// root renormalise.  The absolute error is within a few 2^-48 (|a| + |b|), so
+// relative accuracy is lost only where a and b nearly cancel, and then only
+// relative to the operands, which is what the pair sums need (about 1e-13 of
+// each term).
 __device__ __forceinline__ dfl operator+(dfl a, dfl b)
 {
     const dfl s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+    return dfl(s.hi, s.lo + (a.lo + b.lo));
 }
 
 __device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
-__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+// Subtraction renormalises: it forms the separations of nearby positions,
+// where hi nearly cancels and the unnormalised lo would be large relative to
+// the difference.
+__device__ __forceinline__ dfl operator-(dfl a, dfl b)
+{
+    const dfl s = two_sum(a.hi, -b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
+}
 
+// Product without the final renormalisation: lo may reach a few ulp of hi
+// instead of half an ulp.  Every consumer (addition, product, conversion to
+// double) takes such operands without loss beyond ~2^-46 relative.
 __device__ __forceinline__ dfl operator*(dfl a, dfl b)
 {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
+    return dfl(p, e);
 }
 
+// Accumulation renormalises (fast two-sum after the sloppy addition): a
+// running sum over thousands of terms would otherwise let lo grow and lose
+// bits in its FP32 additions.
 __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b)
 {
-    a = a + b;
+    const dfl s = two_sum(a.hi, b.hi);
+    a = fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
     return a;
 }
 
@@ -80,6 +98,7 @@ __device__ __forceinline__ dfl mb_max(dfl a, dfl b) { return a < b ? b : a; }
 
 __device__ __forceinline__ dfl mb_rsqrt(dfl x)
 {
+    x = fast_two_sum(x.hi, x.lo);  // the FP32 estimate needs the normalised hi
     const float y0 = rsqrtf(x.hi);
     const dfl y(y0, 0.f);
     // r = 1 - x y0^2, small; y = y0 + y0 r / 2
