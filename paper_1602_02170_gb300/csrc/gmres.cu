@@ -205,10 +205,16 @@ __global__ void givens_kernel(double *__restrict__ sm, Small L, int j) { givens_
 // One CTA does the whole orthogonalisation of w = V_{j+1} for small systems:
 // both classical Gram-Schmidt passes (h = V^T w, w -= V h), their merged
 // coefficients as column j of H, |w|, the Givens update and w /= |w|.  The
-// same steps as the multi-kernel sequence, without its 9 launches.
+// same steps as the multi-kernel sequence, without its 9 launches.  T is the
+// arithmetic of the passes: double, or float for the FP32 inner iterations
+// of mixed precision, whose basis only needs FP32 orthogonality (the FP32
+// matvec already limits the Arnoldi relation to that level, and the outer
+// refinement restores FP64 accuracy); GB300's FP64 rate on one SM made the
+// double passes the largest cost of a small solve.
 constexpr int kOrthThreads = 1024;
 constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one CTA
 
+template <typename T>
 __global__ void __launch_bounds__(kOrthThreads) orth_small_kernel(double *__restrict__ V,
                                                                   int64_t L, int j,
                                                                   double *__restrict__ sm,
@@ -230,17 +236,17 @@ __global__ void __launch_bounds__(kOrthThreads) orth_small_kernel(double *__rest
     for (int pass = 0; pass < 2; ++pass) {
         for (int i = warp; i <= j; i += nw) {
             const double *v = V + (int64_t)i * L;
-            double acc = 0.0;
-            for (int64_t e = lane; e < L; e += 32) acc += v[e] * w[e];
+            T acc = T(0);
+            for (int64_t e = lane; e < L; e += 32) acc += T(v[e]) * T(w[e]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) hs[i] = acc;
+            if (lane == 0) hs[i] = double(acc);
         }
         __syncthreads();
         for (int64_t e = threadIdx.x; e < L; e += blockDim.x) {
-            double acc = w[e];
-            for (int i = 0; i <= j; ++i) acc -= V[(int64_t)i * L + e] * hs[i];
-            w[e] = acc;
+            T acc = T(w[e]);
+            for (int i = 0; i <= j; ++i) acc -= T(V[(int64_t)i * L + e]) * T(hs[i]);
+            w[e] = double(acc);
         }
         for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = pass == 0 ? hs[i] : hc[i] + hs[i];
         __syncthreads();
@@ -508,8 +514,11 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                 ++iters;
                 k = j + 1;
                 if ((int64_t)(j + 1) * L <= kOrthSmallMax) {
-                    orth_small_kernel<<<1, kOrthThreads, sizeof(double) * (4 * m + 3 + 32), s>>>(
-                        S.V, L, j, S.sm, sl);
+                    const size_t osm = sizeof(double) * (4 * m + 3 + 32);
+                    if (inner == MB_FP32_KAHAN)
+                        orth_small_kernel<float><<<1, kOrthThreads, osm, s>>>(S.V, L, j, S.sm, sl);
+                    else
+                        orth_small_kernel<double><<<1, kOrthThreads, osm, s>>>(S.V, L, j, S.sm, sl);
                     count_launch();
                     MB_CUDA_TRY(ctx, cudaGetLastError());
                     double est = 0.0;

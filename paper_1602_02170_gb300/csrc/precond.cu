@@ -427,18 +427,14 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             for (int i = c + threadIdx.x; i < n; i += blockDim.x) L[(size_t)i * ld + c] *= il;
             if (threadIdx.x >= 32 && threadIdx.x < 38) B[6 * c + threadIdx.x - 32] *= il;
             __syncthreads();
-            // trailing update with the scaled column: one FMA per entry
-            const int w = n - c - 1;
-            for (int e = threadIdx.x; e < w * (w + 1) / 2; e += blockDim.x) {
-                int i, j;
-                tri_index(e, i, j);
-                i += c + 1;
-                j += c + 1;
-                L[(size_t)i * ld + j] -= L[(size_t)i * ld + c] * L[(size_t)j * ld + c];
-            }
-            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
-                const int i = c + 1 + e / 6, bcol = e % 6;
-                B[6 * i + bcol] -= L[(size_t)i * ld + c] * B[6 * c + bcol];
+            // trailing update with the scaled column, one FMA per entry: rows
+            // i > c round-robin over the warps, lanes across j in (c, i] and
+            // the six B columns (no index decoding per entry)
+            for (int i = c + 1 + warp; i < n; i += nw) {
+                double *Li = L + (size_t)i * ld;
+                const double lic = Li[c];
+                for (int j = c + 1 + lane; j <= i; j += 32) Li[j] -= lic * L[(size_t)j * ld + c];
+                if (lane < 6) B[6 * i + lane] -= lic * B[6 * c + lane];
             }
         }
         __syncthreads();
