@@ -32,6 +32,7 @@ mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what)
     if (ctx->held - buf.bytes + grow > ctx->budget)
         return set_err(ctx, MB_ENOMEM, "%s: %zu bytes would exceed the HBM budget (%zu held of %zu)",
                        what, grow, ctx->held - buf.bytes, ctx->budget);
+    ++ctx->alloc_gen;  // captured graphs that hold the old pointer are stale
     if (buf.ptr) {
         cudaFree(buf.ptr);
         ctx->held -= buf.bytes;
@@ -50,6 +51,7 @@ mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what)
 
 void release(mb_context *ctx, DevBuf &buf)
 {
+    ++ctx->alloc_gen;
     if (buf.ptr) {
         cudaFree(buf.ptr);
         ctx->held -= buf.bytes;
@@ -184,6 +186,9 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
                       &ctx->sol_dx, &ctx->sol_ym,
                       &ctx->batch_ws};
+    for (auto &g : ctx->iter_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (DevBuf *b : bufs) release(ctx, *b);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);
     for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }

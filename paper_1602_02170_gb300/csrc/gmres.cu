@@ -399,6 +399,91 @@ struct Solver {
     }
 };
 
+// The cache entry for a step signature: the matching one, else a free slot,
+// else the least recently used entry (its graph destroyed).
+IterGraph &graph_entry(mb_context *ctx, const IterSig &sig)
+{
+    auto &v = ctx->iter_graphs;
+    IterGraph *hit = nullptr;
+    for (auto &g : v)
+        if (g.sig == sig) { hit = &g; break; }
+    if (!hit) {
+        if (v.size() < kMaxIterGraphs) {
+            v.emplace_back();
+            hit = &v.back();
+        } else {
+            hit = &v[0];
+            for (auto &g : v)
+                if (g.last_use < hit->last_use) hit = &g;
+            if (hit->exec) cudaGraphExecDestroy(hit->exec);
+            *hit = IterGraph{};
+        }
+    }
+    hit->last_use = ++ctx->graph_clock;
+    return *hit;
+}
+
+// Run one Arnoldi step through its cached graph: replay it when the
+// signature matches, capture it when this signature was met once before,
+// otherwise only record the signature (the caller then runs the step
+// directly).  *ran tells whether the step was launched here.  A capture
+// that fails for any reason is dropped and the step runs directly.
+template <typename Step>
+mb_status run_step_graph(mb_context *ctx, IterGraph &g, const IterSig &sig, Step &step,
+                         cudaStream_t s, bool *ran)
+{
+    *ran = false;
+    if (g.exec && g.sig == sig) {
+        MB_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
+        count_launch(g.launches);
+        *ran = true;
+        return MB_OK;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!(g.seen && g.sig == sig)) {
+        g.seen = true;
+        g.sig = sig;
+        return MB_OK;
+    }
+    // capture on the context's own stream (capture is not allowed on the
+    // legacy default stream); nothing executes until the launch on s
+    if (!ctx->cap_stream &&
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ctx->cap_stream = nullptr;
+        cudaGetLastError();
+        return MB_OK;
+    }
+    const long long l0 = g_launches.load();
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return MB_OK;
+    }
+    const std::string saved_err = ctx->err;
+    const mb_status st = step(ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    const long long captured = g_launches.load() - l0;
+    count_launch(-captured);  // nothing ran yet
+    if (st != MB_OK || e != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        g.exec = nullptr;
+        g.seen = false;
+        cudaGetLastError();
+        ctx->err = saved_err;
+        return MB_OK;
+    }
+    cudaGraphDestroy(graph);
+    g.launches = captured;
+    MB_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
+    count_launch(g.launches);
+    *ran = true;
+    return MB_OK;
+}
+
 }  // namespace
 
 mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
@@ -509,23 +594,44 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                 double *vj = S.V + (int64_t)j * L;
                 double *zj = S.Z + (int64_t)j * L;
                 double *vn = S.V + (int64_t)(j + 1) * L;
-                precond_apply_packed(ctx, vj, zj, s);
-                MB_TRY(S.apply_A(zj, vn, inner));
                 ++iters;
                 k = j + 1;
                 if ((int64_t)(j + 1) * L <= kOrthSmallMax) {
-                    const size_t osm = sizeof(double) * (4 * m + 3 + 32);
-                    if (inner == MB_FP32_KAHAN)
-                        orth_small_kernel<float><<<1, kOrthThreads, osm, s>>>(S.V, L, j, S.sm, sl);
-                    else
-                        orth_small_kernel<double><<<1, kOrthThreads, osm, s>>>(S.V, L, j, S.sm, sl);
-                    count_launch();
-                    MB_CUDA_TRY(ctx, cudaGetLastError());
+                    // small system: preconditioner, matvec and the one-CTA
+                    // orthogonalisation, replayed as a CUDA graph once captured
+                    auto step = [&](cudaStream_t cs) -> mb_status {
+                        S.s = cs;
+                        precond_apply_packed(ctx, vj, zj, cs);
+                        const mb_status st = S.apply_A(zj, vn, inner);
+                        S.s = s;
+                        if (st != MB_OK) return st;
+                        const size_t osm = sizeof(double) * (4 * m + 3 + 32);
+                        if (inner == MB_FP32_KAHAN)
+                            orth_small_kernel<float><<<1, kOrthThreads, osm, cs>>>(S.V, L, j, S.sm, sl);
+                        else
+                            orth_small_kernel<double><<<1, kOrthThreads, osm, cs>>>(S.V, L, j, S.sm, sl);
+                        count_launch();
+                        MB_CUDA_TRY(ctx, cudaGetLastError());
+                        return MB_OK;
+                    };
+                    bool ran = false;
+                    if (!ctx->profiling) {
+                        IterSig sig;
+                        sig.gen = ctx->alloc_gen; sig.j = j; sig.m = m; sig.inner = (int)inner;
+                        sig.wall = p->wall; sig.variant = ctx->pair_variant;
+                        sig.pc_max_np = ctx->pc_max_np; sig.n = n; sig.nb = nb; sig.L = L;
+                        sig.pc_nb = ctx->pc_nb; sig.a = p->a; sig.eta = p->eta; sig.q = q;
+                        sig.V = S.V; sig.Z = S.Z; sig.sm = S.sm;
+                        MB_TRY(run_step_graph(ctx, graph_entry(ctx, sig), sig, step, s, &ran));
+                    }
+                    if (!ran) MB_TRY(step(s));
                     double est = 0.0;
                     MB_TRY(S.read_est(&est));
                     if (!(est > inner_abs)) break;
                     continue;
                 }
+                precond_apply_packed(ctx, vj, zj, s);
+                MB_TRY(S.apply_A(zj, vn, inner));
                 // CGS2
                 S.dots(S.V, j + 1, vn, S.sm + sl.h(), 0);
                 subtract_span_kernel<<<vg, 256, 0, s>>>(S.V, L, j + 1, S.sm + sl.h(), vn, L);

@@ -22,6 +22,37 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Everything a captured Arnoldi step of the single-problem solver bakes in:
+// the context's allocation generation (any workspace reallocation changes
+// it), the step index and sizes, the scalars of the kernels and the caller
+// and workspace pointers they read.
+struct IterSig {
+    uint64_t gen = 0;
+    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0;
+    int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
+    double a = 0.0, eta = 0.0;
+    const void *q = nullptr, *V = nullptr, *Z = nullptr, *sm = nullptr;
+    bool operator==(const IterSig &o) const
+    {
+        return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
+               variant == o.variant && pc_max_np == o.pc_max_np && n == o.n && nb == o.nb &&
+               L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
+               V == o.V && Z == o.Z && sm == o.sm;
+    }
+};
+
+// One Arnoldi step captured as a CUDA graph.  A step is captured the second
+// time it is met with the same signature (the first run sizes every buffer
+// and settles the autotuner) and replayed from then on.
+struct IterGraph {
+    IterSig sig;
+    bool seen = false;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;  // kernels in the graph (launch accounting)
+    uint64_t last_use = 0;   // for least-recently-used eviction
+};
+constexpr size_t kMaxIterGraphs = 256;  // cached steps per context
+
 }  // namespace mb
 
 struct mb_context {
@@ -53,6 +84,12 @@ struct mb_context {
     mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
     mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)
     void *host_small = nullptr;  // pinned host mirror of small scalars
+
+    uint64_t alloc_gen = 0;             // bumped by every workspace (re)allocation
+    std::vector<mb::IterGraph> iter_graphs;  // captured Arnoldi steps (any problem, any step)
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;       // private stream for captures (the caller's
+                                             // stream may be the legacy one)
 
     // FP32 pair-kernel variant: -1 = autotune per (size class, wall), else fixed
     int pair_variant = -1;

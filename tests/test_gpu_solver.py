@@ -217,6 +217,30 @@ def test_mixed_running_product_matches_fresh_residual(ctx, restart):
     assert abs(fresh - info["rel_residual"]) <= 0.2 * tol
 
 
+def test_repeated_and_interleaved_solves_replay_captured_steps(ctx):
+    """Small systems run each Arnoldi step as a CUDA graph from the second
+    time the step is met on: three rounds of two interleaved problems in
+    two precisions (record, capture, replay) agree with the first round to
+    well within the solve tolerance (the double-float product's atomics
+    make rounding differ from run to run)."""
+    probs = [I.config_small_suspension(1), I.mixed_suspension(5, 10)]
+    devs = [_dev_susp(s) for s in probs]
+    first = {}
+    for rnd in range(3):
+        for k, (s, d) in enumerate(zip(probs, devs)):
+            for prec in ("mixed", "fp64"):
+                U, W, lam, info = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"],
+                                                     d["F"], d["T"], s.a, s.eta, True, tol=1e-10,
+                                                     prec=prec)
+                assert info["converged"] == 1
+                got = (host(U), host(W), host(lam))
+                if rnd == 0:
+                    first[(k, prec)] = got
+                else:
+                    for x, y in zip(got, first[(k, prec)]):
+                        assert rel_l2(x, y) <= 1e-9
+
+
 def test_solve_fp32_small_suspension(ctx):
     _solve_and_compare(ctx, I.config_small_suspension(2), "fp32", 1e-6, 1e-5)
 
