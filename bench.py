@@ -86,6 +86,39 @@ def parse():
 
 
 # ------------------------------------------------------------------ helpers
+def max_over_ranks(dist, x: float, device="cpu") -> float:
+    """The largest of every rank's x (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(dist, units_local: float, seconds_local: float, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time.  Returns (rate, max seconds)."""
+    t_max = max_over_ranks(dist, seconds_local, device)
+    units = float(units_local)
+    if dist is not None:
+        import torch
+
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = float(u.item())
+    return units / t_max, t_max
+
+
+def shard(n_items: int, rank: int, world: int) -> range:
+    """Contiguous share of n_items independent problems for one rank (the
+    first n_items % world ranks take one more)."""
+    q, rem = divmod(n_items, world)
+    lo = rank * q + min(rank, rem)
+    return range(lo, lo + q + (1 if rank < rem else 0))
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -278,12 +311,9 @@ def run_ours(args):
     ctx.profile_enable(False)
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     t_local = step_ms / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    pairs = float(n) * float(n) * args.steps * world
-    value = pairs / t_max
+    pairs_local = float(n) * float(n) * args.steps
+    value, t_max = whole_job_rate(dist, pairs_local, t_local, device)
+    pairs = pairs_local * world
     kernel_avg_s = pair_ms / 1e3 / max(1, pair_launches)
     achieved = FLOPS_PER_PAIR * float(n) * n / kernel_avg_s / 1e12
 
@@ -299,10 +329,7 @@ def run_ours(args):
     for _ in range(args.steps):
         ctx.mobility_matvec(r_h, f_h, a, 1.0, True, args.prec, out=u_h)
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = pairs / float(te.item())
+    e2e_value, _ = whole_job_rate(dist, pairs_local, e2e_s, device)
 
     # ---- mobility solves of the small suspension (latency distribution)
     solve = None
@@ -318,7 +345,7 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_blobs": n, "precision":
@@ -464,7 +491,9 @@ def bench_batch(args):
     """256 independent mixed suspensions (42-blob shells and 15-blob
     boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
     to 1e-8; compared on a random subset with the plain FP64 path solving one
-    problem at a time, at the same tolerance."""
+    problem at a time, at the same tolerance.  Under torchrun the problems
+    are split into contiguous shares, one per rank (no collective on the data
+    path); the rate is all problems over the slowest rank's time."""
     import numpy as np
     import torch
 
@@ -473,22 +502,40 @@ def bench_batch(args):
     from paper_1602_02170_gb300 import build as B
     from paper_1602_02170_gb300 import inputs as I
 
+    rank, world, local = dist_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
     B.build()
-    ctx = mb.Context(0)
+    ctx = mb.Context(local)
     t0 = time.perf_counter()
     susp = I.config_batched(1)
     gen_s = time.perf_counter() - t0
-    probs = [_dev_problem(s) for s in susp]
+    mine = list(shard(len(susp), rank, world))
+    probs = {k: _dev_problem(susp[k]) for k in mine}
     a = susp[0].a
-    ctx.solve_batch(probs[:4], a, tol=1e-8, prec="mixed")  # warm-up
+    ctx.solve_batch([probs[k] for k in mine[:4]], a, tol=1e-8, prec="mixed")  # warm-up
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
-    res = ctx.solve_batch(probs, a, tol=1e-8, maxit=300, restart=60, prec="mixed")
+    res_list = ctx.solve_batch([probs[k] for k in mine], a, tol=1e-8, maxit=300, restart=60,
+                               prec="mixed")
     torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    iters = [r[3]["iters"] for r in res]
+    t_local = time.perf_counter() - t0
+    rate, t_batch = whole_job_rate(dist, len(mine), t_local, torch.device("cuda", local))
+    res = dict(zip(mine, res_list))
+    iters = [r[3]["iters"] for r in res_list]
+    if rank != 0:
+        dist.barrier()
+        ctx.close()
+        return 0
     rng = np.random.default_rng(5)
-    sub = sorted(rng.choice(len(susp), 8, replace=False).tolist())
+    sub = sorted(rng.choice(mine, min(8, len(mine)), replace=False).tolist())
     t0 = time.perf_counter()
     sub_batch = ctx.solve_batch([probs[k] for k in sub], a, tol=1e-8, prec="mixed")
     torch.cuda.synchronize()
@@ -513,18 +560,21 @@ def bench_batch(args):
     pairs = float(sum(s.n_blobs ** 2 for s in susp))
     line = {"metric": "mobility solves/s", "workload": "batched: 256 mixed suspensions "
             "(42-blob shells / 15-blob boomerangs, a=0.1625), bodies log-uniform 8..2048, "
-            "z in [1.2,3]", "value": len(susp) / t_batch, "unit": "solves/s", "seconds": t_batch,
+            "z in [1.2,3]", "value": rate, "unit": "solves/s", "seconds": t_batch,
             "tol": 1e-8, "prec": "mixed (fp32 + df64 residual), one batched launch per kernel",
             "n_blobs_total": int(sum(s.n_blobs for s in susp)),
             "n_bodies_total": int(sum(s.n_bodies for s in susp)),
-            "pairs_per_batched_matvec": pairs, "iters_median": float(np.median(iters)),
-            "iters_max": int(max(iters)), "generation_s": gen_s,
+            "pairs_per_batched_matvec": pairs, "iters_median_rank0": float(np.median(iters)),
+            "iters_max_rank0": int(max(iters)), "generation_s": gen_s,
             "subset": {"problems": sub, "batched_mixed_solves_per_s": len(sub) / t_sub_batch,
                        "fp64_one_at_a_time_solves_per_s": len(sub) / t_sub_fp64,
                        "max_rel_diff_U_batched_vs_fp64": diff,
                        "oracle_rel_err_U_small_problems": oracle_err},
-            "n_gpus": 1}
+            "n_gpus": world, "scaling": "strong",
+            "parallelism": "problems split across ranks" if world > 1 else "single GPU"}
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
     ctx.close()
     return 0
 
