@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--solves", type=int, default=30)
     p.add_argument("--solve-prec", default="mixed", choices=["mixed", "fp32", "fp64", "df64"],
                    help="precision of the --workload small solves")
+    p.add_argument("--precond", default="wall", choices=["wall", "free_shared"],
+                   help="block preconditioner of the --workload small / monolayer solves")
     p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve"],
                    default="matvec",
                    help="matvec: the benchmark line below; monolayer / batch / serve: the "
@@ -377,7 +379,7 @@ def run_ours(args):
     return 0
 
 
-def bench_solves(ctx, count, prec="mixed"):
+def bench_solves(ctx, count, prec="mixed", precond="wall"):
     """Mobility solves of the 8 x 42-blob suspension (tol 1e-10; 1e-6 for fp32)."""
     import numpy as np
     import torch
@@ -391,12 +393,12 @@ def bench_solves(ctx, count, prec="mixed"):
             s.eta, True)
     tol = 1e-6 if prec == "fp32" else 1e-10
     for _ in range(3):
-        ctx.solve_mobility(*args, tol=tol, prec=prec)
+        ctx.solve_mobility(*args, tol=tol, prec=prec, precond=precond)
     lat = []
     infos = []
     for _ in range(count):
         t0 = time.perf_counter()
-        U, W, lam, info = ctx.solve_mobility(*args, tol=tol, prec=prec)
+        U, W, lam, info = ctx.solve_mobility(*args, tol=tol, prec=prec, precond=precond)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0)
         infos.append(info)
@@ -405,7 +407,8 @@ def bench_solves(ctx, count, prec="mixed"):
     eU = float(np.linalg.norm(U.cpu().numpy() - Ur) / np.linalg.norm(Ur))
     eW = float(np.linalg.norm(W.cpu().numpy() - Wr) / np.linalg.norm(Wr))
     lat_ms = sorted(1e3 * x for x in lat)
-    return {"workload": f"8 x 42-blob shells above the wall (N=336), GMRES tol {tol:g}, {prec}",
+    return {"workload": f"8 x 42-blob shells above the wall (N=336), GMRES tol {tol:g}, {prec}, "
+                        f"{precond} preconditioner",
             "solves_per_s": count / sum(lat), "p50_ms": lat_ms[len(lat_ms) // 2],
             "p99_ms": lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)],
             "iters": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
@@ -422,7 +425,7 @@ def bench_small(args):
 
     B.build()
     ctx = mb.Context(0)
-    line = bench_solves(ctx, args.solves, args.solve_prec)
+    line = bench_solves(ctx, args.solves, args.solve_prec, args.precond)
     line.update({"metric": "mobility solves/s", "unit": "solves/s", "n_gpus": 1})
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -461,7 +464,7 @@ def bench_monolayer(args):
     t0 = time.perf_counter()
     U, W, lam, info = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"],
                                          P["T"], s.a, 1.0, True, tol=1e-8, maxit=300, restart=60,
-                                         prec="mixed")
+                                         prec="mixed", precond=args.precond)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     # fresh residual of the returned solution with one double-float product (untimed)
@@ -478,6 +481,7 @@ def bench_monolayer(args):
     line = {"metric": "mobility solves/s", "workload": "monolayer: 4096 x 162-blob shells, "
             "N=663552, a=0.12, 200x200 patch, z in [1.2,1.6]", "value": 1.0 / dt,
             "unit": "solves/s", "seconds": dt, "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)",
+            "precond": args.precond, "precond_bytes": ctx.workspace_bytes(),
             "info": info, "pairs_per_matvec": float(s.n_blobs) ** 2,
             "fresh_df64_rel_residual": fresh / bnorm,
             "oracle_sampled_residual_rows_max_over_bnorm": float(np.abs(res).max() / bnorm),

@@ -64,10 +64,27 @@ typedef enum {
 
 typedef struct mb_context mb_context;
 
+/* Block-diagonal preconditioner (Section 2.2.2).
+ *   MB_PRECOND_WALL         each body's own blob mobility block M^(pp),
+ *                           including the wall, factorised for every
+ *                           configuration (the default);
+ *   MB_PRECOND_FREE_SHARED  the blocks of an unbounded domain, which by the
+ *                           rotation and translation invariance of the RPY
+ *                           tensor depend only on the body's shape: one
+ *                           factorisation per shape (bodies with identical
+ *                           reference offsets rho), applied to each body by
+ *                           rotating the right-hand side into the reference
+ *                           frame and the result back (Section 2.2.2).  The
+ *                           wall is then left to the Krylov solver: the
+ *                           approximate preconditioner of Section 5.4. */
+typedef enum { MB_PRECOND_WALL = 0, MB_PRECOND_FREE_SHARED = 1 } mb_precond;
+
 /* Solver parameters.  tol is the target of ||b - A x||_2 / ||b||_2 for the
  * saddle-point system (Eq. saddle_M), measured with the FP64 pair kernel
  * (or FP32 when prec == MB_FP32_KAHAN).  maxit caps the total number of
- * Krylov iterations, restart the Krylov subspace size between restarts. */
+ * Krylov iterations, restart the Krylov subspace size between restarts.
+ * precond selects the preconditioner (mb_solve_mobility only; the batched
+ * and serving engines use MB_PRECOND_WALL and reject the other). */
 typedef struct {
     double a;
     double eta;
@@ -76,6 +93,7 @@ typedef struct {
     int maxit;
     int restart;
     mb_precision prec;
+    mb_precond precond;
 } mb_params;
 
 typedef struct {
@@ -249,7 +267,24 @@ mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, c
                            int wall, void *stream);
 
 /*
- * Apply the preconditioner set up by the last mb_precond_setup on ctx:
+ * Set up the shared unbounded-domain preconditioner (MB_PRECOND_FREE_SHARED)
+ * for n_b bodies given by their orientations theta (n_b x 4, unit
+ * quaternions, scalar first), blob_start (n_b + 1) and reference offsets rho
+ * (N x 3), all device arrays.  Bodies whose offsets are identical (same
+ * count, bitwise equal values) share one FP64 factorisation of their
+ * free-space block M^(pp) and 6 x 6 Schur complement (Section 2.2.2).  The
+ * orientations are copied, so the caller's arrays may change afterwards.
+ * Synchronises the stream.  MB_EINVAL for malformed blob_start, MB_ENOMEM
+ * beyond the context budget, MB_ESINGULAR if a shape's block is not positive
+ * definite (mb_last_error names a body of that shape).
+ */
+mb_status mb_precond_setup_shared(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                                  const double *theta, const int64_t *blob_start,
+                                  const double *rho, double a, double eta, void *stream);
+
+/*
+ * Apply the preconditioner set up by the last mb_precond_setup or
+ * mb_precond_setup_shared on ctx:
  * solve [[M~, -K], [-K^T, 0]] [lambda; UO] = [w; g] (Eq. saddle_M_precon)
  * body by body.  w, lambda: N x 3; g, UO: n_b x 6 (device).
  */

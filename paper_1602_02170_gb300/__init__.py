@@ -56,6 +56,7 @@ EXPORTED_SYMBOLS = [
     "mb_K_apply",
     "mb_KT_apply",
     "mb_precond_setup",
+    "mb_precond_setup_shared",
     "mb_precond_apply",
     "mb_solve_mobility",
     "mb_solve_batch",
@@ -89,7 +90,18 @@ class Params(ctypes.Structure):
         ("maxit", ctypes.c_int),
         ("restart", ctypes.c_int),
         ("prec", ctypes.c_int),
+        ("precond", ctypes.c_int),
     ]
+
+
+PRECOND_WALL, PRECOND_FREE_SHARED = 0, 1
+_PRECOND = {"wall": PRECOND_WALL, "free_shared": PRECOND_FREE_SHARED}
+
+
+def _precond(kind):
+    if isinstance(kind, str):
+        return _PRECOND[kind]
+    return int(kind)
 
 
 class Problem(ctypes.Structure):
@@ -167,6 +179,7 @@ def load_library():
     L.mb_K_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_KT_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_precond_setup.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, ci, vp]
+    L.mb_precond_setup_shared.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, vp]
     L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.mb_solve_mobility.argtypes = [
         vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
@@ -366,6 +379,17 @@ class Context:
                                             _ptr(blob_start), float(a), float(eta),
                                             int(bool(wall)), self._stream(stream)))
 
+    def precond_setup_shared(self, theta, blob_start, rho, a, eta=1.0, stream=None):
+        """Unbounded-domain block preconditioner shared by bodies of the same
+        shape (MB_PRECOND_FREE_SHARED), applied through each body's rotation."""
+        torch = self._torch
+        nb, n = int(theta.shape[0]), int(rho.shape[0])
+        self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        self._check(self.L.mb_precond_setup_shared(self.handle, nb, n, _ptr(theta),
+                                                   _ptr(blob_start), _ptr(rho), float(a),
+                                                   float(eta), self._stream(stream)))
+
     def precond_apply(self, w, g, stream=None):
         torch = self._torch
         lam = torch.empty_like(w)
@@ -377,8 +401,10 @@ class Context:
 
     def solve_mobility(self, q, theta, blob_start, rho, F, T, a, eta=1.0, wall=True, slip=None,
                        tol=1e-10, maxit=200, restart=100, prec="fp64", stream=None,
-                       raise_on_nonconvergence=True):
-        """Solve Eq. saddle_M; returns (U, Omega, lambda, info dict)."""
+                       raise_on_nonconvergence=True, precond="wall"):
+        """Solve Eq. saddle_M; returns (U, Omega, lambda, info dict).
+        precond: "wall" (per-body blocks with the wall) or "free_shared"
+        (unbounded-domain blocks, one per body shape)."""
         torch = self._torch
         nb, n = int(q.shape[0]), int(rho.shape[0])
         self._dev(q, (nb, 3)); self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
@@ -390,7 +416,7 @@ class Context:
         Om = torch.empty((nb, 3), dtype=torch.float64, device=q.device)
         lam = torch.empty((n, 3), dtype=torch.float64, device=q.device)
         p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
-                   _prec(prec))
+                   _prec(prec), _precond(precond))
         info = Info()
         st = self.L.mb_solve_mobility(
             self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(F),

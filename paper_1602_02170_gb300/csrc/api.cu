@@ -184,7 +184,7 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->stage_u, &ctx->pinv, &ctx->pinv_off, &ctx->blob_start_copy,
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
-                      &ctx->sol_dx, &ctx->sol_ym,
+                      &ctx->sol_dx, &ctx->sol_ym, &ctx->pc_type, &ctx->pc_theta, &ctx->pc_ref,
                       &ctx->batch_ws};
     for (auto &g : ctx->iter_graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -333,6 +333,18 @@ mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, c
                          (cudaStream_t)stream);
 }
 
+mb_status mb_precond_setup_shared(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                                  const double *theta, const int64_t *blob_start,
+                                  const double *rho, double a, double eta, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (n_bodies <= 0 || n_blobs <= 0) return set_err(ctx, MB_EINVAL, "need at least one body");
+    if (bad_phys(a, eta)) return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
+    if (!theta || !blob_start || !rho) return set_err(ctx, MB_EINVAL, "null array pointer");
+    return precond_setup_shared(ctx, n_bodies, n_blobs, theta, blob_start, rho, a, eta,
+                                (cudaStream_t)stream);
+}
+
 mb_status mb_precond_apply(mb_context *ctx, const double *w, const double *g, double *lambda,
                            double *UO, void *stream)
 {
@@ -357,6 +369,8 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
     if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
         params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
         return set_err(ctx, MB_EINVAL, "unknown precision mode");
+    if (params->precond != MB_PRECOND_WALL && params->precond != MB_PRECOND_FREE_SHARED)
+        return set_err(ctx, MB_EINVAL, "unknown preconditioner kind");
     if (!q || !theta || !blob_start || !rho || !F || !T || !U || !Omega || !lambda)
         return set_err(ctx, MB_EINVAL, "null array pointer");
     if (n_blobs > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
@@ -378,6 +392,8 @@ mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *prob
     if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
         params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
         return set_err(ctx, MB_EINVAL, "unknown precision mode");
+    if (params->precond != MB_PRECOND_WALL)
+        return set_err(ctx, MB_EINVAL, "the batched engine uses MB_PRECOND_WALL only");
     int64_t n_tot = 0;
     for (int p = 0; p < n_problems; ++p) {
         const mb_problem &P = problems[p];

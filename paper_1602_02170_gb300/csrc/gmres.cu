@@ -516,7 +516,10 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
 
     double *r = (double *)ctx->sol_r.ptr;
     MB_TRY(blob_positions(ctx, nb, n, q, theta, blob_start, rho, r, s));
-    MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s));
+    if (p->precond == MB_PRECOND_FREE_SHARED)
+        MB_TRY(precond_setup_shared(ctx, nb, n, theta, blob_start, rho, p->a, p->eta, s));
+    else
+        MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s));
     if (p->prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const auto t1 = clk::now();
@@ -619,7 +622,8 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                         IterSig sig;
                         sig.gen = ctx->alloc_gen; sig.j = j; sig.m = m; sig.inner = (int)inner;
                         sig.wall = p->wall; sig.variant = ctx->pair_variant;
-                        sig.pc_max_np = ctx->pc_max_np; sig.n = n; sig.nb = nb; sig.L = L;
+                        sig.pc_max_np = ctx->pc_max_np; sig.pc_kind = ctx->pc_kind;
+                        sig.n = n; sig.nb = nb; sig.L = L;
                         sig.pc_nb = ctx->pc_nb; sig.a = p->a; sig.eta = p->eta; sig.q = q;
                         sig.V = S.V; sig.Z = S.Z; sig.sm = S.sm;
                         MB_TRY(run_step_graph(ctx, graph_entry(ctx, sig), sig, step, s, &ran));

@@ -28,14 +28,15 @@ struct DevBuf {
 // and workspace pointers they read.
 struct IterSig {
     uint64_t gen = 0;
-    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0;
+    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0;
     int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
     double a = 0.0, eta = 0.0;
     const void *q = nullptr, *V = nullptr, *Z = nullptr, *sm = nullptr;
     bool operator==(const IterSig &o) const
     {
         return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
-               variant == o.variant && pc_max_np == o.pc_max_np && n == o.n && nb == o.nb &&
+               variant == o.variant && pc_max_np == o.pc_max_np && pc_kind == o.pc_kind &&
+               n == o.n && nb == o.nb &&
                L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
                V == o.V && Z == o.Z && sm == o.sm;
     }
@@ -67,13 +68,20 @@ struct mb_context {
     mb::DevBuf partial;          // per-source-chunk partial velocities (FP64)
     mb::DevBuf stage_r, stage_f, stage_u;  // staging for host-pointer calls
 
-    // preconditioner (last mb_precond_setup)
-    mb::DevBuf pinv;             // per-body explicit inverse, (3n_p+6)^2 doubles
-    mb::DevBuf pinv_off;         // int64 offsets into pinv, n_b + 1
+    // preconditioner (last mb_precond_setup / mb_precond_setup_shared)
+    mb::DevBuf pinv;             // explicit inverses, (3n_p+6)^2 doubles each: one per
+                                 // body (wall kind) or one per body shape (shared kind)
+    mb::DevBuf pinv_off;         // int64 offsets into pinv (bodies or shapes, + 1)
     mb::DevBuf blob_start_copy;  // int64 copy of blob_start used by apply
     mb::DevBuf flag;             // int status flags written by kernels
+    mb::DevBuf pc_type;          // shared kind: int shape index of every body
+    mb::DevBuf pc_theta;         // shared kind: copy of the bodies' quaternions
+    mb::DevBuf pc_ref;           // shared kind: reference positions, zero centres,
+                                 // CSR offsets of the shapes (setup input)
     int64_t pc_nb = 0, pc_n = 0;
     int pc_max_np = 0;
+    int pc_kind = 0;             // mb_precond of the current blocks
+    int64_t pc_shapes = 0;       // shared kind: distinct shapes
 
     // solver workspace
     mb::DevBuf sol_r;            // blob positions
@@ -143,6 +151,10 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
                               const int64_t *start, const int64_t *poff, double *P, int max_np,
                               double a, double eta, int wall, int *flags, int flag_slot,
                               cudaStream_t s);
+// Shared unbounded-domain blocks, one per body shape (precond.cu).
+mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const double *theta,
+                               const int64_t *blob_start, const double *rho, double a,
+                               double eta, cudaStream_t s);
 // z = P^-1 v where v = [w (3N); g (6 n_b)] packed contiguously, same for z.
 void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s);
 

@@ -13,6 +13,8 @@
 //     P_p^-1 = [[M_p^-1 - Q_p N_p Q_p^T, -Q_p N_p], [-N_p Q_p^T, -N_p]],
 // so that one application is one batched FP64 GEMV per body.
 #include <algorithm>
+#include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "mb_internal.cuh"
@@ -663,6 +665,73 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
     return MB_OK;
 }
 
+// Shared unbounded-domain preconditioner (MB_PRECOND_FREE_SHARED).  The
+// free-space block of a body rotated by R is R~ M_ref R~^T, R~ = diag(R, ..,
+// R), and K_p = R~ K_ref diag(R^T, R^T) blob by blob (K_ref from the
+// reference offsets), so the whole indefinite block inverse is
+// diag(R~, R, R) P_ref^-1 diag(R~, R, R)^T (Section 2.2.2).  Work items are
+// (body, chunk of rows) like precond_apply_kernel; rows come in whole
+// triples so that each CTA rotates its own results back.
+__device__ __forceinline__ void quat_matrix(const double *__restrict__ th, double R[9])
+{
+    double s = th[0], x = th[1], y = th[2], z = th[3];
+    const double inv = rsqrt(s * s + x * x + y * y + z * z);
+    s *= inv; x *= inv; y *= inv; z *= inv;
+    // R = (s^2 - v.v) I + 2 v v^T + 2 s [v]x
+    const double d = s * s - (x * x + y * y + z * z);
+    R[0] = d + 2.0 * x * x;     R[1] = 2.0 * x * y - 2.0 * s * z; R[2] = 2.0 * x * z + 2.0 * s * y;
+    R[3] = 2.0 * y * x + 2.0 * s * z; R[4] = d + 2.0 * y * y;     R[5] = 2.0 * y * z - 2.0 * s * x;
+    R[6] = 2.0 * z * x - 2.0 * s * y; R[7] = 2.0 * z * y + 2.0 * s * x; R[8] = d + 2.0 * z * z;
+}
+
+__global__ void __launch_bounds__(256) precond_apply_shared_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int *__restrict__ shape,
+    const int64_t *__restrict__ poff, const double *__restrict__ P,
+    const double *__restrict__ theta, const double *__restrict__ w, const double *__restrict__ g,
+    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows)
+{
+    extern __shared__ double xs[];  // m rotated inputs, then `rows` results
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t item = blockIdx.x; item < nb * chunks; item += gridDim.x) {
+        const int64_t p = item / chunks;
+        const int r0 = (int)(item % chunks) * rows;
+        const int64_t b0 = start[p];
+        const int np = (int)(start[p + 1] - b0), n = 3 * np, m = n + 6;
+        const int r1 = min(m, r0 + rows);
+        if (r0 >= m) continue;  // uniform over the CTA
+        double R[9];
+        quat_matrix(theta + 4 * p, R);
+        double *ys = xs + m;
+        __syncthreads();
+        // x = diag(R~, R, R)^T [w_p; g_p], one triple per thread
+        for (int t = threadIdx.x; t < m / 3; t += blockDim.x) {
+            const double *v = t < np ? w + 3 * (b0 + t) : g + 6 * p + 3 * (t - np);
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+                xs[3 * t + al] = R[al] * v[0] + R[3 + al] * v[1] + R[6 + al] * v[2];
+        }
+        __syncthreads();
+        const double *Pp = P + poff[shape[p]];
+        for (int row = r0 + warp; row < r1; row += nw) {
+            const double *pr = Pp + (size_t)row * m;
+            double acc = 0.0;
+            for (int c = lane; c < m; c += 32) acc += pr[c] * xs[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) ys[row - r0] = acc;
+        }
+        __syncthreads();
+        // rotate the triples of this chunk back
+        for (int t = r0 / 3 + threadIdx.x; t < r1 / 3; t += blockDim.x) {
+            const double *y = ys + 3 * t - r0;
+            double *out = t < np ? lam + 3 * (b0 + t) : UO + 6 * p + 3 * (t - np);
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+                out[al] = R[3 * al] * y[0] + R[3 * al + 1] * y[1] + R[3 * al + 2] * y[2];
+        }
+    }
+}
+
 }  // namespace
 
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
@@ -740,6 +809,8 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     ctx->pc_nb = nb;
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
+    ctx->pc_kind = MB_PRECOND_WALL;
+    ctx->pc_shapes = 0;
     if (first_bad != big) {
         ctx->pc_nb = 0;
         return set_err(ctx, MB_ESINGULAR,
@@ -788,6 +859,121 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
                  : launch(precond_setup_kernel<false, false>);
 }
 
+mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const double *theta,
+                               const int64_t *blob_start, const double *rho, double a,
+                               double eta, cudaStream_t s)
+{
+    // offsets and reference positions on the host, to group bodies by shape
+    std::vector<int64_t> hstart(nb + 1);
+    std::vector<double> hrho(3 * (size_t)n);
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(hstart.data(), blob_start, sizeof(int64_t) * (nb + 1),
+                                     cudaMemcpyDeviceToHost, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * 3 * (size_t)n,
+                                     cudaMemcpyDeviceToHost, s));
+    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hstart[0] != 0 || hstart[nb] != n)
+        return set_err(ctx, MB_EINVAL, "blob_start[0] must be 0 and blob_start[n_b] = N");
+    // shape of every body: bodies with the same blob count and bitwise equal
+    // offsets share one (an FNV-style hash over the 64-bit words, confirmed
+    // by comparison)
+    std::vector<int> shape(nb);
+    std::vector<int64_t> rep_body;                 // first body of each shape
+    std::unordered_map<uint64_t, std::vector<int>> by_hash;
+    int max_np = 0;
+    for (int64_t p = 0; p < nb; ++p) {
+        const int64_t np = hstart[p + 1] - hstart[p];
+        if (np < 1) return set_err(ctx, MB_EINVAL, "body %lld has no blobs", (long long)p);
+        max_np = std::max<int>(max_np, (int)np);
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)np;
+        for (int64_t e = 3 * hstart[p]; e < 3 * hstart[p + 1]; ++e) {
+            uint64_t bits;
+            std::memcpy(&bits, &hrho[e], sizeof(bits));
+            h = (h ^ bits) * 1099511628211ull;
+            h ^= h >> 29;
+        }
+        int found = -1;
+        for (int t : by_hash[h]) {
+            const int64_t q0 = rep_body[t];
+            if (hstart[q0 + 1] - hstart[q0] == np &&
+                std::memcmp(hrho.data() + 3 * hstart[q0], hrho.data() + 3 * hstart[p],
+                            sizeof(double) * 3 * (size_t)np) == 0) {
+                found = t;
+                break;
+            }
+        }
+        if (found < 0) {
+            found = (int)rep_body.size();
+            rep_body.push_back(p);
+            by_hash[h].push_back(found);
+        }
+        shape[p] = found;
+    }
+    const int64_t ns = (int64_t)rep_body.size();
+    // reference bodies: positions rho, centre 0, identity orientation
+    std::vector<int64_t> rstart(ns + 1), off(ns + 1);
+    rstart[0] = 0;
+    off[0] = 0;
+    for (int64_t t = 0; t < ns; ++t) {
+        const int64_t np = hstart[rep_body[t] + 1] - hstart[rep_body[t]];
+        rstart[t + 1] = rstart[t] + np;
+        off[t + 1] = off[t] + (3 * np + 6) * (3 * np + 6);
+    }
+    std::vector<double> ref(3 * (size_t)rstart[ns] + 3 * (size_t)ns, 0.0);
+    for (int64_t t = 0; t < ns; ++t)
+        std::memcpy(ref.data() + 3 * rstart[t], hrho.data() + 3 * hstart[rep_body[t]],
+                    sizeof(double) * 3 * (size_t)(rstart[t + 1] - rstart[t]));
+    const size_t ref_doubles = ref.size();
+    MB_TRY(ensure(ctx, ctx->pc_ref, sizeof(double) * ref_doubles + sizeof(int64_t) * 2 * (ns + 1),
+                  "preconditioner reference bodies"));
+    MB_TRY(ensure(ctx, ctx->pinv, sizeof(double) * off[ns], "preconditioner"));
+    MB_TRY(ensure(ctx, ctx->pinv_off, sizeof(int64_t) * (ns + 1), "preconditioner"));
+    MB_TRY(ensure(ctx, ctx->blob_start_copy, sizeof(int64_t) * (nb + 1), "preconditioner"));
+    MB_TRY(ensure(ctx, ctx->pc_type, sizeof(int) * nb, "preconditioner shapes"));
+    MB_TRY(ensure(ctx, ctx->pc_theta, sizeof(double) * 4 * nb, "preconditioner orientations"));
+    MB_TRY(ensure(ctx, ctx->flag, sizeof(int) * 4, "flags"));
+    double *dref = (double *)ctx->pc_ref.ptr;
+    int64_t *dstart = (int64_t *)(dref + ref_doubles);
+    int64_t *doff = dstart + (ns + 1);
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(dref, ref.data(), sizeof(double) * ref_doubles,
+                                     cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(dstart, rstart.data(), sizeof(int64_t) * (ns + 1),
+                                     cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (ns + 1),
+                                     cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pinv_off.ptr, off.data(), sizeof(int64_t) * (ns + 1),
+                                     cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->blob_start_copy.ptr, hstart.data(),
+                                     sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pc_type.ptr, shape.data(), sizeof(int) * nb,
+                                     cudaMemcpyHostToDevice, s));
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->pc_theta.ptr, theta, sizeof(double) * 4 * nb,
+                                     cudaMemcpyDeviceToDevice, s));
+    const int big = 0x7fffffff;
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->flag.ptr, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+    int max_ref_np = 0;
+    for (int64_t t = 0; t < ns; ++t)
+        max_ref_np = std::max<int>(max_ref_np, (int)(rstart[t + 1] - rstart[t]));
+    MB_TRY(precond_setup_range(ctx, ns, dref, dref + 3 * rstart[ns], dstart, doff,
+                               (double *)ctx->pinv.ptr, max_ref_np, a, eta, 0,
+                               (int *)ctx->flag.ptr, -1, s));
+    int first_bad = big;
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(&first_bad, ctx->flag.ptr, sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    ctx->pc_nb = nb;
+    ctx->pc_n = n;
+    ctx->pc_max_np = max_np;
+    ctx->pc_kind = MB_PRECOND_FREE_SHARED;
+    ctx->pc_shapes = ns;
+    if (first_bad != big) {
+        ctx->pc_nb = 0;
+        return set_err(ctx, MB_ESINGULAR,
+                       "body %lld: free-space block of its shape or its Schur complement is not "
+                       "positive definite", (long long)rep_body[first_bad]);
+    }
+    return MB_OK;
+}
+
 static void precond_apply_impl(mb_context *ctx, const double *w, const double *g, double *lam,
                                double *UO, cudaStream_t s)
 {
@@ -795,8 +981,17 @@ static void precond_apply_impl(mb_context *ctx, const double *w, const double *g
     // few bodies: split each body's rows so that about two CTAs per SM have work
     const int64_t want = ceil_div(2 * (int64_t)ctx->sm_count, ctx->pc_nb);
     const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ceil_div(m, 8)));
-    const int rows = (int)ceil_div(m, chunks);
     const int grid = (int)std::min<int64_t>(ctx->pc_nb * chunks, 8 * (int64_t)ctx->sm_count);
+    if (ctx->pc_kind == MB_PRECOND_FREE_SHARED) {
+        const int rows = 3 * (int)ceil_div(m / 3, chunks);  // whole triples
+        precond_apply_shared_kernel<<<grid, 256, sizeof(double) * (m + rows), s>>>(
+            ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int *)ctx->pc_type.ptr,
+            (const int64_t *)ctx->pinv_off.ptr, (const double *)ctx->pinv.ptr,
+            (const double *)ctx->pc_theta.ptr, w, g, lam, UO, chunks, rows);
+        count_launch();
+        return;
+    }
+    const int rows = (int)ceil_div(m, chunks);
     precond_apply_kernel<<<grid, 256, sizeof(double) * m, s>>>(
         ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int64_t *)ctx->pinv_off.ptr,
         (const double *)ctx->pinv.ptr, w, g, lam, UO, chunks, rows);

@@ -1588,6 +1588,8 @@ mb_status mb_server_create(mb_context *ctx, const mb_params *params,
     if (!(params->a > 0.0) || !(params->eta > 0.0) || !(params->tol > 0.0) || params->maxit < 1 ||
         params->restart < 1 || params->prec < MB_FP64 || params->prec > MB_DF64)
         return set_err(ctx, MB_EINVAL, "bad solver parameters");
+    if (params->precond != MB_PRECOND_WALL)
+        return set_err(ctx, MB_EINVAL, "the serving engine uses MB_PRECOND_WALL only");
     if (limits->max_blobs < 1 || limits->max_bodies < 1 || limits->max_precond_bytes < 8 ||
         limits->max_requests < 1 || limits->max_requests > (1 << 20))
         return set_err(ctx, MB_EINVAL, "bad server limits");
