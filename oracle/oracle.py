@@ -22,6 +22,9 @@ Functions and the passages they follow:
   precond_apply                     Eq. saddle_M_precon with the block-diagonal
                                     mobility of Eq. M_tilde_block_diag, one
                                     body at a time, solved directly (LU)
+  solve_resistance                  Eq. resistance_problem: M lambda = K U + slip
+                                    by Cholesky, then (F, T) = K^T lambda
+                                    (Section 2.1.2)
   residual_rows                     rows of Eq. saddle_M's residual for chosen
                                     blobs, for sampled checks at large N
 """
@@ -252,6 +255,21 @@ def solve_schur(r, q, blob_start, F, T, a, eta=1.0, wall=True, slip=None):
     lam = sl.cho_solve(cM, K @ UO + s)
     UO = UO.reshape(nb, 6)
     return UO[:, :3].copy(), UO[:, 3:].copy(), lam.reshape(n, 3)
+
+
+def solve_resistance(r, q, blob_start, U, Omega, a, eta=1.0, wall=True, slip=None):
+    """Eq. resistance_problem: the blob forces lambda with M lambda = K [U; Omega]
+    + slip, by Cholesky of the dense M, and the body forces and torques
+    (F, T) = K^T lambda they add up to.  Returns (F, T, lambda)."""
+    import scipy.linalg as sl
+
+    n = r.shape[0]
+    M = mobility_matrix(r, a, eta, wall)
+    K = K_matrix(r, q, blob_start)
+    s = np.zeros(3 * n) if slip is None else _c(slip).reshape(-1)
+    lam = sl.cho_solve(sl.cho_factor(M, lower=True), K @ _body_vec(U, Omega) + s)
+    FT = (K.T @ lam).reshape(-1, 6)
+    return FT[:, :3].copy(), FT[:, 3:].copy(), lam.reshape(n, 3)
 
 
 def body_mobility(r, q, blob_start, a, eta=1.0, wall=True):

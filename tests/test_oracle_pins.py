@@ -268,3 +268,56 @@ def test_matvec_equals_dense_product():
     np.testing.assert_allclose(u.reshape(-1), M @ f.reshape(-1), rtol=1e-13, atol=1e-15)
     t = np.array([5, 0, 199, 17])
     np.testing.assert_allclose(O.matvec(r, f, 0.5, targets=t), u[t], rtol=1e-14)
+
+
+# ------------------------------------------------------------ resistance problem
+def test_resistance_of_isotropic_shell_matches_effective_radii():
+    """Eq. resistance_problem for one 12-blob shell in an unbounded domain:
+    the icosahedral symmetry makes its resistance isotropic, so translating
+    at U needs F = 6 pi eta R_h U and rotating at Omega needs
+    T = 8 pi eta R_tau^3 Omega, with R_h and R_tau of Table Stresslets_3D."""
+    g = json.load(open(os.path.join(GOLDEN, "effective_radii.json")))
+    for n, ratio, rh_ref, rt_ref in g["rows"]:
+        if n != 12:
+            continue
+        rho = I.shell(12)
+        a = ratio * I.min_spacing(rho)
+        q = np.zeros((1, 3))
+        for axis in range(3):
+            e = np.zeros((1, 3))
+            e[0, axis] = 1.0
+            F, T, _ = O.solve_resistance(rho, q, np.array([0, 12]), e, np.zeros((1, 3)), a, 1.0,
+                                         wall=False)
+            assert abs(F[0, axis] / (6 * PI) - rh_ref) <= 1.5e-4
+            assert np.abs(np.delete(F[0], axis)).max() <= 1e-12 and np.abs(T).max() <= 1e-12
+            F, T, _ = O.solve_resistance(rho, q, np.array([0, 12]), np.zeros((1, 3)), e, a, 1.0,
+                                         wall=False)
+            assert abs((T[0, axis] / (8 * PI)) ** (1 / 3) - rt_ref) <= 1.5e-4
+            assert np.abs(np.delete(T[0], axis)).max() <= 1e-12 and np.abs(F).max() <= 1e-12
+
+
+def test_resistance_inverts_the_mobility_problem():
+    """Section 2.1.2: the body resistance R = K^T M^-1 K is the inverse of the
+    body mobility N.  Solving the mobility problem for (U, Omega) under given
+    (F, T) and slip, then the resistance problem with that motion and slip,
+    returns the forces and torques and the same blob forces."""
+    s = I.mixed_suspension(11, 4)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    slip = _rng(3).standard_normal((s.n_blobs, 3)) * 0.2
+    U, W, lam = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True, slip)
+    F, T, lam2 = O.solve_resistance(r, s.q, s.blob_start, U, W, s.a, 1.0, True, slip)
+    np.testing.assert_allclose(F, s.F, rtol=0, atol=1e-9 * np.abs(s.F).max())
+    np.testing.assert_allclose(T, s.T, rtol=0, atol=1e-9 * np.abs(s.F).max())
+    np.testing.assert_allclose(lam2, lam, rtol=0, atol=1e-9 * np.abs(lam).max())
+
+
+def test_resistance_rigid_slip_cancels_motion():
+    """A slip equal to minus a rigid motion of the bodies, with the bodies
+    moving by that motion, leaves the fluid at rest: lambda = 0, F = T = 0."""
+    s = I.config_small_suspension(2)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = _rng(4)
+    V, Wv = rng.standard_normal((s.n_bodies, 3)), rng.standard_normal((s.n_bodies, 3))
+    slip = -O.K_apply(V, Wv, r, s.q, s.blob_start)
+    F, T, lam = O.solve_resistance(r, s.q, s.blob_start, V, Wv, s.a, 1.0, True, slip)
+    assert np.abs(lam).max() <= 1e-12 and np.abs(F).max() <= 1e-12 and np.abs(T).max() <= 1e-12
