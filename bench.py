@@ -74,7 +74,8 @@ def parse():
                    help="precision of the --workload small solves")
     p.add_argument("--precond", default="wall", choices=["wall", "free_shared"],
                    help="block preconditioner of the --workload small / monolayer solves")
-    p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve"],
+    p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve",
+                                          "resistance"],
                    default="matvec",
                    help="matvec: the benchmark line below; monolayer / batch / serve: the "
                         "663,552-blob monolayer solve, 256 batched suspensions, and the "
@@ -491,6 +492,61 @@ def bench_monolayer(args):
     return 0
 
 
+def bench_resistance(args):
+    """Iterations and time of the resistance problem (Eq. resistance_problem)
+    beside the mobility problem, for growing suspensions of 42-blob shells in
+    an unbounded domain at volume fraction 0.1 (mixed precision, tol 1e-8).
+    Section 4.3 reports resistance iterations growing like N^(1/3) while the
+    mobility problem's stay flat; the fitted exponent is printed."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    a, R, phi = 0.243, 1.0, 0.1
+    rows = []
+    for nb in (8, 64, 512, 2048):
+        box = (nb * 4.0 / 3.0 * math.pi * (R + a) ** 3 / phi) ** (1.0 / 3.0)
+        s = I.sphere_suspension(17 + nb, nb, 42, a, box, R + a + 0.05, R + a + 0.05 + box)
+        P = _dev_problem(s)
+        rng = np.random.default_rng(nb)
+        U = torch.as_tensor(rng.standard_normal((nb, 3))).cuda()
+        W = torch.as_tensor(0.5 * rng.standard_normal((nb, 3))).cuda()
+        row = {"n_bodies": nb, "n_blobs": int(s.n_blobs)}
+        for kind in ("mobility", "resistance"):
+            def run():
+                if kind == "mobility":
+                    return ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"],
+                                              P["F"], P["T"], a, 1.0, False, tol=1e-8,
+                                              maxit=2000, restart=100, prec="mixed")
+                return ctx.solve_resistance(P["q"], P["theta"], P["blob_start"], P["rho"], U, W, a,
+                                            1.0, False, tol=1e-8, maxit=2000, restart=100,
+                                            prec="mixed")
+            run()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = run()
+            torch.cuda.synchronize()
+            row[kind] = {"iters": out[3]["iters"], "restarts": out[3]["restarts"],
+                         "seconds": time.perf_counter() - t0,
+                         "rel_residual": out[3]["rel_residual"]}
+        rows.append(row)
+    n = np.array([r["n_blobs"] for r in rows], dtype=float)
+    fit = {k: float(np.polyfit(np.log(n), np.log([r[k]["iters"] for r in rows]), 1)[0])
+           for k in ("mobility", "resistance")}
+    line = {"metric": "GMRES iterations vs N, resistance and mobility problems",
+            "workload": "42-blob shells (a=0.243) in an unbounded domain, volume fraction 0.1, "
+                        "mixed precision, tol 1e-8, restart 100",
+            "rows": rows, "fitted_exponent_iters_vs_N": fit, "n_gpus": 1}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def bench_batch(args):
     """256 independent mixed suspensions (42-blob shells and 15-blob
     boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
@@ -681,6 +737,8 @@ def main():
         return run_reference(args)
     if args.workload == "small":
         return bench_small(args)
+    if args.workload == "resistance":
+        return bench_resistance(args)
     if args.workload == "monolayer":
         return bench_monolayer(args)
     if args.workload == "batch":

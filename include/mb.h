@@ -314,6 +314,30 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
                             const mb_params *params, double *U, double *Omega, double *lambda,
                             mb_info *info, void *stream);
 
+/*
+ * Solve the resistance problem (Eq. resistance_problem):
+ *   M lambda = K [U; Omega] + slip,   (F, T) = K^T lambda,
+ * for the blob forces lambda that move the bodies rigidly with prescribed
+ * velocities (U, Omega), and the forces and torques they add up to
+ * (F = R U + R~ slip of Section 2.1.2).  Right-preconditioned GMRES on M with
+ * the block-diagonal preconditioner of the blob blocks M^(pp)^-1 (per body
+ * with the wall, or shared per shape without it: params->precond); mixed
+ * precision refines like mb_solve_mobility.  The iteration count grows with
+ * the linear size of the suspension, unlike the mobility problem's
+ * (Section 4.3).
+ *
+ *   q, theta, blob_start, rho : bodies (device; see mb_blob_positions)
+ *   U, Omega : n_b x 3 prescribed velocities (device)
+ *   slip     : N x 3 apparent slip or NULL
+ *   F, T     : n_b x 3 outputs; lambda: N x 3 output (device)
+ * Synchronises the stream; errors as mb_solve_mobility.
+ */
+mb_status mb_solve_resistance(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                              const double *q, const double *theta, const int64_t *blob_start,
+                              const double *rho, const double *U, const double *Omega,
+                              const double *slip, const mb_params *params, double *F, double *T,
+                              double *lambda, mb_info *info, void *stream);
+
 /* One independent problem of a batch (all pointers device pointers; layout
  * as for mb_solve_mobility; slip may be NULL). */
 typedef struct {

@@ -59,6 +59,7 @@ EXPORTED_SYMBOLS = [
     "mb_precond_setup_shared",
     "mb_precond_apply",
     "mb_solve_mobility",
+    "mb_solve_resistance",
     "mb_solve_batch",
     "mb_server_create",
     "mb_server_destroy",
@@ -182,6 +183,10 @@ def load_library():
     L.mb_precond_setup_shared.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, vp]
     L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.mb_solve_mobility.argtypes = [
+        vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
+        ctypes.POINTER(Info), vp,
+    ]
+    L.mb_solve_resistance.argtypes = [
         vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
         ctypes.POINTER(Info), vp,
     ]
@@ -426,6 +431,32 @@ class Context:
             return U, Om, lam, info.as_dict()
         self._check(st)
         return U, Om, lam, info.as_dict()
+
+    def solve_resistance(self, q, theta, blob_start, rho, U, Omega, a, eta=1.0, wall=True,
+                         slip=None, tol=1e-10, maxit=500, restart=100, prec="fp64", stream=None,
+                         raise_on_nonconvergence=True, precond="wall"):
+        """Solve Eq. resistance_problem; returns (F, T, lambda, info dict)."""
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(rho.shape[0])
+        self._dev(q, (nb, 3)); self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
+        self._dev(U, (nb, 3)); self._dev(Omega, (nb, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if slip is not None:
+            self._dev(slip, (n, 3))
+        F = torch.empty((nb, 3), dtype=torch.float64, device=q.device)
+        T = torch.empty((nb, 3), dtype=torch.float64, device=q.device)
+        lam = torch.empty((n, 3), dtype=torch.float64, device=q.device)
+        p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
+                   _prec(prec), _precond(precond))
+        info = Info()
+        st = self.L.mb_solve_resistance(
+            self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(U),
+            _ptr(Omega), _ptr(slip), ctypes.byref(p), _ptr(F), _ptr(T), _ptr(lam),
+            ctypes.byref(info), self._stream(stream))
+        if st == 4 and not raise_on_nonconvergence:
+            return F, T, lam, info.as_dict()
+        self._check(st)
+        return F, T, lam, info.as_dict()
 
     def solve_batch(self, problems, a, eta=1.0, wall=True, tol=1e-10, maxit=200, restart=100,
                     prec="mixed", stream=None, raise_on_nonconvergence=True):

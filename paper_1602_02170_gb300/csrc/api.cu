@@ -378,6 +378,31 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
                           Omega, lambda, info, (cudaStream_t)stream);
 }
 
+mb_status mb_solve_resistance(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                              const double *q, const double *theta, const int64_t *blob_start,
+                              const double *rho, const double *U, const double *Omega,
+                              const double *slip, const mb_params *params, double *F, double *T,
+                              double *lambda, mb_info *info, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (!params) return set_err(ctx, MB_EINVAL, "null params");
+    if (n_bodies <= 0 || n_blobs <= 0) return set_err(ctx, MB_EINVAL, "need at least one body");
+    if (bad_phys(params->a, params->eta))
+        return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
+    if (!(params->tol > 0.0) || params->maxit < 1 || params->restart < 1)
+        return set_err(ctx, MB_EINVAL, "tol > 0, maxit >= 1 and restart >= 1 required");
+    if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
+        params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
+        return set_err(ctx, MB_EINVAL, "unknown precision mode");
+    if (params->precond != MB_PRECOND_WALL && params->precond != MB_PRECOND_FREE_SHARED)
+        return set_err(ctx, MB_EINVAL, "unknown preconditioner kind");
+    if (!q || !theta || !blob_start || !rho || !U || !Omega || !F || !T || !lambda)
+        return set_err(ctx, MB_EINVAL, "null array pointer");
+    if (n_blobs > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
+    return solve_resistance(ctx, n_bodies, n_blobs, q, theta, blob_start, rho, U, Omega, slip,
+                            params, F, T, lambda, info, (cudaStream_t)stream);
+}
+
 mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *problems,
                          const mb_params *params, mb_info *infos, void *stream)
 {

@@ -343,8 +343,47 @@ __global__ void unpack_solution_kernel(int64_t n, int64_t nb, const double *__re
     }
 }
 
+// b = K [U; Omega] + slip on the blobs (resistance right-hand side)
+__global__ void build_rhs_resist_kernel(int64_t nb, int64_t n, const double *__restrict__ r,
+                                        const double *__restrict__ q,
+                                        const int64_t *__restrict__ start,
+                                        const double *__restrict__ U,
+                                        const double *__restrict__ Om,
+                                        const double *__restrict__ slip, double *__restrict__ b)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nb;  // body of blob i: start[lo] <= i < start[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (start[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const double dx = r[3 * i] - q[3 * lo], dy = r[3 * i + 1] - q[3 * lo + 1],
+                     dz = r[3 * i + 2] - q[3 * lo + 2];
+        const double *u = U + 3 * lo, *w = Om + 3 * lo;
+        const double v[3] = {u[0] + (w[1] * dz - w[2] * dy), u[1] + (w[2] * dx - w[0] * dz),
+                             u[2] + (w[0] * dy - w[1] * dx)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) b[3 * i + c] = v[c] + (slip ? slip[3 * i + c] : 0.0);
+    }
+}
+
+// F, T from the packed n_b x 6 K^T lambda
+__global__ void split_ft_kernel(int64_t nb, const double *__restrict__ FT, double *__restrict__ F,
+                                double *__restrict__ T)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 6 * nb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / 6, c = e % 6;
+        if (c < 3) F[3 * p + c] = FT[e];
+        else T[3 * p + c - 3] = FT[e];
+    }
+}
+
 struct Solver {
     mb_context *ctx;
+    bool resist = false;  // A = M alone (resistance problem), L = 3N
     cudaStream_t s;
     int64_t n, nb, L;
     const double *r, *q;
@@ -360,6 +399,7 @@ struct Solver {
     mb_status apply_A(const double *xin, double *y, mb_precision prec)
     {
         MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s));
+        if (resist) return MB_OK;
         launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
         launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
         MB_CUDA_TRY(ctx, cudaGetLastError());
@@ -373,10 +413,18 @@ struct Solver {
         MB_TRY(matvec_packed(ctx, r, dx, n, a, eta, wall, prec, y, s));
         accumulate_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, ym, 3 * n);
         count_launch();
+        if (resist) return MB_OK;
         launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
         launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
+    }
+
+    // z = P^-1 v (the indefinite blocks, or the blob blocks alone)
+    void precond(const double *v, double *z, cudaStream_t cs)
+    {
+        if (resist) precond_apply_blobs(ctx, v, z, cs);
+        else precond_apply_packed(ctx, v, z, cs);
     }
 
     // out[0..nk) = V[0..nk) . w  (accumulate: out += ...)
@@ -486,16 +534,19 @@ mb_status run_step_graph(mb_context *ctx, IterGraph &g, const IterSig &sig, Step
 
 }  // namespace
 
-mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
-                         const double *theta, const int64_t *blob_start, const double *rho,
-                         const double *F, const double *T, const double *slip,
-                         const mb_params *p, double *U, double *Omega, double *lambda,
-                         mb_info *info, cudaStream_t s)
+// Mobility problem (resist = 0): inputs in_a, in_b = F, T; outputs out_a,
+// out_b = U, Omega.  Resistance problem (resist = 1): inputs U, Omega;
+// outputs F, T.  lambda is the blob-force output of both.
+static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n, const double *q,
+                             const double *theta, const int64_t *blob_start, const double *rho,
+                             const double *in_a, const double *in_b, const double *slip,
+                             const mb_params *p, double *out_a, double *out_b, double *lambda,
+                             mb_info *info, cudaStream_t s)
 {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     const int m = std::max(1, std::min(p->restart, 500));
-    const int64_t L = 3 * n + 6 * nb;
+    const int64_t L = resist ? 3 * n : 3 * n + 6 * nb;
     Small sl{m};
 
     MB_TRY(ensure(ctx, ctx->sol_r, sizeof(double) * 3 * n, "blob positions"));
@@ -504,7 +555,7 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     MB_TRY(ensure(ctx, ctx->sol_b, sizeof(double) * L, "rhs"));
     MB_TRY(ensure(ctx, ctx->sol_x, sizeof(double) * L, "iterate"));
     MB_TRY(ensure(ctx, ctx->sol_w, sizeof(double) * L, "work vector"));
-    MB_TRY(ensure(ctx, ctx->sol_t, sizeof(double) * L, "work vector"));
+    MB_TRY(ensure(ctx, ctx->sol_t, sizeof(double) * std::max<int64_t>(L, 6 * nb), "work vector"));
     const bool mixed = p->prec == MB_MIXED_REFINE;
     if (mixed) {
         MB_TRY(ensure(ctx, ctx->sol_dx, sizeof(double) * L, "cycle correction"));
@@ -517,14 +568,15 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     double *r = (double *)ctx->sol_r.ptr;
     MB_TRY(blob_positions(ctx, nb, n, q, theta, blob_start, rho, r, s));
     if (p->precond == MB_PRECOND_FREE_SHARED)
-        MB_TRY(precond_setup_shared(ctx, nb, n, theta, blob_start, rho, p->a, p->eta, s));
+        MB_TRY(precond_setup_shared(ctx, nb, n, theta, blob_start, rho, p->a, p->eta, s, !resist));
     else
-        MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s));
+        MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s, !resist));
     if (p->prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const auto t1 = clk::now();
 
     Solver S;
+    S.resist = resist != 0;
     S.ctx = ctx; S.s = s; S.n = n; S.nb = nb; S.L = L; S.r = r; S.q = q;
     S.start = (const int64_t *)ctx->blob_start_copy.ptr;
     S.a = p->a; S.eta = p->eta; S.wall = p->wall; S.m = m; S.sl = sl;
@@ -538,7 +590,11 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
     const mb_precision outer = outer_precision(p->prec);
     const int vg = vec_grid(L);
 
-    build_rhs_kernel<<<vg, 256, 0, s>>>(n, nb, slip, F, T, S.b);
+    if (resist)
+        build_rhs_resist_kernel<<<vec_grid(n), 256, 0, s>>>(nb, n, r, q, S.start, in_a, in_b, slip,
+                                                            S.b);
+    else
+        build_rhs_kernel<<<vg, 256, 0, s>>>(n, nb, slip, in_a, in_b, S.b);
     count_launch();
     MB_CUDA_TRY(ctx, cudaMemsetAsync(S.x, 0, sizeof(double) * L, s));
     double *dx = mixed ? (double *)ctx->sol_dx.ptr : nullptr;
@@ -604,7 +660,7 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                     // orthogonalisation, replayed as a CUDA graph once captured
                     auto step = [&](cudaStream_t cs) -> mb_status {
                         S.s = cs;
-                        precond_apply_packed(ctx, vj, zj, cs);
+                        S.precond(vj, zj, cs);
                         const mb_status st = S.apply_A(zj, vn, inner);
                         S.s = s;
                         if (st != MB_OK) return st;
@@ -623,6 +679,7 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                         sig.gen = ctx->alloc_gen; sig.j = j; sig.m = m; sig.inner = (int)inner;
                         sig.wall = p->wall; sig.variant = ctx->pair_variant;
                         sig.pc_max_np = ctx->pc_max_np; sig.pc_kind = ctx->pc_kind;
+                        sig.mode = resist;
                         sig.n = n; sig.nb = nb; sig.L = L;
                         sig.pc_nb = ctx->pc_nb; sig.a = p->a; sig.eta = p->eta; sig.q = q;
                         sig.V = S.V; sig.Z = S.Z; sig.sm = S.sm;
@@ -634,7 +691,7 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                     if (!(est > inner_abs)) break;
                     continue;
                 }
-                precond_apply_packed(ctx, vj, zj, s);
+                S.precond(vj, zj, s);
                 MB_TRY(S.apply_A(zj, vn, inner));
                 // CGS2
                 S.dots(S.V, j + 1, vn, S.sm + sl.h(), 0);
@@ -667,7 +724,14 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
             ++restarts;
         }
     }
-    unpack_solution_kernel<<<vg, 256, 0, s>>>(n, nb, S.x, U, Omega, lambda);
+    if (resist) {
+        MB_CUDA_TRY(ctx, cudaMemcpyAsync(lambda, S.x, sizeof(double) * 3 * n,
+                                         cudaMemcpyDeviceToDevice, s));
+        launch_KT_apply(nb, r, q, S.start, S.x, S.t, 1.0, s);
+        split_ft_kernel<<<vec_grid(6 * nb), 256, 0, s>>>(nb, S.t, out_a, out_b);
+    } else {
+        unpack_solution_kernel<<<vg, 256, 0, s>>>(n, nb, S.x, out_a, out_b, lambda);
+    }
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -684,6 +748,26 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
         return set_err(ctx, MB_ENOTCONVERGED, "GMRES reached maxit=%d with relative residual %.3e",
                        p->maxit, rel);
     return MB_OK;
+}
+
+mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                         const double *theta, const int64_t *blob_start, const double *rho,
+                         const double *F, const double *T, const double *slip,
+                         const mb_params *p, double *U, double *Omega, double *lambda,
+                         mb_info *info, cudaStream_t s)
+{
+    return solve_rigid(ctx, 0, nb, n, q, theta, blob_start, rho, F, T, slip, p, U, Omega, lambda,
+                       info, s);
+}
+
+mb_status solve_resistance(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                           const double *theta, const int64_t *blob_start, const double *rho,
+                           const double *U, const double *Omega, const double *slip,
+                           const mb_params *p, double *F, double *T, double *lambda,
+                           mb_info *info, cudaStream_t s)
+{
+    return solve_rigid(ctx, 1, nb, n, q, theta, blob_start, rho, U, Omega, slip, p, F, T, lambda,
+                       info, s);
 }
 
 }  // namespace mb

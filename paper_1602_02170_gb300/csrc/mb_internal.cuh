@@ -28,7 +28,7 @@ struct DevBuf {
 // and workspace pointers they read.
 struct IterSig {
     uint64_t gen = 0;
-    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0;
+    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0, mode = 0;
     int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
     double a = 0.0, eta = 0.0;
     const void *q = nullptr, *V = nullptr, *Z = nullptr, *sm = nullptr;
@@ -36,6 +36,7 @@ struct IterSig {
     {
         return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
                variant == o.variant && pc_max_np == o.pc_max_np && pc_kind == o.pc_kind &&
+               mode == o.mode &&
                n == o.n && nb == o.nb &&
                L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
                V == o.V && Z == o.Z && sm == o.sm;
@@ -81,6 +82,7 @@ struct mb_context {
     int64_t pc_nb = 0, pc_n = 0;
     int pc_max_np = 0;
     int pc_kind = 0;             // mb_precond of the current blocks
+    int pc_schur = 1;            // 0: blocks hold M_pp^-1 only (resistance problem)
     int64_t pc_shapes = 0;       // shared kind: distinct shapes
 
     // solver workspace
@@ -142,23 +144,32 @@ void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t
                      const double *lambda, double *FT, double alpha, cudaStream_t s);
 
 // Preconditioner (precond.cu)
+// schur = 0 keeps only the blob blocks M_pp^-1 (resistance problem).
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                         const double *q, const int64_t *blob_start, double a, double eta,
-                        int wall, cudaStream_t s);
+                        int wall, cudaStream_t s, int schur = 1);
 // Asynchronous setup of the blocks of nb bodies: start (nb+1, global blob
 // indices), poff (nb offsets into P); a failing body sets flags[flag_slot] = 2.
 mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, const double *q,
                               const int64_t *start, const int64_t *poff, double *P, int max_np,
                               double a, double eta, int wall, int *flags, int flag_slot,
-                              cudaStream_t s);
+                              cudaStream_t s, int schur = 1);
 // Shared unbounded-domain blocks, one per body shape (precond.cu).
 mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const double *theta,
                                const int64_t *blob_start, const double *rho, double a,
-                               double eta, cudaStream_t s);
+                               double eta, cudaStream_t s, int schur = 1);
 // z = P^-1 v where v = [w (3N); g (6 n_b)] packed contiguously, same for z.
 void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s);
+// z = M~^-1 w with the blob blocks alone (w, z: 3N), for the resistance problem.
+void precond_apply_blobs(mb_context *ctx, const double *w, double *z, cudaStream_t s);
 
 // Solver (gmres.cu)
+// Eq. resistance_problem: M lambda = K [U; Omega] + slip, then (F, T) = K^T lambda.
+mb_status solve_resistance(mb_context *ctx, int64_t nb, int64_t n, const double *q,
+                           const double *theta, const int64_t *blob_start, const double *rho,
+                           const double *U, const double *Omega, const double *slip,
+                           const mb_params *p, double *F, double *T, double *lambda,
+                           mb_info *info, cudaStream_t s);
 mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
                          const double *theta, const int64_t *blob_start, const double *rho,
                          const double *F, const double *T, const double *slip,

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
     const int64_t *__restrict__ start, const int64_t *__restrict__ poff, PairConsts<double> k,
     double scale, double *__restrict__ P, double *__restrict__ scratch, int64_t scratch_stride,
-    int *__restrict__ flag, int flag_slot)
+    int *__restrict__ flag, int flag_slot, int schur)
 {
     extern __shared__ double sm[];
     for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
                 }
             for (int c = 0; c < 6 && !bad; ++c) {
                 const double d = A[c][c];
-                if (!(d > 0.0)) { bad = 1; break; }
+                if (!(d > 0.0)) { bad = schur; break; }
                 for (int b = 0; b < 12; ++b) A[c][b] /= d;
                 for (int a = 0; a < 6; ++a)
                     if (a != c) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
                 double acc = 0.0;
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk) acc += QN[i * 6 + kk] * Q[j * 6 + kk];
-                v = Pp[(size_t)i * m + j] - acc;
+                v = schur ? Pp[(size_t)i * m + j] - acc : Pp[(size_t)i * m + j];
             } else if (i < n) {
                 v = -QN[i * 6 + (j - n)];
             } else if (j < n) {
@@ -258,8 +258,10 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
 __global__ void __launch_bounds__(256) precond_apply_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     const double *__restrict__ P, const double *__restrict__ w, const double *__restrict__ g,
-    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows)
+    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows, int body_rows)
 {
+    // body_rows = 6: the indefinite block on [w_p; g_p]; 0: the blob block
+    // M_pp^-1 alone on w_p (the resistance problem's preconditioner)
     extern __shared__ double xs[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t item = blockIdx.x; item < nb * chunks; item += gridDim.x) {
@@ -267,18 +269,18 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(
         const int r0 = (int)(item % chunks) * rows;
         const int64_t b0 = start[p];
         const int n = 3 * (int)(start[p + 1] - b0);
-        const int m = n + 6;
-        const int r1 = min(m, r0 + rows);
-        if (r0 >= m) continue;  // uniform over the CTA
+        const int m = n + 6, me = n + body_rows;  // stored stride, rows used
+        const int r1 = min(me, r0 + rows);
+        if (r0 >= me) continue;  // uniform over the CTA
         __syncthreads();
-        for (int e = threadIdx.x; e < m; e += blockDim.x)
+        for (int e = threadIdx.x; e < me; e += blockDim.x)
             xs[e] = e < n ? w[3 * b0 + e] : g[6 * p + (e - n)];
         __syncthreads();
         const double *Pp = P + poff[p];
         for (int row = r0 + warp; row < r1; row += nw) {
             const double *pr = Pp + (size_t)row * m;
             double acc = 0.0;
-            for (int c = lane; c < m; c += 32) acc += pr[c] * xs[c];
+            for (int c = lane; c < me; c += 32) acc += pr[c] * xs[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) {
@@ -373,7 +375,7 @@ template <bool L_SMEM>
 __global__ void __launch_bounds__(256) pc_factor_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
     const int64_t *__restrict__ start, const int64_t *__restrict__ poff, double *__restrict__ P,
-    SplitScratch scr, int *__restrict__ flag, int flag_slot, int64_t p_base)
+    SplitScratch scr, int *__restrict__ flag, int flag_slot, int64_t p_base, int schur)
 {
     extern __shared__ double sm[];
     __shared__ int bad;
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
                 }
             for (int c = 0; c < 6 && !bad; ++c) {
                 const double dd = A[c][c];
-                if (!(dd > 0.0)) { bad = 1; break; }
+                if (!(dd > 0.0)) { bad = schur; break; }
                 for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
                 for (int a = 0; a < 6; ++a)
                     if (a != c) {
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(256) pc_trinv_kernel(
 // lower 32 x 32 tiles (I >= J) of the n x n block, mirrored to the upper.
 __global__ void __launch_bounds__(256) pc_product_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
-    double *__restrict__ P, SplitScratch scr, int tiles_per_body)
+    double *__restrict__ P, SplitScratch scr, int tiles_per_body, int schur)
 {
     __shared__ double Wi[kTile][kTile + 1], Wj[kTile][kTile + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of threads
@@ -609,8 +611,9 @@ __global__ void __launch_bounds__(256) pc_product_kernel(
             const int i = i0 + ty + 8 * rr;
             if (i >= n || j >= n || (I == J && j > i)) continue;
             double v = acc[rr];
+            if (schur)
 #pragma unroll
-            for (int bb = 0; bb < 6; ++bb) v -= QN[6 * i + bb] * Qs[6 * j + bb];
+                for (int bb = 0; bb < 6; ++bb) v -= QN[6 * i + bb] * Qs[6 * j + bb];
             Pp[(size_t)i * m + j] = v;
             Pp[(size_t)j * m + i] = v;
         }
@@ -620,7 +623,7 @@ __global__ void __launch_bounds__(256) pc_product_kernel(
 // Runs S1..S4 over groups of bodies whose scratch fits the cap.
 mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double *q,
                       const int64_t *start, const int64_t *poff, double *P, int max_np, double a,
-                      double eta, int wall, int *flag, int flag_slot, cudaStream_t s)
+                      double eta, int wall, int *flag, int flag_slot, int schur, cudaStream_t s)
 {
     const int nmax = 3 * max_np;
     const int64_t stride = split_stride(nmax);
@@ -649,7 +652,7 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)fsmem));
         factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
-            ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0);
+            ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
         const int gt = (int)std::min<int64_t>(ng * col_groups, 16 * (int64_t)ctx->sm_count);
         if (nmax <= 128)
             pc_trinv_kernel<4><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
@@ -658,7 +661,7 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
         else
             pc_trinv_kernel<16><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
         const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
-        pc_product_kernel<<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles);
+        pc_product_kernel<<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles, schur);
         count_launch(4);
         MB_CUDA_TRY(ctx, cudaGetLastError());
     }
@@ -688,23 +691,23 @@ __global__ void __launch_bounds__(256) precond_apply_shared_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int *__restrict__ shape,
     const int64_t *__restrict__ poff, const double *__restrict__ P,
     const double *__restrict__ theta, const double *__restrict__ w, const double *__restrict__ g,
-    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows)
+    double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows, int body_rows)
 {
-    extern __shared__ double xs[];  // m rotated inputs, then `rows` results
+    extern __shared__ double xs[];  // me rotated inputs, then `rows` results
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t item = blockIdx.x; item < nb * chunks; item += gridDim.x) {
         const int64_t p = item / chunks;
         const int r0 = (int)(item % chunks) * rows;
         const int64_t b0 = start[p];
-        const int np = (int)(start[p + 1] - b0), n = 3 * np, m = n + 6;
-        const int r1 = min(m, r0 + rows);
-        if (r0 >= m) continue;  // uniform over the CTA
+        const int np = (int)(start[p + 1] - b0), n = 3 * np, m = n + 6, me = n + body_rows;
+        const int r1 = min(me, r0 + rows);
+        if (r0 >= me) continue;  // uniform over the CTA
         double R[9];
         quat_matrix(theta + 4 * p, R);
-        double *ys = xs + m;
+        double *ys = xs + me;
         __syncthreads();
         // x = diag(R~, R, R)^T [w_p; g_p], one triple per thread
-        for (int t = threadIdx.x; t < m / 3; t += blockDim.x) {
+        for (int t = threadIdx.x; t < me / 3; t += blockDim.x) {
             const double *v = t < np ? w + 3 * (b0 + t) : g + 6 * p + 3 * (t - np);
 #pragma unroll
             for (int al = 0; al < 3; ++al)
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(256) precond_apply_shared_kernel(
         for (int row = r0 + warp; row < r1; row += nw) {
             const double *pr = Pp + (size_t)row * m;
             double acc = 0.0;
-            for (int c = lane; c < m; c += 32) acc += pr[c] * xs[c];
+            for (int c = lane; c < me; c += 32) acc += pr[c] * xs[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) ys[row - r0] = acc;
@@ -736,7 +739,7 @@ __global__ void __launch_bounds__(256) precond_apply_shared_kernel(
 
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                         const double *q, const int64_t *blob_start, double a, double eta,
-                        int wall, cudaStream_t s)
+                        int wall, cudaStream_t s, int schur)
 {
     // body sizes on the host
     std::vector<int64_t> hstart(nb + 1);
@@ -784,13 +787,13 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
         if (nmax <= kSplitMaxRows)
             return setup_split(ctx, nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                (const int64_t *)ctx->pinv_off.ptr, (double *)ctx->pinv.ptr, max_np,
-                               a, eta, wall, (int *)ctx->flag.ptr, -1, s);
+                               a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                                (const int64_t *)ctx->pinv_off.ptr, k, scale,
                                                (double *)ctx->pinv.ptr, scratch, stride,
-                                               (int *)ctx->flag.ptr, -1);
+                                               (int *)ctx->flag.ptr, -1, schur);
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
@@ -811,6 +814,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     ctx->pc_max_np = max_np;
     ctx->pc_kind = MB_PRECOND_WALL;
     ctx->pc_shapes = 0;
+    ctx->pc_schur = schur;
     if (first_bad != big) {
         ctx->pc_nb = 0;
         return set_err(ctx, MB_ESINGULAR,
@@ -823,7 +827,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
 mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, const double *q,
                               const int64_t *start, const int64_t *poff, double *P, int max_np,
                               double a, double eta, int wall, int *flags, int flag_slot,
-                              cudaStream_t s)
+                              cudaStream_t s, int schur)
 {
     const int nmax = 3 * max_np;
     const bool lsmem = nmax <= kSmemMaxRows;
@@ -843,11 +847,11 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
     auto launch = [&](auto kern) -> mb_status {
         if (nmax <= kSplitMaxRows)
             return setup_split(ctx, nb, r, q, start, poff, P, max_np, a, eta, wall, flags,
-                               flag_slot, s);
+                               flag_slot, schur, s);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, start, poff, k, scale, P, scratch, stride,
-                                               flags, flag_slot);
+                                               flags, flag_slot, schur);
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
@@ -861,7 +865,7 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
 
 mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const double *theta,
                                const int64_t *blob_start, const double *rho, double a,
-                               double eta, cudaStream_t s)
+                               double eta, cudaStream_t s, int schur)
 {
     // offsets and reference positions on the host, to group bodies by shape
     std::vector<int64_t> hstart(nb + 1);
@@ -955,7 +959,7 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
         max_ref_np = std::max<int>(max_ref_np, (int)(rstart[t + 1] - rstart[t]));
     MB_TRY(precond_setup_range(ctx, ns, dref, dref + 3 * rstart[ns], dstart, doff,
                                (double *)ctx->pinv.ptr, max_ref_np, a, eta, 0,
-                               (int *)ctx->flag.ptr, -1, s));
+                               (int *)ctx->flag.ptr, -1, s, schur));
     int first_bad = big;
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(&first_bad, ctx->flag.ptr, sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
@@ -965,6 +969,7 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
     ctx->pc_max_np = max_np;
     ctx->pc_kind = MB_PRECOND_FREE_SHARED;
     ctx->pc_shapes = ns;
+    ctx->pc_schur = schur;
     if (first_bad != big) {
         ctx->pc_nb = 0;
         return set_err(ctx, MB_ESINGULAR,
@@ -975,9 +980,9 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
 }
 
 static void precond_apply_impl(mb_context *ctx, const double *w, const double *g, double *lam,
-                               double *UO, cudaStream_t s)
+                               double *UO, cudaStream_t s, int body_rows = 6)
 {
-    const int m = 3 * ctx->pc_max_np + 6;
+    const int m = 3 * ctx->pc_max_np + body_rows;
     // few bodies: split each body's rows so that about two CTAs per SM have work
     const int64_t want = ceil_div(2 * (int64_t)ctx->sm_count, ctx->pc_nb);
     const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(want, ceil_div(m, 8)));
@@ -987,14 +992,14 @@ static void precond_apply_impl(mb_context *ctx, const double *w, const double *g
         precond_apply_shared_kernel<<<grid, 256, sizeof(double) * (m + rows), s>>>(
             ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int *)ctx->pc_type.ptr,
             (const int64_t *)ctx->pinv_off.ptr, (const double *)ctx->pinv.ptr,
-            (const double *)ctx->pc_theta.ptr, w, g, lam, UO, chunks, rows);
+            (const double *)ctx->pc_theta.ptr, w, g, lam, UO, chunks, rows, body_rows);
         count_launch();
         return;
     }
     const int rows = (int)ceil_div(m, chunks);
     precond_apply_kernel<<<grid, 256, sizeof(double) * m, s>>>(
         ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int64_t *)ctx->pinv_off.ptr,
-        (const double *)ctx->pinv.ptr, w, g, lam, UO, chunks, rows);
+        (const double *)ctx->pinv.ptr, w, g, lam, UO, chunks, rows, body_rows);
     count_launch();
 }
 
@@ -1004,10 +1009,18 @@ void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStrea
     precond_apply_impl(ctx, v, v + n3, z, z + n3, s);
 }
 
+void precond_apply_blobs(mb_context *ctx, const double *w, double *z, cudaStream_t s)
+{
+    precond_apply_impl(ctx, w, nullptr, z, nullptr, s, 0);
+}
+
 mb_status precond_apply_public(mb_context *ctx, const double *w, const double *g, double *lam,
                                double *UO, cudaStream_t s)
 {
     if (ctx->pc_nb == 0) return set_err(ctx, MB_EINVAL, "no preconditioner has been set up");
+    if (!ctx->pc_schur)
+        return set_err(ctx, MB_EINVAL, "the current blocks belong to a resistance solve; "
+                                       "call mb_precond_setup again");
     if (3 * ctx->pc_max_np + 6 > 6000)
         return set_err(ctx, MB_EINVAL, "body too large for the preconditioner apply");
     precond_apply_impl(ctx, w, g, lam, UO, s);
