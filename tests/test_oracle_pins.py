@@ -321,3 +321,56 @@ def test_resistance_rigid_slip_cancels_motion():
     slip = -O.K_apply(V, Wv, r, s.q, s.blob_start)
     F, T, lam = O.solve_resistance(r, s.q, s.blob_start, V, Wv, s.a, 1.0, True, slip)
     assert np.abs(lam).max() <= 1e-12 and np.abs(F).max() <= 1e-12 and np.abs(T).max() <= 1e-12
+
+
+# ------------------------------------------------------------ active slip
+def _strain_slip(rho, gamma=1.0):
+    """Apparent slip -v(r_i) for the planar strain v = gamma (x, -y, 0)."""
+    return -gamma * np.stack([rho[:, 0], -rho[:, 1], np.zeros(len(rho))], axis=1)
+
+
+def _stresslet_11(lam, rho):
+    """s_11 of the symmetric traceless first moment sum_i lambda_i (x) r_i."""
+    S = lam.T @ rho
+    s = 0.5 * (S + S.T) - np.trace(S) / 3.0 * np.eye(3)
+    return s[0, 0]
+
+
+def test_stresslet_radii_table():
+    """R_s of force- and torque-free shells under the strain slip reproduces
+    Table Stresslets_3D (left); the free body does not move."""
+    g = json.load(open(os.path.join(GOLDEN, "stresslet_radii.json")))
+    for n, ratio, rs_ref in g["rows"]:
+        rho = I.shell(int(n))
+        a = ratio * I.min_spacing(rho)
+        z = np.zeros((1, 3))
+        U, W, lam = O.solve_saddle(rho, z, np.array([0, n]), z, z, a, 1.0, False,
+                                   _strain_slip(rho))
+        rs = (-3.0 * _stresslet_11(lam, rho) / (20.0 * PI)) ** (1.0 / 3.0)
+        assert abs(rs - rs_ref) <= 1.5e-4, (n, ratio, rs, rs_ref)
+        assert np.abs(U).max() <= 1e-12 and np.abs(W).max() <= 1e-12
+
+
+def squirmer_slip(rho, B1=1.0):
+    """Tangential slip B1 sin(theta) e_theta of a squirmer (Section 4.2)."""
+    th = np.arccos(np.clip(rho[:, 2] / np.linalg.norm(rho, axis=1), -1.0, 1.0))
+    ph = np.arctan2(rho[:, 1], rho[:, 0])
+    e_th = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], axis=1)
+    return B1 * np.sin(th)[:, None] * e_th
+
+
+def test_squirmer_speed_converges_linearly_in_blob_radius():
+    """Section 4.2: a force- and torque-free squirmer swims along z, and the
+    relative error of its speed against (2/3) B1 is linear in a/R_g: halving
+    a (162 -> 642 blobs at fixed a/s) halves it, and it vanishes with a."""
+    eps = []
+    for n in (162, 642):
+        rho = I.shell(n)
+        a = 0.5 * I.min_spacing(rho)
+        z = np.zeros((1, 3))
+        U, W, _ = O.solve_saddle(rho, z, np.array([0, n]), z, z, a, 1.0, False, squirmer_slip(rho))
+        assert np.abs(U[0, :2]).max() <= 1e-12 and np.abs(W).max() <= 1e-12
+        eps.append((U[0, 2] / (2.0 / 3.0) - 1.0, a))
+    (e1, a1), (e2, a2) = eps
+    assert 0 < e2 < e1
+    assert abs((e2 / a2) / (e1 / a1) - 1.0) <= 0.05   # the same slope: linear in a
