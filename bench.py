@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--precond", default="wall", choices=["wall", "free_shared"],
                    help="block preconditioner of the --workload small / monolayer solves")
     p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve",
-                                          "resistance"],
+                                          "resistance", "active"],
                    default="matvec",
                    help="matvec: the benchmark line below; monolayer / batch / serve: the "
                         "663,552-blob monolayer solve, 256 batched suspensions, and the "
@@ -547,6 +547,56 @@ def bench_resistance(args):
     return 0
 
 
+def bench_active(args):
+    """Active slip on single shells in an unbounded domain: the squirmer's
+    speed against (2/3) B1 (Section 4.2) and the stresslet radius R_s under
+    the strain slip (Section 4.1), with solve times (FP64, tol 1e-10)."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    d = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x)).to("cuda", dt)
+    rows = []
+    for n in (42, 162, 642):
+        rho = I.shell(n)
+        a = 0.5 * I.min_spacing(rho)
+        th = np.arccos(np.clip(rho[:, 2] / np.linalg.norm(rho, axis=1), -1.0, 1.0))
+        ph = np.arctan2(rho[:, 1], rho[:, 0])
+        e_th = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], axis=1)
+        squirm = np.sin(th)[:, None] * e_th
+        strain = -np.stack([rho[:, 0], -rho[:, 1], np.zeros(n)], axis=1)
+        body = (d(np.zeros((1, 3))), d([[1.0, 0, 0, 0]]), d([0, n], torch.int64), d(rho))
+        z = d(np.zeros((1, 3)))
+        row = {"n_blobs": n, "a_over_Rg": a}
+        for name, slip in (("squirmer", squirm), ("strain", strain)):
+            ctx.solve_mobility(*body, z, z, a, 1.0, False, d(slip), tol=1e-10, prec="fp64")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            U, W, lam, info = ctx.solve_mobility(*body, z, z, a, 1.0, False, d(slip), tol=1e-10,
+                                                 prec="fp64")
+            torch.cuda.synchronize()
+            row[name + "_ms"] = 1e3 * (time.perf_counter() - t0)
+            if name == "squirmer":
+                uz = float(U[0, 2])
+                row["squirmer_speed_over_2B1_3"] = uz / (2.0 / 3.0)
+                row["squirmer_rel_err_over_a"] = (uz / (2.0 / 3.0) - 1.0) / a
+            else:
+                S = ctx.lambda_moments(body[3], body[0], body[2], lam)[0].cpu().numpy()
+                s = 0.5 * (S + S.T) - np.trace(S) / 3.0 * np.eye(3)
+                row["Rs_over_Rg"] = float((-3.0 * s[0, 0] / (20.0 * math.pi)) ** (1.0 / 3.0))
+        rows.append(row)
+    print(json.dumps({"metric": "active slip: squirmer speed and stresslet radius",
+                      "workload": "single icosahedral shells, a = s/2, unbounded domain, FP64, "
+                                  "tol 1e-10", "rows": rows, "n_gpus": 1}), flush=True)
+    ctx.close()
+    return 0
+
+
 def bench_batch(args):
     """256 independent mixed suspensions (42-blob shells and 15-blob
     boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
@@ -739,6 +789,8 @@ def main():
         return bench_small(args)
     if args.workload == "resistance":
         return bench_resistance(args)
+    if args.workload == "active":
+        return bench_active(args)
     if args.workload == "monolayer":
         return bench_monolayer(args)
     if args.workload == "batch":

@@ -267,6 +267,17 @@ mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, c
                            int wall, void *stream);
 
 /*
+ * First moments of the blob forces, body by body:
+ *   S_p[a][b] = sum_{i in p} lambda_i,a (r_i - q_p)_b     (S: n_b x 9, row-major)
+ * Its symmetric traceless part is the stresslet of body p (Section 4.1: the
+ * stresslet radius R_s under an applied strain slip), its antisymmetric part
+ * the torque.  r, lambda: N x 3; q: n_b x 3; blob_start: n_b + 1 (device).
+ */
+mb_status mb_lambda_moments(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
+                            const double *q, const int64_t *blob_start, const double *lambda,
+                            double *S, void *stream);
+
+/*
  * Set up the shared unbounded-domain preconditioner (MB_PRECOND_FREE_SHARED)
  * for n_b bodies given by their orientations theta (n_b x 4, unit
  * quaternions, scalar first), blob_start (n_b + 1) and reference offsets rho

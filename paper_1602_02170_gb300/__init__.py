@@ -55,6 +55,7 @@ EXPORTED_SYMBOLS = [
     "mb_blob_positions",
     "mb_K_apply",
     "mb_KT_apply",
+    "mb_lambda_moments",
     "mb_precond_setup",
     "mb_precond_setup_shared",
     "mb_precond_apply",
@@ -180,6 +181,7 @@ def load_library():
     L.mb_K_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_KT_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_precond_setup.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, ci, vp]
+    L.mb_lambda_moments.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_precond_setup_shared.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, vp]
     L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.mb_solve_mobility.argtypes = [
@@ -373,6 +375,18 @@ class Context:
             out = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
         self._check(self.L.mb_KT_apply(self.handle, nb, n, _ptr(r), _ptr(q), _ptr(blob_start),
                                        _ptr(lam), _ptr(out), self._stream(stream)))
+        return out
+
+    def lambda_moments(self, r, q, blob_start, lam, out=None, stream=None):
+        """S_p = sum_i lambda_i (x) (r_i - q_p), one 3 x 3 matrix per body."""
+        torch = self._torch
+        nb, n = int(q.shape[0]), int(r.shape[0])
+        self._dev(r, (n, 3)); self._dev(q, (nb, 3)); self._dev(lam, (n, 3))
+        self._dev(blob_start, (nb + 1,), torch.int64)
+        if out is None:
+            out = torch.empty((nb, 3, 3), dtype=torch.float64, device=r.device)
+        self._check(self.L.mb_lambda_moments(self.handle, nb, n, _ptr(r), _ptr(q), _ptr(blob_start),
+                                             _ptr(lam), _ptr(out), self._stream(stream)))
         return out
 
     def precond_setup(self, r, q, blob_start, a, eta=1.0, wall=True, stream=None):

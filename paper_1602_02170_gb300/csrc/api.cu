@@ -321,6 +321,19 @@ mb_status mb_KT_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const 
     return MB_OK;
 }
 
+mb_status mb_lambda_moments(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
+                            const double *q, const int64_t *blob_start, const double *lambda,
+                            double *S, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (n_bodies < 0 || n_blobs < 0) return set_err(ctx, MB_EINVAL, "negative size");
+    if (n_bodies == 0) return MB_OK;
+    if (!r || !q || !blob_start || !lambda || !S) return set_err(ctx, MB_EINVAL, "null array pointer");
+    launch_moments(n_bodies, r, q, blob_start, lambda, S, (cudaStream_t)stream);
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    return MB_OK;
+}
+
 mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
                            const double *q, const int64_t *blob_start, double a, double eta,
                            int wall, void *stream)

@@ -176,6 +176,49 @@ void launch_K_apply(int64_t nb, int64_t n, const double *r, const double *q,
     count_launch();
 }
 
+// S_p[a][b] = sum_{i in p} lambda_i,a (r_i - q_p)_b: the first moment of the
+// blob forces, whose symmetric traceless part is the body's stresslet
+// (Section 4.1).  One warp per body.
+__global__ void moments_kernel(int64_t nb, const double *__restrict__ r,
+                               const double *__restrict__ q, const int64_t *__restrict__ start,
+                               const double *__restrict__ lam, double *__restrict__ S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < nb;
+         p += warps) {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        for (int64_t i = start[p] + lane; i < start[p + 1]; i += 32) {
+            const double d[3] = {r[3 * i] - qx, r[3 * i + 1] - qy, r[3 * i + 2] - qz};
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) acc[3 * al + be] += lam[3 * i + al] * d[be];
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        if (lane < 9) {
+            double v = acc[0];
+#pragma unroll
+            for (int c = 1; c < 9; ++c)
+                if (lane == c) v = acc[c];
+            S[9 * p + lane] = v;
+        }
+    }
+}
+
+void launch_moments(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
+                    const double *lambda, double *S, cudaStream_t s)
+{
+    if (nb == 0) return;
+    moments_kernel<<<grid_for(nb * 32, 256), 256, 0, s>>>(nb, r, q, blob_start, lambda, S);
+    count_launch();
+}
+
 void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
                      const double *lambda, double *FT, double alpha, cudaStream_t s)
 {

@@ -139,6 +139,9 @@ mb_status blob_positions(mb_context *ctx, int64_t nb, int64_t n, const double *q
 void launch_K_apply(int64_t nb, int64_t n, const double *r, const double *q,
                     const int64_t *blob_start, const double *UO, double *v, double alpha,
                     double beta, cudaStream_t s);
+// S_p = sum_i lambda_i (x) (r_i - q_p)   (S: n_b x 9, row-major 3 x 3)
+void launch_moments(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
+                    const double *lambda, double *S, cudaStream_t s);
 // FT = alpha * K^T lambda      (FT: n_b x 6)
 void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
                      const double *lambda, double *FT, double alpha, cudaStream_t s);

@@ -569,6 +569,57 @@ __global__ void __launch_bounds__(256) pc_trinv_kernel(
     }
 }
 
+// S3 for larger blocks (3 n_p up to kSplitMaxRowsSmem): the same
+// substitution with the warp's column in shared memory instead of registers
+// (n doubles per warp); __syncwarp orders each step's update before the
+// next step's read of the new pivot row.
+constexpr int kSplitMaxRowsSmem = 2048;
+constexpr int kTrinvSmemWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTrinvSmemWarps) pc_trinv_smem_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int col_groups)
+{
+    extern __shared__ double colbuf[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double *w = colbuf + (size_t)warp * scr.nmax;
+    for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
+        const int64_t p = item / col_groups;
+        const int c = (int)(item % col_groups) * nw + warp;
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        if (c >= n) continue;  // warp-uniform
+        const double *Lt = P + poff[p];
+        double *W = scr.W(p);
+        const double *G = scr.G(p), *dW = scr.dW(p), *Nm = scr.N(p);
+        const int ldw = scr.nmax;
+        for (int i = lane; i < n; i += 32) w[i] = i == c ? 1.0 : 0.0;
+        for (int kk = (c & ~(kTile - 1)) + lane; kk < c; kk += 32) W[(size_t)kk * ldw + c] = 0.0;
+        __syncwarp();
+        double qa = 0.0;  // lane b < 6: Q[c][b]
+        for (int k = c; k < n; ++k) {
+            const double wk = w[k] * dW[k];
+            if (lane == 0) W[(size_t)k * ldw + c] = wk;
+            if (lane < 6) qa += wk * G[6 * k + lane];
+            const double *lk = Lt + (size_t)k * m;
+            for (int i = k + 1 + lane; i < n; i += 32) w[i] -= lk[i] * wk;
+            __syncwarp();
+        }
+        double qn = 0.0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const double qv = __shfl_sync(0xffffffffu, qa, a);
+            if (lane < 6) qn += qv * Nm[a * 6 + lane];
+        }
+        if (lane < 6) {
+            scr.Q(p)[6 * c + lane] = qa;
+            scr.QN(p)[6 * c + lane] = qn;
+            P[poff[p] + (size_t)c * m + n + lane] = -qn;
+            P[poff[p] + (size_t)(n + lane) * m + c] = -qn;
+        }
+        __syncwarp();  // the next column reuses w
+    }
+}
+
 // S4: P_p[i][j] = sum_k W[k][i] W[k][j] - sum_b QN[i][b] Q[j][b] on the
 // lower 32 x 32 tiles (I >= J) of the n x n block, mirrored to the upper.
 __global__ void __launch_bounds__(256) pc_product_kernel(
@@ -654,7 +705,14 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
         factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
             ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
         const int gt = (int)std::min<int64_t>(ng * col_groups, 16 * (int64_t)ctx->sm_count);
-        if (nmax <= 128)
+        if (nmax > kSplitMaxRows) {
+            const size_t tsm = sizeof(double) * (size_t)nmax * kTrinvSmemWarps;
+            MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_trinv_smem_kernel,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)tsm));
+            pc_trinv_smem_kernel<<<gt, 32 * kTrinvSmemWarps, tsm, s>>>(ng, st, po, P, scr,
+                                                                      col_groups);
+        } else if (nmax <= 128)
             pc_trinv_kernel<4><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
         else if (nmax <= 256)
             pc_trinv_kernel<8><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
@@ -777,14 +835,14 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     int grid = (int)std::min<int64_t>(nb, 4 * (int64_t)ctx->sm_count);
     double *scratch = nullptr;
     int64_t stride = 0;
-    if (!lsmem && nmax > kSplitMaxRows) {
+    if (!lsmem && nmax > kSplitMaxRowsSmem) {
         grid = (int)std::min<int64_t>(nb, ctx->sm_count);
         stride = (int64_t)nmax * nmax;
         MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
         scratch = (double *)ctx->sol_dots.ptr;
     }
     auto launch = [&](auto kern) -> mb_status {
-        if (nmax <= kSplitMaxRows)
+        if (nmax <= kSplitMaxRowsSmem)
             return setup_split(ctx, nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                (const int64_t *)ctx->pinv_off.ptr, (double *)ctx->pinv.ptr, max_np,
                                a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s);
@@ -838,14 +896,14 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
     int grid = (int)std::min<int64_t>(nb, 4 * (int64_t)ctx->sm_count);
     double *scratch = nullptr;
     int64_t stride = 0;
-    if (!lsmem && nmax > kSplitMaxRows) {
+    if (!lsmem && nmax > kSplitMaxRowsSmem) {
         grid = (int)std::min<int64_t>(nb, ctx->sm_count);
         stride = (int64_t)nmax * nmax;
         MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
         scratch = (double *)ctx->sol_dots.ptr;
     }
     auto launch = [&](auto kern) -> mb_status {
-        if (nmax <= kSplitMaxRows)
+        if (nmax <= kSplitMaxRowsSmem)
             return setup_split(ctx, nb, r, q, start, poff, P, max_np, a, eta, wall, flags,
                                flag_slot, schur, s);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

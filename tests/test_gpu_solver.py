@@ -104,20 +104,29 @@ def test_preconditioner_large_bodies_global_path(ctx):
     assert rel_l2(host(UO), UO_ref) <= 1e-8
 
 
-def test_preconditioner_very_large_bodies_single_kernel_path(ctx):
-    """Bodies of 180 blobs (540 rows) exceed the split setup's register
-    column limit and take the one-kernel-per-body setup."""
-    g = np.stack(np.meshgrid(np.arange(6), np.arange(6), np.arange(5), indexing="ij"), -1)
+def _lattice_bodies(shape, nbod, seed):
+    """nbod jittered cubic-lattice bodies of prod(shape) blobs (spacing 2.2 a)."""
+    g = np.stack(np.meshgrid(*[np.arange(k) for k in shape], indexing="ij"), -1)
     a = 0.1
-    rho1 = (g.reshape(-1, 3) - np.array([2.5, 2.5, 2.0])) * (2.2 * a)
-    rng = np.random.default_rng(6)
-    rho = np.concatenate([rho1 + 0.01 * a * rng.standard_normal(rho1.shape) for _ in range(2)])
-    s = I.Suspension(q=np.array([[0.0, 0.0, 1.5], [2.0, 0.5, 1.7]]),
-                     theta=I.random_unit_quaternions(rng, 2),
-                     blob_start=np.array([0, 180, 360], dtype=np.int64), rho=rho,
-                     F=np.zeros((2, 3)), T=np.zeros((2, 3)), a=a)
+    rho1 = (g.reshape(-1, 3) - (np.array(shape) - 1) / 2.0) * (2.2 * a)
+    rng = np.random.default_rng(seed)
+    nbl = len(rho1)
+    rho = np.concatenate([rho1 + 0.01 * a * rng.standard_normal(rho1.shape) for _ in range(nbod)])
+    q = np.array([[2.5 * k, 0.3 * k, 1.5 + 0.2 * k] for k in range(nbod)])
+    return I.Suspension(q=q, theta=I.random_unit_quaternions(rng, nbod),
+                        blob_start=np.arange(nbod + 1, dtype=np.int64) * nbl, rho=rho,
+                        F=np.zeros((nbod, 3)), T=np.zeros((nbod, 3)), a=a)
+
+
+@pytest.mark.parametrize("shape,nbod", [((6, 6, 5), 2), ((10, 10, 7), 1)])
+def test_preconditioner_very_large_bodies(ctx, shape, nbod):
+    """Bodies of 180 blobs (540 rows) take the split setup with the column of
+    L^-1 in shared memory; 700 blobs (2,100 rows) the one-kernel-per-body
+    setup."""
+    s = _lattice_bodies(shape, nbod, 6)
+    rng = np.random.default_rng(7)
     r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
-    assert r[:, 2].min() > a
+    assert r[:, 2].min() > s.a
     w = rng.standard_normal((s.n_blobs, 3))
     gg = rng.standard_normal((s.n_bodies, 6))
     d = _dev_susp(s)
