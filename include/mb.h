@@ -267,6 +267,30 @@ mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, c
                            int wall, void *stream);
 
 /*
+ * Velocity at arbitrary points x (n_points x 3) of the flow driven by forces
+ * f on n_blobs blobs at r (Eq. RPYTensor with the wall correction when
+ * wall != 0):  u(x_t) = sum_j M(x_t, r_j) f_j, every point treated as a
+ * tracer blob of the same radius a.  Points may coincide with blobs (the
+ * overlap branch is regular at zero distance); with the wall they must lie
+ * above it (z > 0).  prec: MB_FP32_KAHAN or MB_FP64.  Device pointers only.
+ */
+mb_status mb_mobility_eval(mb_context *ctx, const double *x, int64_t n_points, const double *r,
+                           const double *f, int64_t n_blobs, double a, double eta, int wall,
+                           mb_precision prec, double *u, void *stream);
+
+/*
+ * Flow rendering of Appendix B: every blob i of radius a is replaced by n_sub
+ * blobs of radius a_sub at r_i + sub_offsets[k] (n_sub x 3, typically points
+ * on the sphere of radius a), each carrying lambda_i / n_sub, and the
+ * velocity v(x) of a tracer blob of radius a_sub is evaluated at the points x
+ * as with mb_mobility_eval.  Device pointers only.
+ */
+mb_status mb_render_flow(mb_context *ctx, const double *x, int64_t n_points, const double *r,
+                         const double *lambda, int64_t n_blobs, const double *sub_offsets,
+                         int n_sub, double a_sub, double eta, int wall, mb_precision prec,
+                         double *v, void *stream);
+
+/*
  * First moments of the blob forces, body by body:
  *   S_p[a][b] = sum_{i in p} lambda_i,a (r_i - q_p)_b     (S: n_b x 9, row-major)
  * Its symmetric traceless part is the stresslet of body p (Section 4.1: the

@@ -22,6 +22,10 @@ Functions and the passages they follow:
   precond_apply                     Eq. saddle_M_precon with the block-diagonal
                                     mobility of Eq. M_tilde_block_diag, one
                                     body at a time, solved directly (LU)
+  eval_points, render_flow           velocity of tracer blobs at arbitrary points
+                                    (Eq. RPYTensor + wall), and the flow
+                                    rendering of Appendix B (blobs split into
+                                    smaller blobs sharing their force)
   solve_resistance                  Eq. resistance_problem: M lambda = K U + slip
                                     by Cholesky, then (F, T) = K^T lambda
                                     (Section 2.1.2)
@@ -151,6 +155,26 @@ def matvec(r, f, a, eta=1.0, wall=True, targets=None):
 
 
 # ---------------------------------------------------------------- bodies
+def eval_points(x, r, f, a, eta=1.0, wall=True):
+    """u(x_t) = sum_j M(x_t, r_j) f_j with the points x as tracer blobs of
+    radius a: the matvec over the blobs and the (force-free) points, read at
+    the points."""
+    x, r, f = _c(x), _c(r), _c(f)
+    allr = np.concatenate([r, x])
+    allf = np.concatenate([f, np.zeros_like(x)])
+    return matvec(allr, allf, a, eta, wall, targets=np.arange(len(r), len(r) + len(x)))
+
+
+def render_flow(x, r, lam, offsets, a_sub, eta=1.0, wall=True):
+    """Appendix B: blob i becomes blobs of radius a_sub at r_i + offsets[k],
+    each with lambda_i / len(offsets); the flow at x is that of a tracer blob
+    of radius a_sub."""
+    r, lam, offsets = _c(r), _c(lam), _c(offsets)
+    rs = (r[:, None, :] + offsets[None, :, :]).reshape(-1, 3)
+    ls = np.repeat(lam / len(offsets), len(offsets), axis=0)
+    return eval_points(x, rs, ls, a_sub, eta, wall)
+
+
 def rotation_matrix(theta):
     """Rotation of a unit quaternion theta = (s, v), scalar first:
     R = (s^2 - v.v) I + 2 v v^T + 2 s [v]_x ."""

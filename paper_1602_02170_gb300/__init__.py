@@ -55,6 +55,8 @@ EXPORTED_SYMBOLS = [
     "mb_blob_positions",
     "mb_K_apply",
     "mb_KT_apply",
+    "mb_mobility_eval",
+    "mb_render_flow",
     "mb_lambda_moments",
     "mb_precond_setup",
     "mb_precond_setup_shared",
@@ -182,6 +184,8 @@ def load_library():
     L.mb_KT_apply.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.mb_precond_setup.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, ci, vp]
     L.mb_lambda_moments.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.mb_mobility_eval.argtypes = [vp, vp, i64, vp, vp, i64, dbl, dbl, ci, ci, vp, vp]
+    L.mb_render_flow.argtypes = [vp, vp, i64, vp, vp, i64, vp, ci, dbl, dbl, ci, ci, vp, vp]
     L.mb_precond_setup_shared.argtypes = [vp, i64, i64, vp, vp, vp, dbl, dbl, vp]
     L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.mb_solve_mobility.argtypes = [
@@ -375,6 +379,34 @@ class Context:
             out = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
         self._check(self.L.mb_KT_apply(self.handle, nb, n, _ptr(r), _ptr(q), _ptr(blob_start),
                                        _ptr(lam), _ptr(out), self._stream(stream)))
+        return out
+
+    def mobility_eval(self, x, r, f, a, eta=1.0, wall=True, prec="fp32", out=None, stream=None):
+        """Velocity at points x (n_points x 3) driven by blob forces f at r."""
+        torch = self._torch
+        nt, n = int(x.shape[0]), int(r.shape[0])
+        self._dev(x, (nt, 3)); self._dev(r, (n, 3)); self._dev(f, (n, 3))
+        if out is None:
+            out = torch.empty((nt, 3), dtype=torch.float64, device=x.device)
+        self._check(self.L.mb_mobility_eval(self.handle, _ptr(x), nt, _ptr(r), _ptr(f), n,
+                                            float(a), float(eta), int(bool(wall)), _prec(prec),
+                                            _ptr(out), self._stream(stream)))
+        return out
+
+    def render_flow(self, x, r, lam, sub_offsets, a_sub, eta=1.0, wall=True, prec="fp32",
+                    out=None, stream=None):
+        """Appendix B: flow at points x with every blob split into the
+        sub_offsets (n_sub x 3) blobs of radius a_sub sharing its force."""
+        torch = self._torch
+        nt, n, ns = int(x.shape[0]), int(r.shape[0]), int(sub_offsets.shape[0])
+        self._dev(x, (nt, 3)); self._dev(r, (n, 3)); self._dev(lam, (n, 3))
+        self._dev(sub_offsets, (ns, 3))
+        if out is None:
+            out = torch.empty((nt, 3), dtype=torch.float64, device=x.device)
+        self._check(self.L.mb_render_flow(self.handle, _ptr(x), nt, _ptr(r), _ptr(lam), n,
+                                          _ptr(sub_offsets), ns, float(a_sub), float(eta),
+                                          int(bool(wall)), _prec(prec), _ptr(out),
+                                          self._stream(stream)))
         return out
 
     def lambda_moments(self, r, q, blob_start, lam, out=None, stream=None):

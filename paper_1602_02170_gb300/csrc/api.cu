@@ -3,6 +3,8 @@
 #include <cmath>
 #include <new>
 
+#include <initializer_list>
+
 #include "mb_internal.cuh"
 
 namespace mb {
@@ -185,6 +187,7 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
                       &ctx->sol_dx, &ctx->sol_ym, &ctx->pc_type, &ctx->pc_theta, &ctx->pc_ref,
+                      &ctx->eval_hi, &ctx->eval_lo, &ctx->render_r, &ctx->render_f,
                       &ctx->batch_ws};
     for (auto &g : ctx->iter_graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -319,6 +322,61 @@ mb_status mb_KT_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const 
     launch_KT_apply(n_bodies, r, q, blob_start, lambda, FT, 1.0, (cudaStream_t)stream);
     MB_CUDA_TRY(ctx, cudaGetLastError());
     return MB_OK;
+}
+
+static mb_status all_device(mb_context *ctx, std::initializer_list<const void *> ptrs)
+{
+    for (const void *p : ptrs) {
+        bool dev = false;
+        MB_TRY(pointer_kind(ctx, p, &dev));
+        if (!dev) return set_err(ctx, MB_EINVAL, "arrays must be device pointers");
+    }
+    return MB_OK;
+}
+
+mb_status mb_mobility_eval(mb_context *ctx, const double *x, int64_t n_points, const double *r,
+                           const double *f, int64_t n_blobs, double a, double eta, int wall,
+                           mb_precision prec, double *u, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (n_points < 0 || n_blobs < 0) return set_err(ctx, MB_EINVAL, "negative size");
+    if (bad_phys(a, eta)) return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
+    if (prec != MB_FP64 && prec != MB_FP32_KAHAN)
+        return set_err(ctx, MB_EINVAL, "flow evaluation supports MB_FP32_KAHAN and MB_FP64");
+    if (n_points == 0) return MB_OK;
+    if (!x || !u) return set_err(ctx, MB_EINVAL, "null array pointer");
+    if (n_blobs == 0) {
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n_points,
+                                         (cudaStream_t)stream));
+        return MB_OK;
+    }
+    if (!r || !f) return set_err(ctx, MB_EINVAL, "null array pointer");
+    MB_TRY(all_device(ctx, {x, r, f, u}));
+    return matvec_eval(ctx, x, n_points, r, f, n_blobs, a, eta, wall, prec, u,
+                       (cudaStream_t)stream);
+}
+
+mb_status mb_render_flow(mb_context *ctx, const double *x, int64_t n_points, const double *r,
+                         const double *lambda, int64_t n_blobs, const double *sub_offsets,
+                         int n_sub, double a_sub, double eta, int wall, mb_precision prec,
+                         double *v, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (n_points < 0 || n_blobs < 0 || n_sub < 1) return set_err(ctx, MB_EINVAL, "bad sizes");
+    if (bad_phys(a_sub, eta)) return set_err(ctx, MB_EINVAL, "a_sub and eta must be positive");
+    if (prec != MB_FP64 && prec != MB_FP32_KAHAN)
+        return set_err(ctx, MB_EINVAL, "flow rendering supports MB_FP32_KAHAN and MB_FP64");
+    if (n_points == 0) return MB_OK;
+    if (!x || !v || (n_blobs > 0 && (!r || !lambda || !sub_offsets)))
+        return set_err(ctx, MB_EINVAL, "null array pointer");
+    if (n_blobs == 0) {
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(v, 0, sizeof(double) * 3 * (size_t)n_points,
+                                         (cudaStream_t)stream));
+        return MB_OK;
+    }
+    MB_TRY(all_device(ctx, {x, r, lambda, sub_offsets, v}));
+    return render_flow(ctx, x, n_points, r, lambda, n_blobs, sub_offsets, n_sub, a_sub, eta, wall,
+                       prec, v, (cudaStream_t)stream);
 }
 
 mb_status mb_lambda_moments(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,

@@ -68,6 +68,8 @@ struct mb_context {
     mb::DevBuf pos_hi, pos_lo;   // packed float4 positions (FP32 path)
     mb::DevBuf partial;          // per-source-chunk partial velocities (FP64)
     mb::DevBuf stage_r, stage_f, stage_u;  // staging for host-pointer calls
+    mb::DevBuf eval_hi, eval_lo;           // packed flow-evaluation points (FP32 path)
+    mb::DevBuf render_r, render_f;         // refined blobs of a flow rendering
 
     // preconditioner (last mb_precond_setup / mb_precond_setup_shared)
     mb::DevBuf pinv;             // explicit inverses, (3n_p+6)^2 doubles each: one per
@@ -128,6 +130,14 @@ mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64
 int tune_key(int64_t n, int wall);
 // Pack positions once (FP32 path); the matvec then only reads f.
 mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s);
+// u(x_t) = sum_j M(x_t, r_j) f_j at nt points x (targets) from ns blobs.
+mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double *r,
+                      const double *f, int64_t ns, double a, double eta, int wall,
+                      mb_precision prec, double *u, cudaStream_t s);
+// Appendix B flow rendering: blobs refined into n_sub blobs of radius a_sub.
+mb_status render_flow(mb_context *ctx, const double *x, int64_t nt, const double *r,
+                      const double *lam, int64_t n, const double *off, int n_sub, double a_sub,
+                      double eta, int wall, mb_precision prec, double *v, cudaStream_t s);
 mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
                         double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
 

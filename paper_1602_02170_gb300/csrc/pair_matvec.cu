@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NT, NT == kNT ? (NP == 1 ? 3 : 2) : 16) pair_f
         const int64_t sc = item / n_tblocks;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        x2_item<WALL, NP, NT>(sP, hi, lo, f, n, tb, j_begin, j_end, k,
+        x2_item<WALL, NP, NT>(sP, hi, lo, n, hi, lo, f, tb, j_begin, j_end, k,
                               direct ? out : out + 3 * sc * n, direct ? scale : 1.0);
     }
 }
@@ -182,13 +182,71 @@ __global__ void __launch_bounds__(NT) pair_f64_kernel(
         const int64_t sc = item / n_tblocks;
         const int64_t j_begin = sc * chunk;
         const int64_t j_end = j_begin + chunk < n ? j_begin + chunk : n;
-        f64_item<WALL, NT>(sm, r, f, n, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
+        f64_item<WALL, NT>(sm, r, n, r, f, tb, j_begin, j_end, k, direct ? out : out + 3 * sc * n,
                            direct ? scale : 1.0);
     }
 }
 
 // Double-float kernel: symmetric over the upper-triangular pairs of blocks
 // of kNT blobs (one target per thread); see dfsym_item.
+// Flow evaluation at points other than the blobs (targets != sources):
+// packed FP32 and FP64 items over (target block, source chunk), partials
+// reduced like the matvec's.  The targets are tracers of the blob radius a
+// (Appendix B renders flows with small blobs of radius a').
+template <bool WALL>
+__global__ void __launch_bounds__(kNT, 3) eval_f32x2_kernel(
+    const float4 *__restrict__ thi, const float4 *__restrict__ tlo, int64_t nt,
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t ns, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts2 k,
+    double *__restrict__ out, double scale, int direct)
+{
+    __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < ns ? j_begin + chunk : ns;
+        x2_item<WALL, 1, kNT>(sP, thi, tlo, nt, hi, lo, f, tb, j_begin, j_end, k,
+                              direct ? out : out + 3 * sc * nt, direct ? scale : 1.0);
+    }
+}
+
+template <bool WALL>
+__global__ void __launch_bounds__(kNT) eval_f64_kernel(
+    const double *__restrict__ x, int64_t nt, const double *__restrict__ r,
+    const double *__restrict__ f, int64_t ns, int64_t chunk, int n_tblocks, int64_t n_items,
+    PairConsts<double> k, double *__restrict__ out, double scale, int direct)
+{
+    __shared__ double sm[6 * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t sc = item / n_tblocks;
+        const int64_t j_begin = sc * chunk;
+        const int64_t j_end = j_begin + chunk < ns ? j_begin + chunk : ns;
+        f64_item<WALL, kNT>(sm, x, nt, r, f, tb, j_begin, j_end, k,
+                            direct ? out : out + 3 * sc * nt, direct ? scale : 1.0);
+    }
+}
+
+// Appendix B: each blob i becomes n_sub blobs at r_i + off_k carrying
+// lambda_i / n_sub each (k fastest).
+__global__ void refine_blobs_kernel(const double *__restrict__ r, const double *__restrict__ lam,
+                                    int64_t n, const double *__restrict__ off, int n_sub,
+                                    double *__restrict__ rs, double *__restrict__ ls)
+{
+    const double w = 1.0 / n_sub;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n_sub;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n_sub;
+        const int k = (int)(e % n_sub);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rs[3 * e + c] = r[3 * i + c] + off[3 * k + c];
+            ls[3 * e + c] = lam[3 * i + c] * w;
+        }
+    }
+}
+
 template <bool WALL, int NT = kNT>
 __global__ void __launch_bounds__(NT) pair_df_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
@@ -233,15 +291,17 @@ struct Plan {
 // Split sources into S chunks so that the items fill whole waves of the
 // resident grid as evenly as possible, with chunks of at least two tiles.
 Plan make_plan(int64_t n, int targets_per_cta, int resident, int64_t s_cap = 64, int tile = kNT,
-               int64_t min_chunk = 2 * kNT)
+               int64_t min_chunk = 2 * kNT, int64_t n_src = -1)
 {
+    // n targets; n_src sources (the same blobs unless given)
+    const int64_t ns = n_src < 0 ? n : n_src;
     Plan p;
     p.n_tblocks = (int)ceil_div(n, targets_per_cta);
-    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(s_cap, ceil_div(n, min_chunk)));
+    const int64_t max_s = std::max<int64_t>(1, std::min<int64_t>(s_cap, ceil_div(ns, min_chunk)));
     double best = -1.0;
     for (int64_t s = 1; s <= max_s; ++s) {
-        const int64_t chunk = ceil_div(ceil_div(n, s), tile) * tile;
-        const int64_t s_eff = ceil_div(n, chunk);
+        const int64_t chunk = ceil_div(ceil_div(ns, s), tile) * tile;
+        const int64_t s_eff = ceil_div(ns, chunk);
         const int64_t items = (int64_t)p.n_tblocks * s_eff;
         const int64_t waves = ceil_div(items, resident);
         double eff = (double)items / (double)(waves * resident);
@@ -535,6 +595,95 @@ mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64
 {
     if (prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
     return matvec_packed(ctx, r, f, n, a, eta, wall, prec, u, s);
+}
+
+mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double *r,
+                      const double *f, int64_t ns, double a, double eta, int wall,
+                      mb_precision prec, double *u, cudaStream_t s)
+{
+    const double scale = 1.0 / (6.0 * kPi * eta * a);
+    if (prec == MB_FP64) {
+        const int res = wall ? resident_ctas(ctx, eval_f64_kernel<true>)
+                             : resident_ctas(ctx, eval_f64_kernel<false>);
+        const Plan p = make_plan(nt, kNT, res, 64, kNT, 2 * kNT, ns);
+        double *out = u;
+        const int direct = p.S == 1;
+        if (!direct) {
+            MB_TRY(ensure(ctx, ctx->partial, sizeof(double) * 3 * (size_t)nt * p.S, "eval partials"));
+            out = (double *)ctx->partial.ptr;
+        }
+        const PairConsts<double> k = PairConsts<double>::make(a);
+        if (wall)
+            eval_f64_kernel<true><<<p.grid, kNT, 0, s>>>(x, nt, r, f, ns, p.chunk, p.n_tblocks,
+                                                         p.items, k, out, scale, direct);
+        else
+            eval_f64_kernel<false><<<p.grid, kNT, 0, s>>>(x, nt, r, f, ns, p.chunk, p.n_tblocks,
+                                                          p.items, k, out, scale, direct);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        if (!direct) {
+            const int grid = (int)std::min<int64_t>(ceil_div(3 * nt, 256), 8 * (int64_t)ctx->sm_count);
+            reduce_partials_kernel<<<grid, 256, 0, s>>>(out, nt, p.S, scale, u);
+            count_launch();
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+        }
+        return MB_OK;
+    }
+    if (prec != MB_FP32_KAHAN)
+        return set_err(ctx, MB_EINVAL, "flow evaluation supports MB_FP32_KAHAN and MB_FP64");
+    // sources packed into the context's position buffers, targets into the eval ones
+    MB_TRY(matvec_pack_positions(ctx, r, ns, s));
+    MB_TRY(ensure(ctx, ctx->eval_hi, sizeof(float4) * (size_t)nt, "packed targets"));
+    MB_TRY(ensure(ctx, ctx->eval_lo, sizeof(float4) * (size_t)nt, "packed targets"));
+    {
+        const int grid = (int)std::min<int64_t>(ceil_div(nt, 256), 8 * (int64_t)ctx->sm_count);
+        pack_hilo_kernel<<<grid, 256, 0, s>>>(x, nt, (float4 *)ctx->eval_hi.ptr,
+                                              (float4 *)ctx->eval_lo.ptr);
+        count_launch();
+    }
+    const int res = wall ? resident_ctas(ctx, eval_f32x2_kernel<true>)
+                         : resident_ctas(ctx, eval_f32x2_kernel<false>);
+    const Plan p = make_plan(nt, 2 * kNT, res, 64, kNT, 2 * kNT, ns);
+    double *out = u;
+    const int direct = p.S == 1;
+    if (!direct) {
+        MB_TRY(ensure(ctx, ctx->partial, sizeof(double) * 3 * (size_t)nt * p.S, "eval partials"));
+        out = (double *)ctx->partial.ptr;
+    }
+    const PairConsts2 k = PairConsts2::make(a);
+    const float4 *thi = (const float4 *)ctx->eval_hi.ptr, *tlo = (const float4 *)ctx->eval_lo.ptr;
+    const float4 *hi = (const float4 *)ctx->pos_hi.ptr, *lo = (const float4 *)ctx->pos_lo.ptr;
+    if (wall)
+        eval_f32x2_kernel<true><<<p.grid, kNT, 0, s>>>(thi, tlo, nt, hi, lo, f, ns, p.chunk,
+                                                       p.n_tblocks, p.items, k, out, scale, direct);
+    else
+        eval_f32x2_kernel<false><<<p.grid, kNT, 0, s>>>(thi, tlo, nt, hi, lo, f, ns, p.chunk,
+                                                        p.n_tblocks, p.items, k, out, scale, direct);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (!direct) {
+        const int grid = (int)std::min<int64_t>(ceil_div(3 * nt, 256), 8 * (int64_t)ctx->sm_count);
+        reduce_partials_kernel<<<grid, 256, 0, s>>>(out, nt, p.S, scale, u);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return MB_OK;
+}
+
+mb_status render_flow(mb_context *ctx, const double *x, int64_t nt, const double *r,
+                      const double *lam, int64_t n, const double *off, int n_sub, double a_sub,
+                      double eta, int wall, mb_precision prec, double *v, cudaStream_t s)
+{
+    const int64_t ns = n * (int64_t)n_sub;
+    MB_TRY(ensure(ctx, ctx->render_r, sizeof(double) * 3 * (size_t)ns, "refined blobs"));
+    MB_TRY(ensure(ctx, ctx->render_f, sizeof(double) * 3 * (size_t)ns, "refined blob forces"));
+    const int grid = (int)std::min<int64_t>(ceil_div(ns, 256), 8 * (int64_t)ctx->sm_count);
+    refine_blobs_kernel<<<grid, 256, 0, s>>>(r, lam, n, off, n_sub, (double *)ctx->render_r.ptr,
+                                             (double *)ctx->render_f.ptr);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    return matvec_eval(ctx, x, nt, (const double *)ctx->render_r.ptr,
+                       (const double *)ctx->render_f.ptr, ns, a_sub, eta, wall, prec, v, s);
 }
 
 // ---------------------------------------------------------------------------

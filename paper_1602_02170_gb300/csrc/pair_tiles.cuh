@@ -4,7 +4,10 @@
 // One call processes one work item: the targets of target block `tb` of one
 // problem against that problem's sources [j_begin, j_end).  Pointers are
 // already offset to the problem; `out` receives the item's velocities at
-// out + 3 i (i = target index within the problem) multiplied by `m`.
+// out + 3 i (i = target index within the problem) multiplied by `m`.  The
+// non-symmetric items take the targets (n of them) from their own arrays,
+// which are the source arrays themselves for a matvec and other points when
+// a flow is evaluated away from the blobs.
 #pragma once
 
 #include "df32.cuh"
@@ -30,9 +33,11 @@ constexpr int kX2SmemFloat4PerSource = 5;
 //   sP[5s+2] = (-x_lo, -x_lo, -y_lo, -y_lo)   sP[5s+3] = (-z_lo, -z_lo, f_x, f_x)
 //   sP[5s+4] = (f_y, f_y, f_z, f_z)
 template <bool WALL, int NP, int NT>
-__device__ __forceinline__ void x2_item(float4 *__restrict__ sP, const float4 *__restrict__ hi,
+__device__ __forceinline__ void x2_item(float4 *__restrict__ sP, const float4 *__restrict__ thi,
+                                        const float4 *__restrict__ tlo, int64_t n,
+                                        const float4 *__restrict__ hi,
                                         const float4 *__restrict__ lo,
-                                        const double *__restrict__ f, int64_t n, int tb,
+                                        const double *__restrict__ f, int tb,
                                         int64_t j_begin, int64_t j_end, const PairConsts2 &k,
                                         double *__restrict__ out, double m)
 {
@@ -45,8 +50,8 @@ __device__ __forceinline__ void x2_item(float4 *__restrict__ sP, const float4 *_
         for (int hh = 0; hh < 2; ++hh) {
             int64_t i = (int64_t)tb * NT * 2 * NP + (2 * q + hh) * NT + threadIdx.x;
             i = i < n ? i : n - 1;
-            h[hh] = hi[i];
-            l[hh] = lo[i];
+            h[hh] = thi[i];
+            l[hh] = tlo[i];
         }
         xh[q] = make_float2(h[0].x, h[1].x);
         yh[q] = make_float2(h[0].y, h[1].y);
@@ -122,8 +127,9 @@ __device__ __forceinline__ void x2_item(float4 *__restrict__ sP, const float4 *_
 
 // FP64 item: one target per thread, sources staged as six double arrays.
 template <bool WALL, int NT>
-__device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *__restrict__ r,
-                                         const double *__restrict__ f, int64_t n, int tb,
+__device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *__restrict__ tr,
+                                         int64_t n, const double *__restrict__ r,
+                                         const double *__restrict__ f, int tb,
                                          int64_t j_begin, int64_t j_end,
                                          const PairConsts<double> &k, double *__restrict__ out,
                                          double m)
@@ -132,7 +138,7 @@ __device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *
            *sfz = sm + 5 * NT;
     const int64_t i = (int64_t)tb * NT + threadIdx.x;
     const int64_t ic = i < n ? i : n - 1;
-    const double xi = r[3 * ic], yi = r[3 * ic + 1], zi = r[3 * ic + 2];
+    const double xi = tr[3 * ic], yi = tr[3 * ic + 1], zi = tr[3 * ic + 2];
     double ux = 0.0, uy = 0.0, uz = 0.0;
     for (int64_t jt = j_begin; jt < j_end; jt += NT) {
         __syncthreads();

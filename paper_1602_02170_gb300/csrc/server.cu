@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kNT, NP == 1 ? 3 : 2) eng_x2_kernel(
         const int tb = (int)(local % P.n_tblocks);
         const int64_t sc = local / P.n_tblocks;
         const int64_t j0 = sc * P.chunk, j1 = j0 + P.chunk < P.n ? j0 + P.chunk : P.n;
-        x2_item<WALL, NP, kNT>(sP, P.hi, P.lo, P.f, P.n, tb, j0, j1, k,
+        x2_item<WALL, NP, kNT>(sP, P.hi, P.lo, P.n, P.hi, P.lo, P.f, tb, j0, j1, k,
                                P.S == 1 ? P.y : P.part + 3 * sc * P.n, P.S == 1 ? scale : 1.0);
     }
 }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kNT) eng_f64_kernel(const Work *__restrict__ W
         const int tb = (int)(local % P.n_tblocks);
         const int64_t sc = local / P.n_tblocks;
         const int64_t j0 = sc * P.chunk, j1 = j0 + P.chunk < P.n ? j0 + P.chunk : P.n;
-        f64_item<WALL, kNT>(sm, P.r, P.f, P.n, tb, j0, j1, k,
+        f64_item<WALL, kNT>(sm, P.r, P.n, P.r, P.f, tb, j0, j1, k,
                             P.S == 1 ? P.y : P.part + 3 * sc * P.n, P.S == 1 ? scale : 1.0);
     }
 }

@@ -374,3 +374,42 @@ def test_squirmer_speed_converges_linearly_in_blob_radius():
     (e1, a1), (e2, a2) = eps
     assert 0 < e2 < e1
     assert abs((e2 / a2) / (e1 / a1) - 1.0) <= 0.05   # the same slope: linear in a
+
+
+# ------------------------------------------------------------ flow evaluation (Appendix B)
+def test_eval_far_field_is_oseen():
+    """Far from a blob the velocity of a tracer blob is the Oseen tensor of
+    the force, (8 pi eta d)^-1 (I + d d^T / d^2) f, up to O(a^2/d^2)."""
+    rng = _rng(9)
+    a, eta = 0.3, 1.7
+    r = rng.uniform(-1, 1, (1, 3))
+    f = rng.standard_normal((1, 3))
+    for _ in range(5):
+        e = rng.standard_normal(3)
+        e /= np.linalg.norm(e)
+        d = 3000 * a
+        x = r + d * e
+        u = O.eval_points(x, r, f, a, eta, wall=False)[0]
+        ref = (np.eye(3) + np.outer(e, e)) @ f[0] / (8 * PI * eta * d)
+        assert np.abs(u - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_render_flow_limits():
+    """Appendix B rendering: (1) one sub-blob at the centre with the blob's
+    own radius reproduces the blob velocities M lambda; (2) far away the
+    rendered flow is the Oseen field of the total force, whatever the split."""
+    s = I.config_small_suspension(1)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    lam = _rng(4).standard_normal((s.n_blobs, 3))
+    v = O.render_flow(r[:7], r, lam, np.zeros((1, 3)), s.a, 1.0, True)
+    np.testing.assert_allclose(v, O.matvec(r, lam, s.a, 1.0, True, targets=np.arange(7)),
+                               rtol=1e-13, atol=1e-13)
+    rho12 = I.shell(12) * s.a
+    one = r[:1]
+    F = lam[:1]
+    far = one + np.array([[800.0, -300.0, 500.0]])
+    v1 = O.render_flow(far, one, F, rho12, 0.05 * s.a, 1.0, False)[0]
+    d = far[0] - one[0]
+    dn = np.linalg.norm(d)
+    ref = (np.eye(3) + np.outer(d, d) / dn ** 2) @ F[0] / (8 * PI * dn)
+    assert np.abs(v1 - ref).max() <= 1e-6 * np.abs(ref).max()
