@@ -350,6 +350,22 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
                             mb_info *info, void *stream);
 
 /*
+ * mb_solve_mobility for permeable bodies (Appendix C): the slip of blob i of
+ * body p gains -kappa_p / (eta dV_i) lambda_i, which adds
+ * shift_i = kappa_p / (eta dV_i) to the three diagonal entries of M for blob
+ * i (in the units of M: velocity per force).  shift: N values (device), one
+ * per blob, >= 0; zero recovers impermeable bodies.  The per-body blocks of
+ * the preconditioner include the shift (params->precond must be
+ * MB_PRECOND_WALL).  Otherwise as mb_solve_mobility.
+ */
+mb_status mb_solve_mobility_permeable(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                                     const double *q, const double *theta,
+                                     const int64_t *blob_start, const double *rho,
+                                     const double *F, const double *T, const double *slip,
+                                     const double *shift, const mb_params *params, double *U,
+                                     double *Omega, double *lambda, mb_info *info, void *stream);
+
+/*
  * Solve the resistance problem (Eq. resistance_problem):
  *   M lambda = K [U; Omega] + slip,   (F, T) = K^T lambda,
  * for the blob forces lambda that move the bodies rigidly with prescribed

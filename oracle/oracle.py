@@ -16,7 +16,9 @@ Functions and the passages they follow:
                                     correction of Section 2.1.1
   K_matrix, K_apply, KT_apply       Eq. noslip_rigid and the force/torque
                                     balance rows of Eq. rigidSystem
-  saddle_matrix, solve_saddle       Eq. saddle_M solved directly (LU)
+  saddle_matrix, solve_saddle       Eq. saddle_M solved directly (LU); the
+                                    permeable-body diagonal of Eq.
+                                    permeable_slip (Appendix C) as an option
   solve_schur                       Eq. BodyMob: U = N (F - K^T M^-1 slip),
                                     lambda = M^-1 (K U + slip), by Cholesky
   precond_apply                     Eq. saddle_M_precon with the block-diagonal
@@ -235,15 +237,20 @@ def _body_vec(F, T):
     return np.concatenate([F, T], axis=1).reshape(-1)
 
 
-def saddle_matrix(r, q, blob_start, a, eta=1.0, wall=True):
-    """[[M, -K], [-K^T, 0]] of Eq. saddle_M."""
+def saddle_matrix(r, q, blob_start, a, eta=1.0, wall=True, shift=None):
+    """[[M, -K], [-K^T, 0]] of Eq. saddle_M.  shift (N values or None) adds
+    kappa_p / (eta dV_i) to the diagonal of M for the blobs of permeable
+    bodies (Eq. permeable_slip, Appendix C)."""
     M = mobility_matrix(r, a, eta, wall)
+    if shift is not None:
+        M = M + np.diag(np.repeat(_c(shift).reshape(-1), 3))
     K = K_matrix(r, q, blob_start)
     nb6 = K.shape[1]
     return np.block([[M, -K], [-K.T, np.zeros((nb6, nb6))]])
 
 
-def solve_saddle(r, q, blob_start, F, T, a, eta=1.0, wall=True, slip=None, pinv=False):
+def solve_saddle(r, q, blob_start, F, T, a, eta=1.0, wall=True, slip=None, pinv=False,
+                 shift=None):
     """Direct LU solve of Eq. saddle_M; returns (U, Omega, lambda).
 
     pinv=True takes the minimum-norm least-squares solution instead, the
@@ -251,7 +258,7 @@ def solve_saddle(r, q, blob_start, F, T, a, eta=1.0, wall=True, slip=None, pinv=
     singular (e.g. blobs on a line cannot spin about it)."""
     n = r.shape[0]
     nb = q.shape[0]
-    A = saddle_matrix(r, q, blob_start, a, eta, wall)
+    A = saddle_matrix(r, q, blob_start, a, eta, wall, shift)
     s = np.zeros(3 * n) if slip is None else _c(slip).reshape(-1)
     b = np.concatenate([s, -_body_vec(F, T)])
     x = np.linalg.lstsq(A, b, rcond=1e-12)[0] if pinv else np.linalg.solve(A, b)

@@ -63,6 +63,7 @@ EXPORTED_SYMBOLS = [
     "mb_precond_apply",
     "mb_solve_mobility",
     "mb_solve_resistance",
+    "mb_solve_mobility_permeable",
     "mb_solve_batch",
     "mb_server_create",
     "mb_server_destroy",
@@ -190,6 +191,10 @@ def load_library():
     L.mb_precond_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.mb_solve_mobility.argtypes = [
         vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
+        ctypes.POINTER(Info), vp,
+    ]
+    L.mb_solve_mobility_permeable.argtypes = [
+        vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Params), vp, vp, vp,
         ctypes.POINTER(Info), vp,
     ]
     L.mb_solve_resistance.argtypes = [
@@ -452,10 +457,11 @@ class Context:
 
     def solve_mobility(self, q, theta, blob_start, rho, F, T, a, eta=1.0, wall=True, slip=None,
                        tol=1e-10, maxit=200, restart=100, prec="fp64", stream=None,
-                       raise_on_nonconvergence=True, precond="wall"):
+                       raise_on_nonconvergence=True, precond="wall", shift=None):
         """Solve Eq. saddle_M; returns (U, Omega, lambda, info dict).
         precond: "wall" (per-body blocks with the wall) or "free_shared"
-        (unbounded-domain blocks, one per body shape)."""
+        (unbounded-domain blocks, one per body shape).  shift: per-blob
+        kappa_p / (eta dV_i) of permeable bodies (Appendix C), or None."""
         torch = self._torch
         nb, n = int(q.shape[0]), int(rho.shape[0])
         self._dev(q, (nb, 3)); self._dev(theta, (nb, 4)); self._dev(rho, (n, 3))
@@ -469,6 +475,16 @@ class Context:
         p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
                    _prec(prec), _precond(precond))
         info = Info()
+        if shift is not None:
+            self._dev(shift, (n,))
+            st = self.L.mb_solve_mobility_permeable(
+                self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(F),
+                _ptr(T), _ptr(slip), _ptr(shift), ctypes.byref(p), _ptr(U), _ptr(Om), _ptr(lam),
+                ctypes.byref(info), self._stream(stream))
+            if st == 4 and not raise_on_nonconvergence:
+                return U, Om, lam, info.as_dict()
+            self._check(st)
+            return U, Om, lam, info.as_dict()
         st = self.L.mb_solve_mobility(
             self.handle, nb, n, _ptr(q), _ptr(theta), _ptr(blob_start), _ptr(rho), _ptr(F),
             _ptr(T), _ptr(slip), ctypes.byref(p), _ptr(U), _ptr(Om), _ptr(lam),

@@ -324,7 +324,7 @@ mb_status mb_KT_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const 
     return MB_OK;
 }
 
-static mb_status all_device(mb_context *ctx, std::initializer_list<const void *> ptrs)
+mb_status all_device(mb_context *ctx, std::initializer_list<const void *> ptrs)
 {
     for (const void *p : ptrs) {
         bool dev = false;
@@ -447,6 +447,37 @@ mb_status mb_solve_mobility(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, 
     if (n_blobs > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
     return solve_mobility(ctx, n_bodies, n_blobs, q, theta, blob_start, rho, F, T, slip, params, U,
                           Omega, lambda, info, (cudaStream_t)stream);
+}
+
+mb_status all_device(mb_context *ctx, std::initializer_list<const void *> ptrs);
+
+mb_status mb_solve_mobility_permeable(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,
+                                     const double *q, const double *theta,
+                                     const int64_t *blob_start, const double *rho,
+                                     const double *F, const double *T, const double *slip,
+                                     const double *shift, const mb_params *params, double *U,
+                                     double *Omega, double *lambda, mb_info *info, void *stream)
+{
+    MB_TRY(check_ctx(ctx));
+    if (!params) return set_err(ctx, MB_EINVAL, "null params");
+    if (!shift) return set_err(ctx, MB_EINVAL, "null shift (use mb_solve_mobility)");
+    if (params->precond != MB_PRECOND_WALL)
+        return set_err(ctx, MB_EINVAL, "permeable bodies use MB_PRECOND_WALL (per-blob shifts "
+                                       "make every body's block its own)");
+    MB_TRY(all_device(ctx, {shift}));
+    if (n_bodies <= 0 || n_blobs <= 0) return set_err(ctx, MB_EINVAL, "need at least one body");
+    if (bad_phys(params->a, params->eta))
+        return set_err(ctx, MB_EINVAL, "a and eta must be positive and finite");
+    if (!(params->tol > 0.0) || params->maxit < 1 || params->restart < 1)
+        return set_err(ctx, MB_EINVAL, "tol > 0, maxit >= 1 and restart >= 1 required");
+    if (params->prec != MB_FP64 && params->prec != MB_FP32_KAHAN &&
+        params->prec != MB_MIXED_REFINE && params->prec != MB_DF64)
+        return set_err(ctx, MB_EINVAL, "unknown precision mode");
+    if (!q || !theta || !blob_start || !rho || !F || !T || !U || !Omega || !lambda)
+        return set_err(ctx, MB_EINVAL, "null array pointer");
+    if (n_blobs > (int64_t)1 << 31) return set_err(ctx, MB_EINVAL, "N above 2^31 is not supported");
+    return solve_mobility(ctx, n_bodies, n_blobs, q, theta, blob_start, rho, F, T, slip, params, U,
+                          Omega, lambda, info, (cudaStream_t)stream, shift);
 }
 
 mb_status mb_solve_resistance(mb_context *ctx, int64_t n_bodies, int64_t n_blobs,

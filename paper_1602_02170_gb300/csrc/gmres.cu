@@ -369,6 +369,16 @@ __global__ void build_rhs_resist_kernel(int64_t nb, int64_t n, const double *__r
     }
 }
 
+// y_i += shift_i x_i on the blob part (permeable bodies: Appendix C adds
+// kappa_p / (eta dV_i) to the diagonal of M)
+__global__ void add_shift_kernel(double *__restrict__ y, const double *__restrict__ x,
+                                 const double *__restrict__ shift, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] += shift[e / 3] * x[e];
+}
+
 // F, T from the packed n_b x 6 K^T lambda
 __global__ void split_ft_kernel(int64_t nb, const double *__restrict__ FT, double *__restrict__ F,
                                 double *__restrict__ T)
@@ -384,6 +394,7 @@ __global__ void split_ft_kernel(int64_t nb, const double *__restrict__ FT, doubl
 struct Solver {
     mb_context *ctx;
     bool resist = false;  // A = M alone (resistance problem), L = 3N
+    const double *shift = nullptr;  // per-blob diagonal addition to M, or null
     cudaStream_t s;
     int64_t n, nb, L;
     const double *r, *q;
@@ -399,6 +410,10 @@ struct Solver {
     mb_status apply_A(const double *xin, double *y, mb_precision prec)
     {
         MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s));
+        if (shift) {
+            add_shift_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, xin, shift, n);
+            count_launch();
+        }
         if (resist) return MB_OK;
         launch_K_apply(nb, n, r, q, start, xin + 3 * n, y, -1.0, 1.0, s);
         launch_KT_apply(nb, r, q, start, xin, y + 3 * n, -1.0, s);
@@ -411,6 +426,10 @@ struct Solver {
                                   mb_precision prec)
     {
         MB_TRY(matvec_packed(ctx, r, dx, n, a, eta, wall, prec, y, s));
+        if (shift) {
+            add_shift_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, dx, shift, n);
+            count_launch();
+        }
         accumulate_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, ym, 3 * n);
         count_launch();
         if (resist) return MB_OK;
@@ -541,7 +560,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                              const double *theta, const int64_t *blob_start, const double *rho,
                              const double *in_a, const double *in_b, const double *slip,
                              const mb_params *p, double *out_a, double *out_b, double *lambda,
-                             mb_info *info, cudaStream_t s)
+                             mb_info *info, cudaStream_t s, const double *shift)
 {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
@@ -570,13 +589,15 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     if (p->precond == MB_PRECOND_FREE_SHARED)
         MB_TRY(precond_setup_shared(ctx, nb, n, theta, blob_start, rho, p->a, p->eta, s, !resist));
     else
-        MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s, !resist));
+        MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s, !resist,
+                             shift));
     if (p->prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
     MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const auto t1 = clk::now();
 
     Solver S;
     S.resist = resist != 0;
+    S.shift = shift;
     S.ctx = ctx; S.s = s; S.n = n; S.nb = nb; S.L = L; S.r = r; S.q = q;
     S.start = (const int64_t *)ctx->blob_start_copy.ptr;
     S.a = p->a; S.eta = p->eta; S.wall = p->wall; S.m = m; S.sl = sl;
@@ -680,6 +701,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         sig.wall = p->wall; sig.variant = ctx->pair_variant;
                         sig.pc_max_np = ctx->pc_max_np; sig.pc_kind = ctx->pc_kind;
                         sig.mode = resist;
+                        sig.shift = shift;
                         sig.n = n; sig.nb = nb; sig.L = L;
                         sig.pc_nb = ctx->pc_nb; sig.a = p->a; sig.eta = p->eta; sig.q = q;
                         sig.V = S.V; sig.Z = S.Z; sig.sm = S.sm;
@@ -754,10 +776,10 @@ mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q
                          const double *theta, const int64_t *blob_start, const double *rho,
                          const double *F, const double *T, const double *slip,
                          const mb_params *p, double *U, double *Omega, double *lambda,
-                         mb_info *info, cudaStream_t s)
+                         mb_info *info, cudaStream_t s, const double *shift)
 {
     return solve_rigid(ctx, 0, nb, n, q, theta, blob_start, rho, F, T, slip, p, U, Omega, lambda,
-                       info, s);
+                       info, s, shift);
 }
 
 mb_status solve_resistance(mb_context *ctx, int64_t nb, int64_t n, const double *q,
@@ -767,7 +789,7 @@ mb_status solve_resistance(mb_context *ctx, int64_t nb, int64_t n, const double 
                            mb_info *info, cudaStream_t s)
 {
     return solve_rigid(ctx, 1, nb, n, q, theta, blob_start, rho, U, Omega, slip, p, F, T, lambda,
-                       info, s);
+                       info, s, nullptr);
 }
 
 }  // namespace mb

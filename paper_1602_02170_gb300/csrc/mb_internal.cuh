@@ -29,6 +29,7 @@ struct DevBuf {
 struct IterSig {
     uint64_t gen = 0;
     int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0, mode = 0;
+    const void *shift = nullptr;
     int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
     double a = 0.0, eta = 0.0;
     const void *q = nullptr, *V = nullptr, *Z = nullptr, *sm = nullptr;
@@ -36,7 +37,7 @@ struct IterSig {
     {
         return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
                variant == o.variant && pc_max_np == o.pc_max_np && pc_kind == o.pc_kind &&
-               mode == o.mode &&
+               mode == o.mode && shift == o.shift &&
                n == o.n && nb == o.nb &&
                L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
                V == o.V && Z == o.Z && sm == o.sm;
@@ -158,9 +159,11 @@ void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t
 
 // Preconditioner (precond.cu)
 // schur = 0 keeps only the blob blocks M_pp^-1 (resistance problem).
+// shift (N per-blob values or null) is added to the diagonal of each M_pp
+// (permeable bodies, Appendix C).
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                         const double *q, const int64_t *blob_start, double a, double eta,
-                        int wall, cudaStream_t s, int schur = 1);
+                        int wall, cudaStream_t s, int schur = 1, const double *shift = nullptr);
 // Asynchronous setup of the blocks of nb bodies: start (nb+1, global blob
 // indices), poff (nb offsets into P); a failing body sets flags[flag_slot] = 2.
 mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, const double *q,
@@ -183,11 +186,13 @@ mb_status solve_resistance(mb_context *ctx, int64_t nb, int64_t n, const double 
                            const double *U, const double *Omega, const double *slip,
                            const mb_params *p, double *F, double *T, double *lambda,
                            mb_info *info, cudaStream_t s);
+// shift: N per-blob additions to the diagonal of M (kappa_p / (eta dV_i),
+// permeable bodies, Appendix C) or null.
 mb_status solve_mobility(mb_context *ctx, int64_t nb, int64_t n, const double *q,
                          const double *theta, const int64_t *blob_start, const double *rho,
                          const double *F, const double *T, const double *slip,
                          const mb_params *p, double *U, double *Omega, double *lambda,
-                         mb_info *info, cudaStream_t s);
+                         mb_info *info, cudaStream_t s, const double *shift = nullptr);
 
 // Batched solves on the serving engine (server.cu)
 mb_status solve_batch(mb_context *ctx, int np, const mb_problem *probs, const mb_params *prm,

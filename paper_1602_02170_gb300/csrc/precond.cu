@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
     const int64_t *__restrict__ start, const int64_t *__restrict__ poff, PairConsts<double> k,
     double scale, double *__restrict__ P, double *__restrict__ scratch, int64_t scratch_stride,
-    int *__restrict__ flag, int flag_slot, int schur)
+    int *__restrict__ flag, int flag_slot, int schur, const double *__restrict__ shift)
 {
     extern __shared__ double sm[];
     for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
             for (int al = 0; al < 3; ++al)
 #pragma unroll
                 for (int be = 0; be < 3; ++be)
-                    L[(3 * bi + al) * n + 3 * bj + be] = scale * blk[3 * al + be];
+                    L[(3 * bi + al) * n + 3 * bj + be] =
+                        scale * blk[3 * al + be] +
+                        (shift && bi == bj && al == be ? shift[b0 + bi] : 0.0);
         }
         __syncthreads();
 
@@ -341,7 +343,8 @@ int64_t split_stride(int nmax) { return (int64_t)nmax * nmax + 19 * (int64_t)nma
 template <bool WALL>
 __global__ void __launch_bounds__(256) pc_assemble_kernel(
     int64_t nb, const double *__restrict__ r, const int64_t *__restrict__ start,
-    const int64_t *__restrict__ poff, PairConsts<double> k, double scale, double *__restrict__ P)
+    const int64_t *__restrict__ poff, PairConsts<double> k, double scale, double *__restrict__ P,
+    const double *__restrict__ shift)
 {
     const int lane = threadIdx.x & 31;
     const int64_t s0 = start[0], rows = start[nb] - s0;
@@ -361,7 +364,8 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
             for (int al = 0; al < 3; ++al)
 #pragma unroll
                 for (int be = 0; be < 3; ++be)
-                    Pp[(size_t)(3 * bi + al) * m + 3 * bj + be] = scale * blk[3 * al + be];
+                    Pp[(size_t)(3 * bi + al) * m + 3 * bj + be] =
+                        scale * blk[3 * al + be] + (shift && bi == bj && al == be ? shift[b] : 0.0);
         }
     }
 }
@@ -674,7 +678,8 @@ __global__ void __launch_bounds__(256) pc_product_kernel(
 // Runs S1..S4 over groups of bodies whose scratch fits the cap.
 mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double *q,
                       const int64_t *start, const int64_t *poff, double *P, int max_np, double a,
-                      double eta, int wall, int *flag, int flag_slot, int schur, cudaStream_t s)
+                      double eta, int wall, int *flag, int flag_slot, int schur, cudaStream_t s,
+                      const double *shift)
 {
     const int nmax = 3 * max_np;
     const int64_t stride = split_stride(nmax);
@@ -696,9 +701,9 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
         const int64_t *po = poff + g0;
         const int ga = (int)std::min<int64_t>(ceil_div(ng * max_np, 8), 8 * (int64_t)ctx->sm_count);
         if (wall)
-            pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P);
+            pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         else
-            pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P);
+            pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         auto factor = lsmem ? pc_factor_kernel<true> : pc_factor_kernel<false>;
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)fsmem));
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(256) precond_apply_shared_kernel(
 
 mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
                         const double *q, const int64_t *blob_start, double a, double eta,
-                        int wall, cudaStream_t s, int schur)
+                        int wall, cudaStream_t s, int schur, const double *shift)
 {
     // body sizes on the host
     std::vector<int64_t> hstart(nb + 1);
@@ -845,13 +850,13 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
         if (nmax <= kSplitMaxRowsSmem)
             return setup_split(ctx, nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                (const int64_t *)ctx->pinv_off.ptr, (double *)ctx->pinv.ptr, max_np,
-                               a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s);
+                               a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s, shift);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                                (const int64_t *)ctx->pinv_off.ptr, k, scale,
                                                (double *)ctx->pinv.ptr, scratch, stride,
-                                               (int *)ctx->flag.ptr, -1, schur);
+                                               (int *)ctx->flag.ptr, -1, schur, shift);
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
@@ -905,11 +910,11 @@ mb_status precond_setup_range(mb_context *ctx, int64_t nb, const double *r, cons
     auto launch = [&](auto kern) -> mb_status {
         if (nmax <= kSplitMaxRowsSmem)
             return setup_split(ctx, nb, r, q, start, poff, P, max_np, a, eta, wall, flags,
-                               flag_slot, schur, s);
+                               flag_slot, schur, s, nullptr);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, start, poff, k, scale, P, scratch, stride,
-                                               flags, flag_slot, schur);
+                                               flags, flag_slot, schur, nullptr);
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;

@@ -319,3 +319,29 @@ def test_solve_not_converged_reports_best_iterate(ctx):
         ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a,
                            s.eta, True, tol=1e-12, maxit=2, prec="fp64")
     assert ei.value.name == "MB_ENOTCONVERGED"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_permeable_bodies_match_oracle(ctx, prec):
+    """Appendix C: kappa_p / (eta dV_i) on the diagonal of M for every blob of
+    a permeable body (one kappa per body, dV_i = 4 pi a^3 / 3); the GPU solve
+    matches the oracle's direct solve of the shifted saddle system."""
+    s = I.mixed_suspension(12, 8)
+    kappa = np.random.default_rng(3).uniform(0.01, 2.0, s.n_bodies)
+    per_blob = np.repeat(kappa, np.diff(s.blob_start))
+    shift = per_blob / (4.0 * np.pi * s.a ** 3 / 3.0)
+    d = _dev_susp(s)
+    U, W, lam, info = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"],
+                                         d["T"], s.a, 1.0, True, tol=1e-11, maxit=400,
+                                         prec=prec, shift=dev(shift))
+    assert info["converged"] == 1
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    Ur, Wr, lr = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True, shift=shift)
+    assert rel_l2(host(U), Ur) <= 1e-8 and rel_l2(host(W), Wr) <= 1e-8
+    assert rel_l2(host(lam), lr) <= 1e-7
+    # zero permeability is the rigid body
+    U0, _, _, _ = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"],
+                                     d["T"], s.a, 1.0, True, tol=1e-11, maxit=400, prec="fp64",
+                                     shift=dev(np.zeros(s.n_blobs)))
+    Ur0, _, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True)
+    assert rel_l2(host(U0), Ur0) <= 1e-8

@@ -413,3 +413,27 @@ def test_render_flow_limits():
     dn = np.linalg.norm(d)
     ref = (np.eye(3) + np.outer(d, d) / dn ** 2) @ F[0] / (8 * PI * dn)
     assert np.abs(v1 - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------ permeable bodies (Appendix C)
+def test_permeable_body_darcy_limit():
+    """Eq. permeable_slip: with a large shift d = kappa / (eta dV) on every
+    blob the body is nearly transparent, lambda ~ K U / d, and the force
+    balance K^T lambda = F gives U -> d F / N_b (the translational block of
+    K^T K is N_b I when the blobs are centred on the tracking point).  The
+    relative deviation is of order N_b times the body's mobility scale
+    1/(6 pi eta R_g) over d, and falls like 1/d."""
+    rho = I.shell(42)
+    a = 0.5 * I.min_spacing(rho)
+    F = np.array([[0.3, -1.1, 0.7]])
+    z = np.zeros((1, 3))
+    dev_prev = None
+    for d in (1e3, 1e5):
+        U, W, _ = O.solve_saddle(rho, z, np.array([0, 42]), F, z, a, 1.0, False,
+                                 shift=np.full(42, d))
+        dev = np.linalg.norm(U[0] * 42 / d - F[0]) / np.linalg.norm(F[0])
+        assert dev <= 1.5 * 42 / (6 * PI * d)
+        if dev_prev is not None:
+            assert dev <= dev_prev * 0.02   # ~1/d decay (100x in d)
+        dev_prev = dev
+        assert np.abs(W).max() <= 1e-9 * np.abs(U).max()
