@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--precond", default="wall", choices=["wall", "free_shared"],
                    help="block preconditioner of the --workload small / monolayer solves")
     p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve",
-                                          "resistance", "active"],
+                                          "resistance", "active", "eval"],
                    default="matvec",
                    help="matvec: the benchmark line below; monolayer / batch / serve: the "
                         "663,552-blob monolayer solve, 256 batched suspensions, and the "
@@ -597,6 +597,43 @@ def bench_active(args):
     return 0
 
 
+def bench_eval(args):
+    """Flow evaluation away from the blobs: 65,536 tracer points over the
+    65,536-blob matvec cloud (FP32 packed kernel), and the Appendix B
+    rendering of the same points with every blob split into 12."""
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    r_np, f_np, a = I.config_matvec_cloud(1, 65536)
+    x_np, _, _ = I.config_matvec_cloud(2, 65536)
+    r, f, x = (torch.from_numpy(v).cuda() for v in (r_np, f_np, x_np))
+    off = torch.from_numpy(I.shell(12) * a).cuda()
+    out = {}
+    for name, call, pairs in (
+            ("eval", lambda: ctx.mobility_eval(x, r, f, a, 1.0, True, "fp32"), 65536.0 ** 2),
+            ("render_12", lambda: ctx.render_flow(x, r, f, off, 0.25 * a, 1.0, True, "fp32"),
+             65536.0 * 65536.0 * 12)):
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            call()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 5
+        out[name] = {"ms": 1e3 * dt, "pairs_per_s": pairs / dt}
+    print(json.dumps({"metric": "flow evaluation pairs/s", "workload": "65,536 points x 65,536 "
+                      "blobs (C2 cloud), wall, FP32; rendering with 12 sub-blobs per blob",
+                      **out, "n_gpus": 1}), flush=True)
+    ctx.close()
+    return 0
+
+
 def bench_batch(args):
     """256 independent mixed suspensions (42-blob shells and 15-blob
     boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
@@ -791,6 +828,8 @@ def main():
         return bench_resistance(args)
     if args.workload == "active":
         return bench_active(args)
+    if args.workload == "eval":
+        return bench_eval(args)
     if args.workload == "monolayer":
         return bench_monolayer(args)
     if args.workload == "batch":
