@@ -65,7 +65,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df64"],
+                   help="matvec precision (fp32 is the benchmark line; fp64 and df64 for "
+                        "profiling the other kernels)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-solve", action="store_true")
@@ -345,27 +347,39 @@ def run_ours(args):
         cpu = {"value": pps, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nt} random targets x {n} sources ({nt * n:.3g} pairs, {dt:.1f} s)"}
 
+    if args.prec == "fp32":
+        roofline = {
+            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for_kernel(),
+            "kernel": KERNEL_NAMES.get(variant, "pair_f32_kernel<wall>"),
+            "kernel_ms_avg": 1e3 * kernel_avg_s, "flops_per_pair": FLOPS_PER_PAIR,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
+            "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ))
+            if clocks else None}
+    else:
+        # profiling lines of the other precisions: the FP32 peak does not apply
+        roofline = {
+            "bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
+            "traffic": None,
+            "kernel": ("pair_df_kernel<wall> (symmetric double-float on the FP32 pipe)"
+                       if args.prec == "df64" else "pair_f64_kernel<wall> (FP64 pipe)"),
+            "kernel_ms_avg": 1e3 * kernel_avg_s, "flops_per_pair": FLOPS_PER_PAIR,
+            "note": "117 algorithmic flop/pair carried out in the higher precision"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_blobs": n, "precision":
-                       "fp32 pair kernel, hi/lo positions, Kahan-compensated sums, fp64 output"
-                       if args.prec == "fp32" else "fp64 pair kernel",
+            "dtype": {"fp32": "f32", "fp64": "f64", "df64": "df64"}[args.prec], "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("N=65536", f"N={n}"), "n_blobs": n,
+                       "precision":
+                       {"fp32": "fp32 pair kernel, hi/lo positions, Kahan-compensated sums, fp64 "
+                                "output",
+                        "fp64": "fp64 pair kernel",
+                        "df64": "double-float symmetric pair kernel"}[args.prec],
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": traffic_for_kernel(),
-                         "kernel": KERNEL_NAMES.get(variant, "pair_f64_kernel<wall>"),
-                         "kernel_ms_avg": 1e3 * kernel_avg_s,
-                         "flops_per_pair": FLOPS_PER_PAIR,
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
-                         "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"]
-                                                                / SM_MAX_MHZ))
-                         if clocks else None},
+            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 24 * n,
                     "d2h_bytes_per_step": 24 * n},
             "gpu_launches": int(launches1 - launches0),
