@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
         double *ils = L_SMEM ? B + 6 * n : sm;  // 1 / sqrt(d_c)
         double *S = ils + n;
         double *Nm = S + 36;
+        double *col = Nm + 36;  // the scaled column c of the current step
         const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
         __syncthreads();
         if (threadIdx.x == 0) bad = 0;
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             B[e] = v;
         }
         int fail = 0;
+        if constexpr (L_SMEM) {
         for (int c = 0; c < n; ++c) {
             __syncthreads();
             const double d = L[(size_t)c * ld + c];
@@ -431,8 +433,14 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             if (lane == 0) il = 1.0 / sqrt(d);
             il = __shfl_sync(0xffffffffu, il, 0);
             if (threadIdx.x == 0) ils[c] = il;
-            // scale column c (L[c][c] becomes sqrt(d)) and row c of B
-            for (int i = c + threadIdx.x; i < n; i += blockDim.x) L[(size_t)i * ld + c] *= il;
+            // scale column c (L[c][c] becomes sqrt(d)) and row c of B; the
+            // scaled column also goes to the shared buffer `col`, read by
+            // every row of the update (a strided column read otherwise)
+            for (int i = c + threadIdx.x; i < n; i += blockDim.x) {
+                const double v = L[(size_t)i * ld + c] * il;
+                L[(size_t)i * ld + c] = v;
+                col[i] = v;
+            }
             if (threadIdx.x >= 32 && threadIdx.x < 38) B[6 * c + threadIdx.x - 32] *= il;
             __syncthreads();
             // trailing update with the scaled column, one FMA per entry: rows
@@ -440,10 +448,60 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             // the six B columns (no index decoding per entry)
             for (int i = c + 1 + warp; i < n; i += nw) {
                 double *Li = L + (size_t)i * ld;
-                const double lic = Li[c];
-                for (int j = c + 1 + lane; j <= i; j += 32) Li[j] -= lic * L[(size_t)j * ld + c];
+                const double lic = col[i];
+                for (int j = c + 1 + lane; j <= i; j += 32) Li[j] -= lic * col[j];
                 if (lane < 6) B[6 * i + lane] -= lic * B[6 * c + lane];
             }
+        }
+        } else {
+        // Block in global memory: left-looking (Crout) order.  Column j is
+        // L[i][j] = (A[i][j] - L[i][0:j] . L[j][0:j]) / L[j][j], one coalesced
+        // dot product per row with the pivot row L[j][0:j] in shared memory
+        // (`col`); every entry is written once, so the inner loop only loads
+        // and the many independent loads in flight hide the memory latency
+        // that the right-looking update's read-modify-writes exposed.  Row j
+        // of G = L^-1 K follows from the same pivot row.
+        for (int c = 0; c < n; ++c) {
+            __syncthreads();  // step c - 1 finished with col
+            for (int k = threadIdx.x; k < c; k += blockDim.x) col[k] = L[(size_t)c * ld + k];
+            __syncthreads();
+            // pivot d = A[c][c] - |L[c][0:c]|^2, computed by every warp alike
+            double acc = 0.0;
+            for (int k = lane; k < c; k += 32) acc += col[k] * col[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const double d = L[(size_t)c * ld + c] - acc;
+            if (!(d > 0.0)) {  // the same value in every thread
+                fail = 1;
+                break;
+            }
+            double il = 0.0;
+            if (lane == 0) il = 1.0 / sqrt(d);
+            il = __shfl_sync(0xffffffffu, il, 0);
+            if (threadIdx.x == 0) {
+                ils[c] = il;
+                L[(size_t)c * ld + c] = d * il;  // sqrt(d)
+            }
+            for (int i = c + 1 + warp; i < n; i += nw) {
+                const double *Li = L + (size_t)i * ld;
+                double dot = 0.0;
+                for (int k = lane; k < c; k += 32) dot += Li[k] * col[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                if (lane == 0) L[(size_t)i * ld + c] = (Li[c] - dot) * il;
+            }
+            if (warp == nw - 1) {
+                // G[c][b] = (K[c][b] - L[c][0:c] . G[0:c][b]) / L[c][c]
+#pragma unroll
+                for (int b = 0; b < 6; ++b) {
+                    double g = 0.0;
+                    for (int k = lane; k < c; k += 32) g += col[k] * B[6 * k + b];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                    if (lane == 0) B[6 * c + b] = (B[6 * c + b] - g) * il;
+                }
+            }
+        }
         }
         __syncthreads();
         if (fail) {  // uniform: a pivot was not positive
@@ -691,7 +749,7 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
     const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
     const bool lsmem = nmax <= kSmemMaxRows;
     const size_t fsmem =
-        sizeof(double) * ((lsmem ? (size_t)nmax * nmax + 6 * (size_t)nmax : 0) + nmax + 72);
+        sizeof(double) * ((lsmem ? (size_t)nmax * nmax + 6 * (size_t)nmax : 0) + 2 * nmax + 72);
     const int col_groups = (int)ceil_div(nmax, 8);
     const int T = (int)ceil_div(nmax, kTile);
     const int tiles = T * (T + 1) / 2;
