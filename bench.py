@@ -337,9 +337,10 @@ def run_ours(args):
     e2e_value, _ = whole_job_rate(dist, pairs_local, e2e_s, device)
 
     # ---- mobility solves of the small suspension (latency distribution)
-    solve = None
+    solve = solve_fp64 = None
     if not args.no_solve and rank == 0:
         solve = bench_solves(ctx, args.solves)
+        solve_fp64 = bench_solves(ctx, args.solves, "fp64")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -386,6 +387,7 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "solve": solve,
+            "solve_fp64": solve_fp64,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
