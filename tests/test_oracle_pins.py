@@ -437,3 +437,19 @@ def test_permeable_body_darcy_limit():
             assert dev <= dev_prev * 0.02   # ~1/d decay (100x in d)
         dev_prev = dev
         assert np.abs(W).max() <= 1e-9 * np.abs(U).max()
+
+
+def test_residual_rows_vanish_at_the_direct_solution():
+    """The sampled rows of Eq. saddle_M's first block row (evaluated with the
+    pair loop, not the dense matrix) vanish at the dense direct solution and
+    not at a perturbed one."""
+    s = I.config_small_suspension(4)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    U, W, lam = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True)
+    rows = np.arange(0, s.n_blobs, 7)
+    res = O.residual_rows(rows, r, s.q, s.blob_start, lam, U, W, s.a)
+    assert np.abs(res).max() <= 1e-12 * np.abs(lam).max()
+    lam2 = lam.copy()
+    lam2[rows[3]] += 1e-6 * np.abs(lam).max()
+    res2 = O.residual_rows(rows, r, s.q, s.blob_start, lam2, U, W, s.a)
+    assert np.abs(res2).max() > 1e-9 * np.abs(lam).max()
