@@ -198,9 +198,14 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
                     A[a][b] = 0.5 * (S[a * 6 + b] + S[b * 6 + a]);
                     A[a][6 + b] = (a == b) ? 1.0 : 0.0;
                 }
+            double smax = 0.0;
+            for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
             for (int c = 0; c < 6 && !bad; ++c) {
                 const double d = A[c][c];
-                if (!(d > 0.0)) { bad = schur; break; }
+                // a pivot below 1e-12 of the largest diagonal entry: a body
+                // that cannot resist some rigid motion (e.g. blobs on a line
+                // through the tracking point cannot resist spin about it)
+                if (!(d > 1e-12 * smax)) { bad = schur; break; }
                 for (int b = 0; b < 12; ++b) A[c][b] /= d;
                 for (int a = 0; a < 6; ++a)
                     if (a != c) {
@@ -540,9 +545,12 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
                     A[a][bb] = 0.5 * (S[a * 6 + bb] + S[bb * 6 + a]);
                     A[a][6 + bb] = (a == bb) ? 1.0 : 0.0;
                 }
+            double smax = 0.0;
+            for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
             for (int c = 0; c < 6 && !bad; ++c) {
                 const double dd = A[c][c];
-                if (!(dd > 0.0)) { bad = schur; break; }
+                // relative pivot test, as in the one-kernel setup
+                if (!(dd > 1e-12 * smax)) { bad = schur; break; }
                 for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
                 for (int a = 0; a < 6; ++a)
                     if (a != c) {

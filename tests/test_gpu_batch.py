@@ -127,3 +127,20 @@ def test_batch_not_converged(ctx):
     for U, W, lam, info in res:
         assert info["converged"] == 0 and info["iters"] == 2
         assert np.isfinite(host(U)).all()
+
+
+def test_batch_with_a_zero_force_problem(ctx):
+    """A problem with b = 0 finishes at admission with zeros; its companions
+    are unaffected."""
+    s0 = I.config_small_suspension(1)
+    s1 = I.config_small_suspension(2)
+    P0 = _prob(s0)
+    P1 = _prob(s1)
+    P1["F"] = torch.zeros_like(P1["F"])
+    P1["T"] = torch.zeros_like(P1["T"])
+    res = ctx.solve_batch([P0, P1], s0.a, tol=1e-10, prec="mixed")
+    U1, W1, lam1, info1 = res[1]
+    assert info1["converged"] == 1 and info1["iters"] == 0
+    assert torch.count_nonzero(U1) == 0 and torch.count_nonzero(lam1) == 0
+    alone = ctx.solve_batch([P0], s0.a, tol=1e-10, prec="mixed")[0]
+    assert rel_l2(host(res[0][0]), host(alone[0])) <= 1e-9

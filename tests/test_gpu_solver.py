@@ -345,3 +345,50 @@ def test_permeable_bodies_match_oracle(ctx, prec):
                                      shift=dev(np.zeros(s.n_blobs)))
     Ur0, _, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, s.a, 1.0, True)
     assert rel_l2(host(U0), Ur0) <= 1e-8
+
+
+def _shell_and_line():
+    """A 42-blob shell (body 0) and three blobs on a line through the
+    tracking point of body 1, which cannot resist spin about that line."""
+    a = 0.243
+    rho0 = I.shell(42)
+    rho1 = np.array([[-2.2 * a, 0.0, 0.0], [0.0, 0.0, 0.0], [2.2 * a, 0.0, 0.0]])
+    return I.Suspension(q=np.array([[0.0, 0.0, 3.0], [4.0, 0.0, 3.0]]),
+                        theta=np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]]),
+                        blob_start=np.array([0, 42, 45], dtype=np.int64),
+                        rho=np.concatenate([rho0, rho1]), F=np.array([[0.0, 0, -1], [0.1, 0, -1]]),
+                        T=np.zeros((2, 3)), a=a)
+
+
+def test_solve_reports_body_that_cannot_resist_a_rigid_motion(ctx):
+    """K_p^T M_pp^-1 K_p is singular for blobs on a line through the tracking
+    point (Section 2.1.2): the setup reports MB_ESINGULAR naming the body
+    instead of solving with a meaningless inverse."""
+    s = _shell_and_line()
+    d = _dev_susp(s)
+    with pytest.raises(mb.MBError) as ei:
+        ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a,
+                           1.0, True, tol=1e-10, prec="fp64")
+    assert ei.value.name == "MB_ESINGULAR" and "body 1" in str(ei.value)
+    # the resistance problem only needs M_pp^-1, which exists
+    U = dev(np.array([[0.0, 0, 1.0], [0.0, 0, 1.0]]))
+    F, T, lam, info = ctx.solve_resistance(d["q"], d["theta"], d["blob_start"], d["rho"], U,
+                                           dev(np.zeros((2, 3))), s.a, 1.0, True, tol=1e-10)
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    Fr, Tr, _ = O.solve_resistance(r, s.q, s.blob_start, host(U), np.zeros((2, 3)), s.a, 1.0, True)
+    assert rel_l2(host(F), Fr) <= 1e-8
+
+
+def test_zero_right_hand_side(ctx):
+    """b = 0 is solved by x = 0 without iterations (mobility and resistance)."""
+    s = I.config_small_suspension(2)
+    d = _dev_susp(s)
+    z = dev(np.zeros((s.n_bodies, 3)))
+    for prec in ("fp64", "mixed"):
+        U, W, lam, info = ctx.solve_mobility(d["q"], d["theta"], d["blob_start"], d["rho"], z, z,
+                                             s.a, 1.0, True, tol=1e-10, prec=prec)
+        assert info["converged"] == 1 and info["iters"] == 0
+        assert np.all(host(U) == 0) and np.all(host(W) == 0) and np.all(host(lam) == 0)
+        F, T, lam, info = ctx.solve_resistance(d["q"], d["theta"], d["blob_start"], d["rho"], z, z,
+                                               s.a, 1.0, True, tol=1e-10, prec=prec)
+        assert info["converged"] == 1 and np.all(host(F) == 0) and np.all(host(lam) == 0)
