@@ -84,6 +84,12 @@ def parse():
                         "serving stream, each printing its own JSON line")
     p.add_argument("--serve-seconds", type=float, default=30.0)
     p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--rates", default="5,8,11,14",
+                   help="serving: comma-separated offered rates (req/s) of the drained runs "
+                        "(empty: 0.5x and 0.8x of the saturated served rate)")
+    p.add_argument("--tick-pairs", type=float, default=0.0,
+                   help="serving: pair evaluations a request may take per tick in the FP32 "
+                        "Arnoldi matvec (0 = engine default, < 0 = no limit)")
     p.add_argument("--pool", type=int, default=40)
     p.add_argument("--pair-variant", type=int, default=-1,
                    help="FP32 pair-kernel variant (-1 autotune; 0..3 pin one, e.g. for profiling)")
@@ -765,7 +771,8 @@ def bench_serve(args):
 
     def run(rate, seconds, seed, drain):
         srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
-                        max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=512)
+                        max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=512,
+                        tick_pairs=args.tick_pairs)
         rng = np.random.default_rng(seed)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 2) + 16))
         arrivals = arrivals[arrivals < seconds]
@@ -812,8 +819,9 @@ def bench_serve(args):
         check.append((k, Ua))
     sat = run(args.rate, args.serve_seconds, 1, drain=False)
     cap = max(sat["served_per_s"], 1e-3)
-    sub = [run(f * cap, max(10.0, args.serve_seconds * 0.6), 2 + i, drain=True)
-           for i, f in enumerate((0.5, 0.8))]
+    rates = ([float(x) for x in args.rates.split(",")] if args.rates else [0.5 * cap, 0.8 * cap])
+    sub = [run(rate, max(10.0, args.serve_seconds * 0.6), 2 + i, drain=True)
+           for i, rate in enumerate(rates)]
     # mix check: serve the three small requests together with a large one
     srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
                     max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=64)
@@ -826,7 +834,8 @@ def bench_serve(args):
     line = {"metric": "mobility solves/s and p99 latency", "workload": "serving: Poisson "
             f"{args.rate:g} req/s, blobs log-uniform 100..2e5 (mixed shells/boomerangs), "
             f"pool of {len(pool)} seeded requests", "value": sat["served_per_s"], "unit": "solves/s",
-            "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)", "saturated": sat,
+            "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)", "tick_pairs": args.tick_pairs,
+            "saturated": sat,
             "sub_saturation": sub, "same_alone_and_in_mix_max_rel_diff_U": mix_diff,
             "pool_generation_s": gen_s, "n_gpus": 1}
     print(json.dumps(line), flush=True)

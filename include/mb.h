@@ -452,6 +452,11 @@ mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *prob
  * while others are in flight join at the next tick.  A request's result does
  * not depend on which others share its ticks (up to the solver tolerance).
  *
+ * A request whose FP32 Arnoldi matvec exceeds limits->tick_pairs pair
+ * evaluations has it split over consecutive ticks (the symmetric kernel
+ * accumulates the parts); its other steps run once, on the first or the last
+ * of those ticks.  Results do not depend on the split.
+ *
  * mb_server_step synchronises `stream` once per tick and reports how many
  * requests are running and queued.  mb_server_poll gives a request's state
  * (0 queued, 1 running, 2 done, 3 failed), its info (setup_ms = time from
@@ -467,6 +472,13 @@ typedef struct {
     int64_t max_precond_bytes;  /* storage for the bodies' preconditioner
                                    blocks: (3 n_p + 6)^2 doubles per body    */
     int max_requests;           /* requests in flight at once                */
+    double tick_pairs;          /* pair evaluations one request may take per
+                                   tick in the FP32 Arnoldi matvec (symmetric
+                                   tile shape): larger requests spread each
+                                   matvec over several ticks, so that small
+                                   requests sharing the ticks are not held up
+                                   by them; 0 = 1e9 (about 2 ms of the FP32
+                                   kernel), < 0 = no limit */
 } mb_server_limits;
 
 mb_status mb_server_create(mb_context *ctx, const mb_params *params,

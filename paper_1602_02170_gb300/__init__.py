@@ -132,6 +132,7 @@ class ServerLimits(ctypes.Structure):
         ("max_bodies", ctypes.c_int64),
         ("max_precond_bytes", ctypes.c_int64),
         ("max_requests", ctypes.c_int),
+        ("tick_pairs", ctypes.c_double),
     ]
 
 
@@ -567,20 +568,22 @@ class Server:
     Context.solve_batch) and returns a ticket; step() runs one scheduling
     tick; poll() reports (state, info, status) with state 0 queued,
     1 running, 2 done, 3 failed.  Results land in the tensors returned by
-    submit(); keep the inputs alive until the ticket is done."""
+    submit(); keep the inputs alive until the ticket is done.  tick_pairs
+    caps the pair evaluations one request's FP32 Arnoldi matvec takes per
+    tick (0: 1e9, < 0: no cap); larger matvecs are spread over ticks."""
 
     QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
 
     def __init__(self, ctx, a, eta=1.0, wall=True, tol=1e-10, maxit=200, restart=60,
                  prec="mixed", max_blobs=1 << 20, max_bodies=1 << 16,
-                 max_precond_bytes=4 << 30, max_requests=256):
+                 max_precond_bytes=4 << 30, max_requests=256, tick_pairs=0.0):
         self.ctx = ctx
         self.L = ctx.L
         self._torch = ctx._torch
         p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
                    _prec(prec))
         lim = ServerLimits(int(max_blobs), int(max_bodies), int(max_precond_bytes),
-                           int(max_requests))
+                           int(max_requests), float(tick_pairs))
         h = ctypes.c_void_p()
         self._check(self.L.mb_server_create(ctx.handle, ctypes.byref(p), ctypes.byref(lim),
                                             ctypes.byref(h)))

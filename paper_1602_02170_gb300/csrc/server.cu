@@ -60,7 +60,7 @@ struct Work {         // pair-kernel work of one request in one launch
     const double *r, *f;
     double *y, *part;
     int64_t n, chunk, item_off;
-    int n_tblocks, S, slot, pad;
+    int n_tblocks, S, slot, tri_lo;  // tri_lo: first block-pair item (symmetric, split matvecs)
 };
 
 struct RSeg {         // chunk of a work entry's local rows for the partial reduction
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kNT, 2) eng_sym_kernel(
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const Work P = W[find_owner(item_off, nw, item)];
         if (!mask[P.slot]) continue;
-        const int64_t local = item - P.item_off;
+        const int64_t local = item - P.item_off + P.tri_lo;
         const int64_t nb = P.n_tblocks;
         int64_t lo_r = 0, hi_r = nb;
         while (hi_r - lo_r > 1) {
@@ -627,6 +627,14 @@ __global__ void eng_accumulate_kernel(double *__restrict__ t, double *__restrict
     }
 }
 
+// out[s] = a[s] && b[s] for every slot
+__global__ void eng_and_kernel(const int *__restrict__ a, const int *__restrict__ b,
+                               int *__restrict__ out, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        out[s] = a[s] && b[s];
+}
+
 // ------------------------------------------------------------------ per-slot scalar kernels
 __global__ void eng_init_kernel(const int *__restrict__ list, int nlist, double *sm, SL L,
                                 SlotState st)
@@ -799,9 +807,10 @@ struct Engine {
     RangeAlloc blobs, bodies, pcs, starts;
     std::vector<int> free_slots;
     bool mixed = false;
+    double tick_pairs = -1;  // per-request pair budget of one tick's Arnoldi matvec (< 0: none)
     int np_variant = 1;     // FP32 tile shape: 1, 2 = packed with 2 or 4 targets per
                             // thread, 3 = symmetric (autotuned)
-    bool tuned = false;
+    std::map<int, int> tuned_by_class;  // autotuned tile shape per size class of a tick's pairs
 
     struct Req {
         int64_t ticket = 0;
@@ -812,6 +821,7 @@ struct Engine {
         int max_np = 1;  // most blobs on one body
         int phase = 0;  // 0 queued, 1 first cycle, 2 residual, 3 arnoldi, 4 done
         int j = 0;
+        int mv_chunks = 1, mv_next = 0;  // split of the current Arnoldi matvec
         clk::time_point t_submit, t_admit, t_done;
         mb_info info{};
         int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
@@ -834,10 +844,11 @@ struct Engine {
     }
 
     mb_status create(mb_context *c, const mb_params *p, int64_t max_blobs, int64_t max_bodies,
-                     int64_t max_pc_doubles, int max_requests)
+                     int64_t max_pc_doubles, int max_requests, double tick_pair_budget = -1)
     {
         ctx = c;
         prm = *p;
+        tick_pairs = tick_pair_budget;
         m = std::max(1, std::min(p->restart, 500));
         L = SL{m};
         n_cap = max_blobs;
@@ -984,9 +995,14 @@ struct Engine {
 
     // Batched pair matvec over `list` slots: y_s = M f_s, f and y at vector
     // slots (fk, yk) of the arena's vector arrays.
+    // tri (symmetric FP32 only): per list entry, the range [lo, hi) of the
+    // request's block-pair items to evaluate (a part of a split matvec);
+    // zero_mask: requests whose output is zeroed first (default: mask).
     mb_status matvec(const std::vector<int> &list, const double *f_base, const std::vector<int64_t> &fk,
                      double *y_base, const std::vector<int64_t> &yk, mb_precision prec,
-                     const int *mask, cudaStream_t s, size_t &toff)
+                     const int *mask, cudaStream_t s, size_t &toff,
+                     const std::vector<std::pair<int64_t, int64_t>> *tri = nullptr,
+                     const int *zero_mask = nullptr)
     {
         if (list.empty()) return MB_OK;
         const double scale = 1.0 / (6.0 * kPi * prm.eta * prm.a);
@@ -1031,7 +1047,13 @@ struct Engine {
                 wk.n_tblocks = (int)nb;
                 wk.S = 1;
                 wk.chunk = wk.n;
-                items += nb * (nb + 1) / 2;
+                wk.tri_lo = 0;
+                int64_t cnt = nb * (nb + 1) / 2;
+                if (tri && x2) {
+                    wk.tri_lo = (int)(*tri)[li].first;
+                    cnt = (*tri)[li].second - (*tri)[li].first;
+                }
+                items += cnt;
                 for (int64_t a = 0; a < 3 * wk.n; a += kSeg)
                     rs.push_back(RSeg{a, std::min<int64_t>(3 * wk.n, a + kSeg), (int)li, 0});
                 W.push_back(wk);
@@ -1064,7 +1086,8 @@ struct Engine {
         const bool wall = prm.wall != 0;
         auto *ev = profile_begin(ctx, s);
         if (sym) {
-            eng_zero_kernel<<<grid_for((int64_t)rs.size(), 1), 256, 0, s>>>(dW, dR, (int)rs.size(), mask);
+            eng_zero_kernel<<<grid_for((int64_t)rs.size(), 1), 256, 0, s>>>(
+                dW, dR, (int)rs.size(), zero_mask ? zero_mask : mask);
             count_launch();
         }
         if (dfs) {
@@ -1271,12 +1294,26 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         return MB_OK;
     }
     // tile shape: the context's pinned pair variant if any (the scalar
-    // variant maps to packed x2), else autotuned on the first inner FP32 matvec
-    if (!tuned && inner == MB_FP32_KAHAN && ctx->pair_variant >= 0) {
-        np_variant = std::min(3, std::max(1, ctx->pair_variant));
-        tuned = true;
+    // variant maps to packed x2), else autotuned once per size class of the
+    // tick's pair work (powers of 4): small ticks favour the packed shapes,
+    // large ones the symmetric shape.  It stays fixed while a split matvec is
+    // in progress, since only the symmetric shape splits.
+    bool mid_split = false, tune = false;
+    double tick_pair_sum = 0;
+    for (int sl : arn) {
+        const Req *rq = running[sl];
+        tick_pair_sum += (double)rq->prob.n_blobs * rq->prob.n_blobs;
+        mid_split = mid_split || (rq->phase == 3 && rq->mv_next > 0);
     }
-    if (!tuned && inner == MB_FP32_KAHAN) {
+    const int size_class = (int)(std::log2(std::max(1.0, tick_pair_sum)) / 2);
+    if (inner == MB_FP32_KAHAN && ctx->pair_variant >= 0) {
+        np_variant = std::min(3, std::max(1, ctx->pair_variant));
+    } else if (inner == MB_FP32_KAHAN && !mid_split) {
+        auto it = tuned_by_class.find(size_class);
+        if (it != tuned_by_class.end()) np_variant = it->second;
+        else tune = true;
+    }
+    if (tune) {
         float best = 1e30f;
         int best_v = 1;
         cudaEvent_t e0, e1;
@@ -1305,7 +1342,7 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         np_variant = best_v;
-        tuned = true;
+        tuned_by_class[size_class] = best_v;
         toff = 0;
     }
 
@@ -1389,9 +1426,45 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
             segs_of(running[sl], segs);
         }
         seg_off.push_back((int)segs.size());
+        // Split matvecs: with the symmetric FP32 tile shape, a request whose
+        // matvec exceeds tick_pairs evaluations does it in parts over
+        // consecutive ticks (the kernel accumulates into its zeroed output).
+        // The preconditioner apply, the zeroing and K / K^T run on the first
+        // part's tick, the orthogonalisation and Givens update on the last's.
+        const bool can_split = tick_pairs > 0 && inner == MB_FP32_KAHAN && np_variant == 3;
+        std::vector<int> first(s_cap, 0), last(s_cap, 0), arn_last;
+        std::vector<std::pair<int64_t, int64_t>> tri;
+        for (int sl : arn) {
+            Req *rq = running[sl];
+            const int64_t nblk = ceil_div(rq->prob.n_blobs, 2 * (int64_t)kNT);
+            const int64_t items = nblk * (nblk + 1) / 2;
+            if (rq->phase != 3 || rq->mv_next == 0) {
+                const double pairs = 0.5 * (double)rq->prob.n_blobs * rq->prob.n_blobs;
+                rq->mv_chunks = can_split
+                                    ? (int)std::min<double>((double)items,
+                                                            std::max(1.0, std::ceil(pairs / tick_pairs)))
+                                    : 1;
+                rq->mv_next = 0;
+            }
+            const int c = rq->mv_next, C = rq->mv_chunks;
+            first[sl] = c == 0;
+            last[sl] = c == C - 1;
+            tri.emplace_back(items * c / C, items * (c + 1) / C);
+            if (last[sl]) arn_last.push_back(sl);
+        }
         Seg *dS = upload(segs, toff, s, &stt);
-        int *dA = upload(arn, toff, s, &stt);
+        int *dA = upload(arn_last, toff, s, &stt);
+        int *dFirst = upload(first, toff, s, &stt);
+        int *dLast = upload(last, toff, s, &stt);
         MB_TRY(stt);
+        // device masks: active and on the first / last part of its matvec
+        int *act_first = (int *)((char *)tick.ptr + ((toff + 255) & ~(size_t)255));
+        toff = ((toff + 255) & ~(size_t)255) + sizeof(int) * s_cap;
+        int *act_last = (int *)((char *)tick.ptr + ((toff + 255) & ~(size_t)255));
+        toff = ((toff + 255) & ~(size_t)255) + sizeof(int) * s_cap;
+        eng_and_kernel<<<grid_for(s_cap, 256), 256, 0, s>>>(st.act, dFirst, act_first, s_cap);
+        eng_and_kernel<<<grid_for(s_cap, 256), 256, 0, s>>>(st.act, dLast, act_last, s_cap);
+        count_launch(2);
         // precond apply for bodies of active slots: Z_j = P^-1 V_j
         int max_np = 1;
         for (int sl : arn) max_np = std::max(max_np, running[sl]->max_np);
@@ -1399,36 +1472,36 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         const int pc_grid = (int)std::min<int64_t>(b_cap, 8 * (int64_t)ctx->sm_count);
         eng_precond_apply_kernel<<<pc_grid, 256, pc_smem, s>>>(body_slot, body_b0, body_b1, poff, 0,
                                                                b_cap, P, V, Z, st.j, ld, n_cap,
-                                                               st.act);
+                                                               act_first);
         count_launch();
-        MB_TRY(matvec(arn, Z, zk, V, vk, inner, st.act, s, toff));
+        MB_TRY(matvec(arn, Z, zk, V, vk, inner, st.act, s, toff, &tri, act_first));
         eng_K_kernel<<<grid_for(n_cap, 256), 256, 0, s>>>(blob_body, blob_slot, 0, n_cap, r, q, Z,
-                                                          st.j, V + ld, st.j, ld, n_cap, st.act,
+                                                          st.j, V + ld, st.j, ld, n_cap, act_first,
                                                           -1.0, 1.0);
         count_launch();
         // K^T writes -K^T z into V_{j+1}: output slot index j+1 via a shifted view
         eng_KT_kernel<<<grid_for(b_cap * 32, 256), 256, 0, s>>>(body_slot, body_b0, body_b1, 0, b_cap,
                                                                 r, q, Z, st.j, V + ld, st.j, ld,
-                                                                n_cap, st.act, -1.0);
+                                                                n_cap, act_first, -1.0);
         count_launch();
         // CGS2: h = V^T w, w -= V h, twice; |w|; normalise (w = V_{j+1})
         const int nk = jmax + 1;
-        MB_TRY(dots(arn, segs, seg_off, V, nullptr, st.j, 1, nk, V + ld, st.j, st.act, L.h(), s,
+        MB_TRY(dots(arn, segs, seg_off, V, nullptr, st.j, 1, nk, V + ld, st.j, act_last, L.h(), s,
                     toff));
         eng_subtract_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(
-            V, ld, st.j, sm, L.total(), L.h(), dS, (int)segs.size(), st.act);
+            V, ld, st.j, sm, L.total(), L.h(), dS, (int)segs.size(), act_last);
         count_launch();
-        MB_TRY(dots(arn, segs, seg_off, V, nullptr, st.j, 1, nk, V + ld, st.j, st.act, L.y(), s,
+        MB_TRY(dots(arn, segs, seg_off, V, nullptr, st.j, 1, nk, V + ld, st.j, act_last, L.y(), s,
                     toff));
         eng_subtract_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(
-            V, ld, st.j, sm, L.total(), L.y(), dS, (int)segs.size(), st.act);
+            V, ld, st.j, sm, L.total(), L.y(), dS, (int)segs.size(), act_last);
         count_launch();
-        MB_TRY(dots(arn, segs, seg_off, V + ld, st.j, nullptr, 0, 1, V + ld, st.j, st.act,
+        MB_TRY(dots(arn, segs, seg_off, V + ld, st.j, nullptr, 0, 1, V + ld, st.j, act_last,
                     L.nrm2(), s, toff));
         eng_normalise_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(
-            V + ld, st.j, V + ld, st.j, ld, sm, L.total(), L.nrm2(), dS, (int)segs.size(), st.act);
+            V + ld, st.j, V + ld, st.j, ld, sm, L.total(), L.nrm2(), dS, (int)segs.size(), act_last);
         count_launch();
-        eng_givens_kernel<<<1, 128, 0, s>>>(dA, (int)arn.size(), sm, L, st, prm.maxit);
+        eng_givens_kernel<<<1, 128, 0, s>>>(dA, (int)arn_last.size(), sm, L, st, prm.maxit);
         count_launch();
         eng_update_kernel<<<grid_for((int64_t)segs.size(), 1), 256, 0, s>>>(
             Z, ld, sm, L.total(), L.y(), st.j, dS, (int)segs.size(), st.park, x, dx);
@@ -1452,9 +1525,12 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
         } else if (h_park[sl]) {
             rq->phase = 2;
             rq->j = 0;
+            rq->mv_next = 0;
         } else if (h_act[sl]) {
             rq->phase = 3;
             rq->j = h_j[sl];
+            // a split matvec continues on the next tick; a finished step starts anew
+            rq->mv_next = rq->mv_next + 1 < rq->mv_chunks ? rq->mv_next + 1 : 0;
         } else {
             rq->phase = 2;  // defensive: restart from the true residual
         }
@@ -1595,8 +1671,9 @@ mb_status mb_server_create(mb_context *ctx, const mb_params *params,
         return set_err(ctx, MB_EINVAL, "bad server limits");
     mb_server *sv = new (std::nothrow) mb_server();
     if (!sv) return MB_ENOMEM;
+    const double budget = limits->tick_pairs == 0.0 ? 1e9 : limits->tick_pairs;
     mb_status st = sv->eng.create(ctx, params, limits->max_blobs, limits->max_bodies,
-                                  limits->max_precond_bytes / 8, limits->max_requests);
+                                  limits->max_precond_bytes / 8, limits->max_requests, budget);
     if (st != MB_OK) {
         delete sv;
         return st;

@@ -114,3 +114,41 @@ def test_server_isolates_a_failing_request(ctx):
         Ur, Wr, _ = O.solve_saddle(rg, g.q, g.blob_start, g.F, g.T, A, 1.0, True)
         assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
     srv.close()
+
+
+def test_server_split_matvec_matches_unsplit(ctx):
+    """A small tick pair budget spreads each large FP32 Arnoldi matvec over
+    several ticks; the solutions match the unsplit engine and the oracle."""
+    sus = [I.mixed_suspension(500, 60), I.mixed_suspension(501, 2)]
+    probs = [_prob(s) for s in sus]
+    ctx.set_pair_variant(3)  # the symmetric tile shape, the one that splits
+    try:
+        res, ticks = {}, {}
+        for budget in (-1.0, 1e5):
+            srv = mb.Server(ctx, A, tol=1e-10, prec="mixed", max_blobs=20000, max_bodies=500,
+                            max_requests=8, tick_pairs=budget)
+            outs = [srv.submit(P) for P in probs]
+            n = 0
+            while True:
+                nr, nq = srv.step()
+                n += 1
+                if nr == 0 and nq == 0:
+                    break
+                assert n < 100000
+            ticks[budget] = n
+            res[budget] = []
+            for t, (U, W, lam) in outs:
+                state, info, status = srv.poll(t)
+                assert state == mb.Server.DONE and status == "MB_OK", (state, status, info)
+                assert info["converged"] == 1 and info["rel_residual"] <= 1e-10
+                res[budget].append((host(U), host(W)))
+            srv.close()
+    finally:
+        ctx.set_pair_variant(-1)
+    # the large request (1,845 blobs) takes 17 ticks per Arnoldi matvec
+    assert ticks[1e5] > 3 * ticks[-1.0], ticks
+    for (Ua, Wa), (Ub, Wb), s in zip(res[-1.0], res[1e5], sus):
+        assert rel_l2(Ub, Ua) <= 1e-8 and rel_l2(Wb, Wa) <= 1e-8
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
+        assert rel_l2(Ub, Ur) <= 1e-6 and rel_l2(Wb, Wr) <= 1e-6
