@@ -341,6 +341,7 @@ constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 constexpr int kF32Variants = 5;
 constexpr int kSmallNT = 32;        // CTA size of the small-problem kernels
 constexpr int64_t kSmallN = 8192;   // below this the FP64 and double-float paths use them
+constexpr int kSmallF64Chunk = 8;   // smallest source chunk of the small FP64 kernel
 
 int f32_targets_per_cta(int v)
 {
@@ -552,7 +553,9 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
     if (small) {
         const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true, kSmallNT>, kSmallNT)
                              : resident_ctas(ctx, pair_f64_kernel<false, kSmallNT>, kSmallNT);
-        p = make_plan(n, kSmallNT, res, 1024, kSmallNT, kSmallNT);
+        // source chunks down to 8 blobs: several one-warp CTAs per SM, since
+        // a single warp leaves the FP64 pipe mostly idle
+        p = make_plan(n, kSmallNT, res, 1024, kSmallF64Chunk, kSmallF64Chunk);
     } else {
         const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true>)
                              : resident_ctas(ctx, pair_f64_kernel<false>);

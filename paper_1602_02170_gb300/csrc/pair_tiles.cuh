@@ -154,8 +154,10 @@ __device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *
             sfz[threadIdx.x] = valid ? f[3 * jc + 2] : 0.0;
         }
         __syncthreads();
+        // the staged sources of this tile (chunks may be shorter than NT)
+        const int cnt = j_end - jt < NT ? (int)(j_end - jt) : NT;
 #pragma unroll 2
-        for (int s = 0; s < NT; ++s)
+        for (int s = 0; s < cnt; ++s)
             pair_accumulate<WALL, double>(xi - sx[s], yi - sy[s], zi - sz[s], zi, sz[s], sfx[s],
                                           sfy[s], sfz[s], k, ux, uy, uz);
     }

@@ -17,6 +17,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "mb_internal.cuh"
 #include "rpy_wall.cuh"
 
@@ -317,6 +319,7 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(
 //    Q (6 nmax) | QN (6 nmax) | dW (nmax) | N (36)].
 constexpr int kSplitMaxRows = 512;
 constexpr int kTile = 32;
+constexpr int kPanel = 8;  // columns per panel of the shared-memory Cholesky
 
 __device__ __forceinline__ int64_t owner_body(const int64_t *__restrict__ start, int64_t nb,
                                               int64_t b)
@@ -375,11 +378,27 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
     }
 }
 
+// Entry (row, col) of K_p (rows 3 i + al of blob i are [I, -[d_i]x],
+// d_i = r_i - q_p); rb points at the body's first blob.
+__device__ __forceinline__ double k_entry(const double *__restrict__ rb, double qx, double qy,
+                                          double qz, int row, int col)
+{
+    const int i = row / 3, al = row % 3;
+    if (col < 3) return al == col ? 1.0 : 0.0;
+    const double dx = rb[3 * i] - qx, dy = rb[3 * i + 1] - qy, dz = rb[3 * i + 2] - qz;
+    // -[d]x = [[0, dz, -dy], [-dz, 0, dx], [dy, -dx, 0]]
+    const int e3 = 3 * al + col - 3;
+    return e3 == 1 ? dz : e3 == 2 ? -dy : e3 == 3 ? -dz : e3 == 5 ? dx
+         : e3 == 6 ? dy : e3 == 7 ? -dx : 0.0;
+}
+
 // S2: one CTA per body.  Right-looking Cholesky on the lower triangle with
 // the six columns B = K_p appended (so that B ends as G = L^-1 K_p): step c
 // scales column c by 1/sqrt(d_c), then subtracts its outer product from the
 // trailing triangle and its multiples of row c from the rows of B below,
-// one FP64 FMA per entry (FP64 issue is the bound on this chip).
+// one FP64 FMA per entry (FP64 issue is the bound on this chip).  Blocks in
+// shared memory take the steps in panels of kPanel columns; blocks in global
+// memory use the left-looking order.
 template <bool L_SMEM>
 __global__ void __launch_bounds__(256) pc_factor_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
     SplitScratch scr, int *__restrict__ flag, int flag_slot, int64_t p_base, int schur)
 {
     extern __shared__ double sm[];
-    __shared__ int bad;
+    __shared__ int bad, pfail;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
         const int64_t b0 = start[p];
@@ -400,7 +419,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
         double *ils = L_SMEM ? B + 6 * n : sm;  // 1 / sqrt(d_c)
         double *S = ils + n;
         double *Nm = S + 36;
-        double *col = Nm + 36;  // the scaled column c of the current step
+        double *col = Nm + 36;  // pivot row (global blocks) / kPanel scaled columns (shared)
         const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
         __syncthreads();
         if (threadIdx.x == 0) bad = 0;
@@ -410,52 +429,80 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
                 if (j <= i) L[e] = Pp[(size_t)i * m + j];
             }
         // B = K_p: rows of blob i are [I, -[d_i]x]
-        for (int e = threadIdx.x; e < 6 * n; e += blockDim.x) {
-            const int row = e / 6, col = e % 6, i = row / 3, al = row % 3;
-            double v;
-            if (col < 3) {
-                v = al == col ? 1.0 : 0.0;
-            } else {
-                const double dx = r[3 * (b0 + i)] - qx, dy = r[3 * (b0 + i) + 1] - qy,
-                             dz = r[3 * (b0 + i) + 2] - qz;
-                // -[d]x = [[0, dz, -dy], [-dz, 0, dx], [dy, -dx, 0]]
-                const int e3 = 3 * al + col - 3;
-                v = e3 == 1 ? dz : e3 == 2 ? -dy : e3 == 3 ? -dz : e3 == 5 ? dx
-                  : e3 == 6 ? dy : e3 == 7 ? -dx : 0.0;
-            }
-            B[e] = v;
-        }
+        for (int e = threadIdx.x; e < 6 * n; e += blockDim.x)
+            B[e] = k_entry(r + 3 * b0, qx, qy, qz, e / 6, e % 6);
         int fail = 0;
         if constexpr (L_SMEM) {
-        for (int c = 0; c < n; ++c) {
+        // Blocked order: warp 0 factors a panel of kPanel columns (rows c0..n-1)
+        // warp-synchronously, keeping the scaled columns transposed in pT
+        // (rows read without bank conflicts); then every warp subtracts the
+        // panel's rank-kPanel product from the trailing triangle and from
+        // the rows of B below the panel.  The same FMAs as column by column,
+        // with two CTA barriers per panel instead of two per column.
+        double *pT = col;
+        for (int c0 = 0; c0 < n; c0 += kPanel) {
+            const int w = n - c0 < kPanel ? n - c0 : kPanel;
+            __syncthreads();  // the previous trailing update is complete
+            if (warp == 0) {
+                int f = 0;
+                for (int c = c0; c < c0 + w; ++c) {
+                    const double d = L[(size_t)c * ld + c];
+                    if (!(d > 0.0)) {  // the same value in every lane
+                        f = 1;
+                        break;
+                    }
+                    double il = 0.0;
+                    if (lane == 0) il = 1.0 / sqrt(d);
+                    il = __shfl_sync(0xffffffffu, il, 0);
+                    if (lane == 0) ils[c] = il;
+                    double *pc = pT + (size_t)(c - c0) * n;
+                    for (int i = c + lane; i < n; i += 32) {
+                        const double v = L[(size_t)i * ld + c] * il;
+                        L[(size_t)i * ld + c] = v;
+                        pc[i] = v;
+                    }
+                    if (lane < 6) B[6 * c + lane] *= il;
+                    __syncwarp();
+                    // the panel's later columns, and the rows of B inside the panel
+                    const int ce = c0 + w - 1;
+                    for (int i = c + 1 + lane; i < n; i += 32) {
+                        const double lic = pc[i];
+                        const int top = i < ce ? i : ce;
+                        for (int cc = c + 1; cc <= top; ++cc) L[(size_t)i * ld + cc] -= lic * pc[cc];
+                    }
+                    for (int e = lane; e < 6 * (ce - c); e += 32) {
+                        const int i = c + 1 + e / 6, b = e % 6;
+                        B[6 * i + b] -= pc[i] * B[6 * c + b];
+                    }
+                    __syncwarp();
+                }
+                if (lane == 0) pfail = f;
+            }
             __syncthreads();
-            const double d = L[(size_t)c * ld + c];
-            if (!(d > 0.0)) {  // every thread reads the same pivot
+            if (pfail) {  // uniform
                 fail = 1;
                 break;
             }
-            double il = 0.0;
-            if (lane == 0) il = 1.0 / sqrt(d);
-            il = __shfl_sync(0xffffffffu, il, 0);
-            if (threadIdx.x == 0) ils[c] = il;
-            // scale column c (L[c][c] becomes sqrt(d)) and row c of B; the
-            // scaled column also goes to the shared buffer `col`, read by
-            // every row of the update (a strided column read otherwise)
-            for (int i = c + threadIdx.x; i < n; i += blockDim.x) {
-                const double v = L[(size_t)i * ld + c] * il;
-                L[(size_t)i * ld + c] = v;
-                col[i] = v;
-            }
-            if (threadIdx.x >= 32 && threadIdx.x < 38) B[6 * c + threadIdx.x - 32] *= il;
-            __syncthreads();
-            // trailing update with the scaled column, one FMA per entry: rows
-            // i > c round-robin over the warps, lanes across j in (c, i] and
-            // the six B columns (no index decoding per entry)
-            for (int i = c + 1 + warp; i < n; i += nw) {
+            const int t0 = c0 + w;
+            for (int i = t0 + warp; i < n; i += nw) {
+                double li[kPanel];
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk) li[kk] = kk < w ? pT[(size_t)kk * n + i] : 0.0;
                 double *Li = L + (size_t)i * ld;
-                const double lic = col[i];
-                for (int j = c + 1 + lane; j <= i; j += 32) Li[j] -= lic * col[j];
-                if (lane < 6) B[6 * i + lane] -= lic * B[6 * c + lane];
+                for (int j = t0 + lane; j <= i; j += 32) {
+                    double acc = Li[j];
+#pragma unroll
+                    for (int kk = 0; kk < kPanel; ++kk)
+                        if (kk < w) acc -= li[kk] * pT[(size_t)kk * n + j];
+                    Li[j] = acc;
+                }
+                if (lane < 6) {
+                    double acc = B[6 * i + lane];
+#pragma unroll
+                    for (int kk = 0; kk < kPanel; ++kk)
+                        if (kk < w) acc -= li[kk] * B[6 * (c0 + kk) + lane];
+                    B[6 * i + lane] = acc;
+                }
             }
         }
         } else {
@@ -574,6 +621,255 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             Ns[threadIdx.x] = Nm[threadIdx.x];
             Pp[(size_t)(n + threadIdx.x / 6) * m + n + threadIdx.x % 6] = -Nm[threadIdx.x];
         }
+    }
+}
+
+// S2 on a cluster of kFacCluster CTAs per body, for problems with fewer
+// bodies than SMs (one SM per body would leave most of the chip idle, and
+// one SM issues about one FP64 FMA per clock).  Rows are dealt cyclically:
+// CTA r holds rows i = r + kFacCluster t of M_p (and of B = K_p) in shared
+// memory.  Per panel of kPanel columns:
+//   (b) every CTA reads the panel's diagonal block and B rows from their
+//       owners and (c) factors them itself: the same data and arithmetic in
+//       every CTA, so the same pivots and the same failure decision;
+//   (d) each CTA solves its own rows below the panel for their panel entries;
+//   (g) after a cluster barrier each CTA gathers the factored panel of all
+//       rows below it and (h) subtracts its rank-kPanel product from its own
+//       rows' trailing entries and B rows.
+// A cluster barrier separates every read of another CTA's shared memory from
+// that CTA's next write of the same entries.  The outputs are those of
+// pc_factor_kernel.
+constexpr int kFacCluster = 8;
+
+size_t factor_cluster_smem(int nmax)
+{
+    const size_t R = (size_t)(nmax + kFacCluster - 1) / kFacCluster;
+    return sizeof(double) * (R * nmax + 6 * R + nmax + kPanel * kPanel + 6 * kPanel +
+                             (size_t)kPanel * nmax + 72);
+}
+
+__global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc_factor_cluster_kernel(
+    int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
+    const int64_t *__restrict__ start, const int64_t *__restrict__ poff, double *__restrict__ P,
+    SplitScratch scr, int *__restrict__ flag, int flag_slot, int64_t p_base, int schur)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int64_t cid = blockIdx.x / kFacCluster, ncl = gridDim.x / kFacCluster;
+    const int nmax = scr.nmax;
+    const int R = (nmax + kFacCluster - 1) / kFacCluster;
+    extern __shared__ double sm[];
+    __shared__ int fail_s, bad;
+    double *Lr = sm;                    // R x nmax: own rows of M_p, becoming L
+    double *Br = Lr + (size_t)R * nmax;  // R x 6: own rows of K_p, becoming G
+    double *ils = Br + 6 * R;           // nmax: 1 / L[c][c] (every CTA keeps all)
+    double *D = ils + nmax;             // kPanel x kPanel: the panel's diagonal block
+    double *Bd = D + kPanel * kPanel;   // kPanel x 6: the panel's rows of B
+    double *Pn = Bd + 6 * kPanel;       // kPanel x nmax: factored panel, transposed
+    double *Sp = Pn + (size_t)kPanel * nmax;  // 36: partial G^T G
+    double *Nm = Sp + 36;               // 36
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t p = cid; p < nb; p += ncl) {
+        const int64_t b0 = start[p];
+        const int np = (int)(start[p + 1] - b0);
+        const int n = 3 * np, m = n + 6;
+        const int nown = n > rank ? (n - 1 - rank) / kFacCluster + 1 : 0;
+        double *Pp = P + poff[p];
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
+            const int li = e / n, j = e % n, i = rank + kFacCluster * li;
+            if (j <= i) Lr[(size_t)li * nmax + j] = Pp[(size_t)i * m + j];
+        }
+        for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x)
+            Br[e] = k_entry(r + 3 * b0, qx, qy, qz, rank + kFacCluster * (e / 6), e % 6);
+        int fail = 0;
+        for (int c0 = 0; c0 < n; c0 += kPanel) {
+            const int w = n - c0 < kPanel ? n - c0 : kPanel, t0 = c0 + w;
+            cluster.sync();  // (a) the previous trailing updates are complete
+            // (b) the diagonal block and its B rows from their owners
+            for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+                const int a = e / w, b = e % w, row = c0 + a;
+                if (b <= a)
+                    D[a * kPanel + b] = cluster.map_shared_rank(Lr, row % kFacCluster)
+                        [(size_t)(row / kFacCluster) * nmax + c0 + b];
+            }
+            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
+                const int row = c0 + e / 6;
+                Bd[e] = cluster.map_shared_rank(Br, row % kFacCluster)[6 * (row / kFacCluster) + e % 6];
+            }
+            __syncthreads();
+            // (c) Cholesky of the block and forward substitution of its B rows (warp 0)
+            if (warp == 0) {
+                int f = 0;
+                for (int c = 0; c < w; ++c) {
+                    const double d = D[c * kPanel + c];
+                    if (!(d > 0.0)) {  // the same value in every lane
+                        f = 1;
+                        break;
+                    }
+                    double il = 0.0;
+                    if (lane == 0) il = 1.0 / sqrt(d);
+                    il = __shfl_sync(0xffffffffu, il, 0);
+                    if (lane == 0) ils[c0 + c] = il;
+                    if (lane >= c && lane < w) D[lane * kPanel + c] *= il;
+                    if (lane < 6) Bd[6 * c + lane] *= il;
+                    __syncwarp();
+                    if (lane > c && lane < w) {
+                        const double lac = D[lane * kPanel + c];
+                        for (int b = c + 1; b <= lane; ++b) D[lane * kPanel + b] -= lac * D[b * kPanel + c];
+                    }
+                    for (int e = lane; e < 6 * (w - 1 - c); e += 32) {
+                        const int a = c + 1 + e / 6, x = e % 6;
+                        Bd[6 * a + x] -= D[a * kPanel + c] * Bd[6 * c + x];
+                    }
+                    __syncwarp();
+                }
+                if (lane == 0) fail_s = f;
+            }
+            __syncthreads();
+            if (fail_s) {  // uniform over the cluster
+                cluster.sync();  // every CTA has finished reading in (b)
+                fail = 1;
+                break;
+            }
+            // (d) own rows below the panel: L[i][c0 + k] by forward substitution
+            for (int li = threadIdx.x; li < nown; li += blockDim.x) {
+                const int i = rank + kFacCluster * li;
+                if (i < t0) continue;
+                double *Li = Lr + (size_t)li * nmax + c0;
+                double x[kPanel];
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) {
+                    if (k < w) {
+                        double a = Li[k];
+#pragma unroll
+                        for (int kk = 0; kk < k; ++kk) a -= x[kk] * D[k * kPanel + kk];
+                        x[k] = a * ils[c0 + k];
+                        Li[k] = x[k];
+                    }
+                }
+            }
+            cluster.sync();  // (f) every CTA's panel entries are final
+            // (g) the factored panel of rows t0..n-1 from their owners; the owners
+            // of the diagonal block's rows store its factored rows and B rows
+            for (int e = threadIdx.x; e < (n - t0) * w; e += blockDim.x) {
+                const int j = t0 + e / w, k = e % w;
+                Pn[(size_t)k * nmax + j] = cluster.map_shared_rank(Lr, j % kFacCluster)
+                    [(size_t)(j / kFacCluster) * nmax + c0 + k];
+            }
+            for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+                const int a = e / w, b = e % w, row = c0 + a;
+                if (row % kFacCluster == rank && b <= a)
+                    Lr[(size_t)(row / kFacCluster) * nmax + c0 + b] = D[a * kPanel + b];
+            }
+            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
+                const int row = c0 + e / 6;
+                if (row % kFacCluster == rank) Br[6 * (row / kFacCluster) + e % 6] = Bd[e];
+            }
+            __syncthreads();
+            // (h) trailing update of own rows i >= t0
+            for (int li = warp; li < nown; li += nw) {
+                const int i = rank + kFacCluster * li;
+                if (i < t0) continue;
+                double *Li = Lr + (size_t)li * nmax;
+                double lk[kPanel];
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) lk[k] = k < w ? Li[c0 + k] : 0.0;
+                for (int j = t0 + lane; j <= i; j += 32) {
+                    double acc = Li[j];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k)
+                        if (k < w) acc -= lk[k] * Pn[(size_t)k * nmax + j];
+                    Li[j] = acc;
+                }
+                if (lane < 6) {
+                    double acc = Br[6 * li + lane];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k)
+                        if (k < w) acc -= lk[k] * Bd[6 * k + lane];
+                    Br[6 * li + lane] = acc;
+                }
+            }
+        }
+        if (fail) {
+            if (rank == 0 && threadIdx.x == 0) {
+                if (flag_slot >= 0) flag[flag_slot] = 2;
+                else atomicMin(flag, (int)(p_base + p));
+            }
+            continue;
+        }
+        __syncthreads();
+        // own rows: L^T into P_p's upper triangle (row k holds column k of L),
+        // 1 / L[i][i] and G to the scratch
+        double *dW = scr.dW(p), *G = scr.G(p);
+        for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
+            const int li = e / n, k = e % n, i = rank + kFacCluster * li;
+            if (k <= i) Pp[(size_t)k * m + i] = Lr[(size_t)li * nmax + k];
+        }
+        for (int li = threadIdx.x; li < nown; li += blockDim.x) {
+            const int i = rank + kFacCluster * li;
+            dW[i] = ils[i];
+        }
+        for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x) {
+            const int li = e / 6, i = rank + kFacCluster * li;
+            G[6 * i + e % 6] = Br[e];
+        }
+        // partial S = G^T G over own rows, one warp per entry
+        for (int ab = warp; ab < 36; ab += nw) {
+            const int a = ab / 6, bb = ab % 6;
+            double acc = 0.0;
+            for (int li = lane; li < nown; li += 32) acc += Br[6 * li + a] * Br[6 * li + bb];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) Sp[ab] = acc;
+        }
+        cluster.sync();  // every CTA's partial S is written
+        if (rank == 0) {
+            // S summed over the cluster in rank order; N = S^-1 by Gauss-Jordan
+            if (threadIdx.x < 36) {
+                double acc = 0.0;
+                for (int rr = 0; rr < kFacCluster; ++rr)
+                    acc += cluster.map_shared_rank(Sp, rr)[threadIdx.x];
+                D[threadIdx.x] = acc;  // the 36 entries of S (the block is free now)
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bad = 0;
+                double A[6][12];
+                for (int a = 0; a < 6; ++a)
+                    for (int bb = 0; bb < 6; ++bb) {
+                        A[a][bb] = 0.5 * (D[a * 6 + bb] + D[bb * 6 + a]);
+                        A[a][6 + bb] = (a == bb) ? 1.0 : 0.0;
+                    }
+                double smax = 0.0;
+                for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
+                for (int c = 0; c < 6 && !bad; ++c) {
+                    const double dd = A[c][c];
+                    // relative pivot test, as in the one-kernel setup
+                    if (!(dd > 1e-12 * smax)) { bad = schur; break; }
+                    for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
+                    for (int a = 0; a < 6; ++a)
+                        if (a != c) {
+                            const double f = A[a][c];
+                            for (int bb = 0; bb < 12; ++bb) A[a][bb] -= f * A[c][bb];
+                        }
+                }
+                for (int a = 0; a < 6; ++a)
+                    for (int bb = 0; bb < 6; ++bb) Nm[a * 6 + bb] = A[a][6 + bb];
+            }
+            __syncthreads();
+            if (bad) {
+                if (threadIdx.x == 0) {
+                    if (flag_slot >= 0) flag[flag_slot] = 2;
+                    else atomicMin(flag, (int)(p_base + p));
+                }
+            } else if (threadIdx.x < 36) {
+                scr.N(p)[threadIdx.x] = Nm[threadIdx.x];
+                Pp[(size_t)(n + threadIdx.x / 6) * m + n + threadIdx.x % 6] = -Nm[threadIdx.x];
+            }
+        }
+        cluster.sync();  // rank 0 has read every partial S
     }
 }
 
@@ -757,7 +1053,8 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
     const double scale = 1.0 / (6.0 * 3.14159265358979323846 * eta * a);
     const bool lsmem = nmax <= kSmemMaxRows;
     const size_t fsmem =
-        sizeof(double) * ((lsmem ? (size_t)nmax * nmax + 6 * (size_t)nmax : 0) + 2 * nmax + 72);
+        sizeof(double) * (lsmem ? (size_t)nmax * nmax + (7 + kPanel) * (size_t)nmax + 72
+                                : 2 * (size_t)nmax + 72);
     const int col_groups = (int)ceil_div(nmax, 8);
     const int T = (int)ceil_div(nmax, kTile);
     const int tiles = T * (T + 1) / 2;
@@ -770,11 +1067,21 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
             pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         else
             pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
-        auto factor = lsmem ? pc_factor_kernel<true> : pc_factor_kernel<false>;
-        MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)fsmem));
-        factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
-            ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
+        if (lsmem && ng < ctx->sm_count) {
+            // fewer bodies than SMs: a cluster of CTAs per body
+            const size_t csm = factor_cluster_smem(nmax);
+            MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_factor_cluster_kernel,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)csm));
+            pc_factor_cluster_kernel<<<(int)ng * kFacCluster, 256, csm, s>>>(
+                ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
+        } else {
+            auto factor = lsmem ? pc_factor_kernel<true> : pc_factor_kernel<false>;
+            MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)fsmem));
+            factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
+                ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
+        }
         const int gt = (int)std::min<int64_t>(ng * col_groups, 16 * (int64_t)ctx->sm_count);
         if (nmax > kSplitMaxRows) {
             const size_t tsm = sizeof(double) * (size_t)nmax * kTrinvSmemWarps;
