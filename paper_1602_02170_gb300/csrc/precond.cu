@@ -28,6 +28,42 @@ namespace {
 constexpr int kSetupThreads = 256;
 constexpr int kSmemMaxRows = 160;   // n = 3 n_p rows held in shared memory up to this
 
+// N = S^-1 for the symmetrised 6 x 6 S by Gauss-Jordan without pivoting, run
+// by one whole warp: lane b < 12 holds column b of [S | I] in registers (one
+// division per pivot, the eliminations as shuffles and FMAs).  Returns 1 in
+// every lane when a pivot falls below 1e-12 of the largest diagonal entry: a
+// body that cannot resist some rigid motion (e.g. blobs on a line through
+// the tracking point cannot resist spin about it).  Writes Nm (row-major)
+// otherwise.
+__device__ int inverse6_warp(const double *__restrict__ S, double *__restrict__ Nm, int lane)
+{
+    double col[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+        col[a] = lane < 6 ? 0.5 * (S[a * 6 + lane] + S[lane * 6 + a]) : (lane - 6 == a ? 1.0 : 0.0);
+    double smax = 0.0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(__shfl_sync(0xffffffffu, col[a], a)));
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double d = __shfl_sync(0xffffffffu, col[c], c);
+        if (!(d > 1e-12 * smax)) return 1;  // the same value in every lane
+        const double rc = col[c] * (1.0 / d);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            if (a == c) continue;
+            const double f = __shfl_sync(0xffffffffu, col[a], c);  // A[a][c]
+            col[a] -= f * rc;
+        }
+        col[c] = rc;
+    }
+    if (lane >= 6 && lane < 12)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) Nm[a * 6 + lane - 6] = col[a];
+    return 0;
+}
+
+
 // Row and column of entry e of a lower triangle enumerated row by row
 // (e = i (i + 1) / 2 + j, j <= i).
 __device__ __forceinline__ void tri_index(int e, int &i, int &j)
@@ -192,31 +228,10 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
         }
         __syncthreads();
 
-        // 6. N = S^-1 by Gauss-Jordan on the symmetrised S (one thread)
-        if (threadIdx.x == 0) {
-            double A[6][12];
-            for (int a = 0; a < 6; ++a)
-                for (int b = 0; b < 6; ++b) {
-                    A[a][b] = 0.5 * (S[a * 6 + b] + S[b * 6 + a]);
-                    A[a][6 + b] = (a == b) ? 1.0 : 0.0;
-                }
-            double smax = 0.0;
-            for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
-            for (int c = 0; c < 6 && !bad; ++c) {
-                const double d = A[c][c];
-                // a pivot below 1e-12 of the largest diagonal entry: a body
-                // that cannot resist some rigid motion (e.g. blobs on a line
-                // through the tracking point cannot resist spin about it)
-                if (!(d > 1e-12 * smax)) { bad = schur; break; }
-                for (int b = 0; b < 12; ++b) A[c][b] /= d;
-                for (int a = 0; a < 6; ++a)
-                    if (a != c) {
-                        const double f = A[a][c];
-                        for (int b = 0; b < 12; ++b) A[a][b] -= f * A[c][b];
-                    }
-            }
-            for (int a = 0; a < 6; ++a)
-                for (int b = 0; b < 6; ++b) Nm[a * 6 + b] = A[a][6 + b];
+        // 6. N = S^-1 on the symmetrised S (warp 0)
+        if (threadIdx.x < 32) {
+            const int f = inverse6_warp(S, Nm, threadIdx.x);
+            if (threadIdx.x == 0 && f) bad = schur;
         }
         __syncthreads();
         if (bad) {
@@ -376,6 +391,23 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
                         scale * blk[3 * al + be] + (shift && bi == bj && al == be ? shift[b] : 0.0);
         }
     }
+}
+
+// 1 / sqrt(d) for the pivots of the cluster factorisation by Newton-Raphson,
+// y <- y (3 - d y^2) / 2: the FP32 hardware reciprocal square root refined by
+// one step in FP32, then one step in FP64 (quadratic convergence: from FP32
+// accuracy to ~1e-14 relative).  Each dependent FP64 operation costs about
+// 64 cycles on this chip, so the short chain matters: the division of 1 by an
+// FP64 square root is about three times longer.  Pivots outside the FP32
+// range take that path.
+__device__ __forceinline__ double rsqrt_newton(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    const float df = (float)d;
+    float yf = rsqrtf(df);
+    yf = yf * (1.5f - 0.5f * df * yf * yf);
+    const double y = (double)yf;
+    return y * (1.5 - 0.5 * d * y * y);
 }
 
 // Entry (row, col) of K_p (rows 3 i + al of blob i are [I, -[d_i]x],
@@ -584,29 +616,10 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
             if (lane == 0) S[ab] = acc;
         }
         __syncthreads();
-        // N = S^-1 by Gauss-Jordan (one thread)
-        if (threadIdx.x == 0) {
-            double A[6][12];
-            for (int a = 0; a < 6; ++a)
-                for (int bb = 0; bb < 6; ++bb) {
-                    A[a][bb] = 0.5 * (S[a * 6 + bb] + S[bb * 6 + a]);
-                    A[a][6 + bb] = (a == bb) ? 1.0 : 0.0;
-                }
-            double smax = 0.0;
-            for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
-            for (int c = 0; c < 6 && !bad; ++c) {
-                const double dd = A[c][c];
-                // relative pivot test, as in the one-kernel setup
-                if (!(dd > 1e-12 * smax)) { bad = schur; break; }
-                for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
-                for (int a = 0; a < 6; ++a)
-                    if (a != c) {
-                        const double f = A[a][c];
-                        for (int bb = 0; bb < 12; ++bb) A[a][bb] -= f * A[c][bb];
-                    }
-            }
-            for (int a = 0; a < 6; ++a)
-                for (int bb = 0; bb < 6; ++bb) Nm[a * 6 + bb] = A[a][6 + bb];
+        // N = S^-1 (warp 0)
+        if (warp == 0) {
+            const int f = inverse6_warp(S, Nm, lane);
+            if (lane == 0 && f) bad = schur;
         }
         __syncthreads();
         if (bad) {
@@ -687,43 +700,56 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         for (int c0 = 0; c0 < n; c0 += kPanel) {
             const int w = n - c0 < kPanel ? n - c0 : kPanel, t0 = c0 + w;
             cluster.sync();  // (a) the previous trailing updates are complete
-            // (b) the diagonal block and its B rows from their owners
-            for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-                const int a = e / w, b = e % w, row = c0 + a;
-                if (b <= a)
-                    D[a * kPanel + b] = cluster.map_shared_rank(Lr, row % kFacCluster)
-                        [(size_t)(row / kFacCluster) * nmax + c0 + b];
-            }
-            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
-                const int row = c0 + e / 6;
-                Bd[e] = cluster.map_shared_rank(Br, row % kFacCluster)[6 * (row / kFacCluster) + e % 6];
-            }
-            __syncthreads();
-            // (c) Cholesky of the block and forward substitution of its B rows (warp 0)
+            // (b) + (c) warp 0: lane a < w reads row a of the diagonal block and
+            // of B from its owner into registers, then the block's Cholesky and
+            // the forward substitution of its B rows run on registers (the
+            // column loop unrolled, the other rows' entries by shuffles); the
+            // factored rows go to D and Bd for the other warps
             if (warp == 0) {
+                double drow[kPanel], brow[6];
+                const int row = c0 + lane;
+                const double *src = lane < w ? cluster.map_shared_rank(Lr, row % kFacCluster) +
+                                                   (size_t)(row / kFacCluster) * nmax + c0
+                                             : nullptr;
+                const double *bsrc =
+                    lane < w ? cluster.map_shared_rank(Br, row % kFacCluster) + 6 * (row / kFacCluster)
+                             : nullptr;
+#pragma unroll
+                for (int b = 0; b < kPanel; ++b) drow[b] = lane < w && b <= lane ? src[b] : 0.0;
+#pragma unroll
+                for (int x = 0; x < 6; ++x) brow[x] = lane < w ? bsrc[x] : 0.0;
                 int f = 0;
-                for (int c = 0; c < w; ++c) {
-                    const double d = D[c * kPanel + c];
-                    if (!(d > 0.0)) {  // the same value in every lane
-                        f = 1;
-                        break;
+#pragma unroll
+                for (int c = 0; c < kPanel; ++c) {
+                    if (c < w && !f) {
+                        const double d = __shfl_sync(0xffffffffu, drow[c], c);
+                        if (!(d > 0.0)) {
+                            f = 1;  // the same value in every lane
+                        } else {
+                            // selects instead of branches; entries above a
+                            // lane's diagonal may take junk and are never read
+                            const double il = rsqrt_newton(d);
+                            if (lane == 0) ils[c0 + c] = il;
+                            drow[c] *= lane >= c ? il : 1.0;  // lane c: sqrt(d)
+                            const double sc = lane == c ? il : 1.0;
+#pragma unroll
+                            for (int x = 0; x < 6; ++x) brow[x] *= sc;
+                            const double lac = lane > c && lane < w ? drow[c] : 0.0;
+#pragma unroll
+                            for (int b = c + 1; b < kPanel; ++b)
+                                drow[b] -= lac * __shfl_sync(0xffffffffu, drow[c], b);
+#pragma unroll
+                            for (int x = 0; x < 6; ++x)
+                                brow[x] -= lac * __shfl_sync(0xffffffffu, brow[x], c);
+                        }
                     }
-                    double il = 0.0;
-                    if (lane == 0) il = 1.0 / sqrt(d);
-                    il = __shfl_sync(0xffffffffu, il, 0);
-                    if (lane == 0) ils[c0 + c] = il;
-                    if (lane >= c && lane < w) D[lane * kPanel + c] *= il;
-                    if (lane < 6) Bd[6 * c + lane] *= il;
-                    __syncwarp();
-                    if (lane > c && lane < w) {
-                        const double lac = D[lane * kPanel + c];
-                        for (int b = c + 1; b <= lane; ++b) D[lane * kPanel + b] -= lac * D[b * kPanel + c];
-                    }
-                    for (int e = lane; e < 6 * (w - 1 - c); e += 32) {
-                        const int a = c + 1 + e / 6, x = e % 6;
-                        Bd[6 * a + x] -= D[a * kPanel + c] * Bd[6 * c + x];
-                    }
-                    __syncwarp();
+                }
+                if (lane < w) {
+#pragma unroll
+                    for (int b = 0; b < kPanel; ++b)
+                        if (b <= lane) D[lane * kPanel + b] = drow[b];
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) Bd[6 * lane + x] = brow[x];
                 }
                 if (lane == 0) fail_s = f;
             }
@@ -733,30 +759,53 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 fail = 1;
                 break;
             }
-            // (d) own rows below the panel: L[i][c0 + k] by forward substitution
+            // (d) own rows below the panel: L[i][c0 + k] by forward substitution,
+            // column-oriented (each x[k], once known, is subtracted from all
+            // later entries at once: a dependent chain of 2 w operations)
             for (int li = threadIdx.x; li < nown; li += blockDim.x) {
                 const int i = rank + kFacCluster * li;
                 if (i < t0) continue;
                 double *Li = Lr + (size_t)li * nmax + c0;
                 double x[kPanel];
 #pragma unroll
+                for (int k = 0; k < kPanel; ++k) x[k] = k < w ? Li[k] : 0.0;
+#pragma unroll
                 for (int k = 0; k < kPanel; ++k) {
                     if (k < w) {
-                        double a = Li[k];
+                        x[k] *= ils[c0 + k];
 #pragma unroll
-                        for (int kk = 0; kk < k; ++kk) a -= x[kk] * D[k * kPanel + kk];
-                        x[k] = a * ils[c0 + k];
-                        Li[k] = x[k];
+                        for (int kk = k + 1; kk < kPanel; ++kk)
+                            if (kk < w) x[kk] -= x[k] * D[kk * kPanel + k];
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k)
+                    if (k < w) Li[k] = x[k];
             }
             cluster.sync();  // (f) every CTA's panel entries are final
             // (g) the factored panel of rows t0..n-1 from their owners; the owners
             // of the diagonal block's rows store its factored rows and B rows
-            for (int e = threadIdx.x; e < (n - t0) * w; e += blockDim.x) {
-                const int j = t0 + e / w, k = e % w;
-                Pn[(size_t)k * nmax + j] = cluster.map_shared_rank(Lr, j % kFacCluster)
-                    [(size_t)(j / kFacCluster) * nmax + c0 + k];
+            // (remote loads issued in batches of kGather per thread before any
+            // store, so that their latencies overlap)
+            constexpr int kGather = 5;
+            const int total = (n - t0) * w;
+            for (int base = 0; base < total; base += kGather * (int)blockDim.x) {
+                double v[kGather];
+                int dst[kGather];
+#pragma unroll
+                for (int u = 0; u < kGather; ++u) {
+                    const int e = base + threadIdx.x + u * (int)blockDim.x;
+                    dst[u] = -1;
+                    if (e < total) {
+                        const int j = t0 + e / w, k = e % w;
+                        v[u] = cluster.map_shared_rank(Lr, j % kFacCluster)
+                            [(size_t)(j / kFacCluster) * nmax + c0 + k];
+                        dst[u] = k * nmax + j;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kGather; ++u)
+                    if (dst[u] >= 0) Pn[dst[u]] = v[u];
             }
             for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
                 const int a = e / w, b = e % w, row = c0 + a;
@@ -776,19 +825,34 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 double lk[kPanel];
 #pragma unroll
                 for (int k = 0; k < kPanel; ++k) lk[k] = k < w ? Li[c0 + k] : 0.0;
-                for (int j = t0 + lane; j <= i; j += 32) {
-                    double acc = Li[j];
+                // two entries per step and two partial sums per entry: four
+                // independent FP64 chains instead of one
+                for (int j = t0 + lane; j <= i; j += 64) {
+                    const int j2 = j + 32;
+                    const bool two = j2 <= i;
+                    double a0 = Li[j], a1 = 0.0, b0 = two ? Li[j2] : 0.0, b1 = 0.0;
 #pragma unroll
-                    for (int k = 0; k < kPanel; ++k)
-                        if (k < w) acc -= lk[k] * Pn[(size_t)k * nmax + j];
-                    Li[j] = acc;
+                    for (int k = 0; k < kPanel; k += 2) {
+                        if (k < w) {
+                            a0 -= lk[k] * Pn[(size_t)k * nmax + j];
+                            if (two) b0 -= lk[k] * Pn[(size_t)k * nmax + j2];
+                        }
+                        if (k + 1 < w) {
+                            a1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j];
+                            if (two) b1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j2];
+                        }
+                    }
+                    Li[j] = a0 + a1;
+                    if (two) Li[j2] = b0 + b1;
                 }
                 if (lane < 6) {
-                    double acc = Br[6 * li + lane];
+                    double a0 = Br[6 * li + lane], a1 = 0.0;
 #pragma unroll
-                    for (int k = 0; k < kPanel; ++k)
-                        if (k < w) acc -= lk[k] * Bd[6 * k + lane];
-                    Br[6 * li + lane] = acc;
+                    for (int k = 0; k < kPanel; k += 2) {
+                        if (k < w) a0 -= lk[k] * Bd[6 * k + lane];
+                        if (k + 1 < w) a1 -= lk[k + 1] * Bd[6 * (k + 1) + lane];
+                    }
+                    Br[6 * li + lane] = a0 + a1;
                 }
             }
         }
@@ -826,7 +890,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         }
         cluster.sync();  // every CTA's partial S is written
         if (rank == 0) {
-            // S summed over the cluster in rank order; N = S^-1 by Gauss-Jordan
+            // S summed over the cluster in rank order; N = S^-1
             if (threadIdx.x < 36) {
                 double acc = 0.0;
                 for (int rr = 0; rr < kFacCluster; ++rr)
@@ -834,29 +898,9 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 D[threadIdx.x] = acc;  // the 36 entries of S (the block is free now)
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                bad = 0;
-                double A[6][12];
-                for (int a = 0; a < 6; ++a)
-                    for (int bb = 0; bb < 6; ++bb) {
-                        A[a][bb] = 0.5 * (D[a * 6 + bb] + D[bb * 6 + a]);
-                        A[a][6 + bb] = (a == bb) ? 1.0 : 0.0;
-                    }
-                double smax = 0.0;
-                for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(A[a][a]));
-                for (int c = 0; c < 6 && !bad; ++c) {
-                    const double dd = A[c][c];
-                    // relative pivot test, as in the one-kernel setup
-                    if (!(dd > 1e-12 * smax)) { bad = schur; break; }
-                    for (int bb = 0; bb < 12; ++bb) A[c][bb] /= dd;
-                    for (int a = 0; a < 6; ++a)
-                        if (a != c) {
-                            const double f = A[a][c];
-                            for (int bb = 0; bb < 12; ++bb) A[a][bb] -= f * A[c][bb];
-                        }
-                }
-                for (int a = 0; a < 6; ++a)
-                    for (int bb = 0; bb < 6; ++bb) Nm[a * 6 + bb] = A[a][6 + bb];
+            if (warp == 0) {
+                const int f = inverse6_warp(D, Nm, lane);
+                if (lane == 0) bad = f ? schur : 0;
             }
             __syncthreads();
             if (bad) {
