@@ -204,103 +204,23 @@ __device__ void givens_column(double *__restrict__ sm, Small L, int j)
 
 __global__ void givens_kernel(double *__restrict__ sm, Small L, int j) { givens_column(sm, L, j); }
 
-// One CTA does the whole orthogonalisation of w = V_{j+1} for small systems:
+// Small systems: one launch does the whole orthogonalisation of w = V_{j+1}:
 // both classical Gram-Schmidt passes (h = V^T w, w -= V h), their merged
 // coefficients as column j of H, |w|, the Givens update and w /= |w|.  The
 // same steps as the multi-kernel sequence, without its 9 launches.  T is the
 // arithmetic of the passes: double, or float for the FP32 inner iterations
 // of mixed precision, whose basis only needs FP32 orthogonality (the FP32
 // matvec already limits the Arnoldi relation to that level, and the outer
-// refinement restores FP64 accuracy); GB300's FP64 rate on one SM made the
-// double passes the largest cost of a small solve.
-constexpr int kOrthThreads = 1024;
-constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one CTA
+// refinement restores FP64 accuracy).
+constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one launch
 
-template <typename T>
-__global__ void __launch_bounds__(kOrthThreads) orth_small_kernel(double *__restrict__ V,
-                                                                  int64_t L, int j,
-                                                                  double *__restrict__ sm,
-                                                                  Small S)
-{
-    // shared: hs[m + 1] pass coefficients, hc[m + 2] merged column j of H,
-    // cs[m], sn[m] previous rotations, red[32] partial sums
-    extern __shared__ double hs[];
-    double *hc = hs + S.m + 1;
-    double *cs = hc + S.m + 2;
-    double *sn = cs + S.m;
-    double *red = sn + S.m;
-    double *w = V + (int64_t)(j + 1) * L;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        cs[i] = sm[S.cs() + i];
-        sn[i] = sm[S.sn() + i];
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int i = warp; i <= j; i += nw) {
-            const double *v = V + (int64_t)i * L;
-            T acc = T(0);
-            for (int64_t e = lane; e < L; e += 32) acc += T(v[e]) * T(w[e]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) hs[i] = double(acc);
-        }
-        __syncthreads();
-        for (int64_t e = threadIdx.x; e < L; e += blockDim.x) {
-            T acc = T(w[e]);
-            for (int i = 0; i <= j; ++i) acc -= T(V[(int64_t)i * L + e]) * T(hs[i]);
-            w[e] = double(acc);
-        }
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = pass == 0 ? hs[i] : hc[i] + hs[i];
-        __syncthreads();
-    }
-    double acc = 0.0;
-    for (int64_t e = threadIdx.x; e < L; e += blockDim.x) acc += w[e] * w[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        acc = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) {
-            // Givens update of column j on the shared copy (as givens_column)
-            hc[j + 1] = sqrt(acc);
-            for (int i = 0; i < j; ++i) {
-                const double a = hc[i], b = hc[i + 1];
-                hc[i] = cs[i] * a + sn[i] * b;
-                hc[i + 1] = -sn[i] * a + cs[i] * b;
-            }
-            const double a = hc[j], b = hc[j + 1];
-            const double rr = hypot(a, b);
-            const double c = rr > 0.0 ? a / rr : 1.0;
-            const double sg = rr > 0.0 ? b / rr : 0.0;
-            hc[j] = rr;
-            hc[j + 1] = 0.0;
-            const double gj = sm[S.g() + j];
-            sm[S.cs() + j] = c;
-            sm[S.sn() + j] = sg;
-            sm[S.g() + j] = c * gj;
-            sm[S.g() + j + 1] = -sg * gj;
-            sm[S.est()] = fabs(-sg * gj);
-            sm[S.nrm2()] = acc;
-            red[0] = acc;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
-    const double d = sqrt(red[0]);
-    const double inv = d > 0.0 ? 1.0 / d : 0.0;
-    for (int64_t e = threadIdx.x; e < L; e += blockDim.x) w[e] *= inv;
-}
-
-// The same orthogonalisation on a cluster of kOrthCluster CTAs: CTA r owns
-// the slice [r per, (r + 1) per) of every vector.  Each pass forms partial
+// The launch is a cluster of kOrthCluster CTAs: CTA r owns the slice
+// [r per, (r + 1) per) of every vector.  Each pass forms partial
 // dot products over the slice, sums the kOrthCluster partials read from the
 // other CTAs' shared memory (the same order in every CTA, so all hold the
 // same coefficients) and updates its own slice.  Rank 0 does the Givens
-// update.  On GB300 one SM issues about one FP64 FMA per clock, so eight SMs
-// shorten the FP64 passes about eightfold; the cluster barriers cost far less.
+// update.  On GB300 one SM sustains about 1.7 FP64 FMA per clock, so eight
+// SMs shorten the FP64 passes; a cluster barrier costs a few hundred cycles.
 constexpr int kOrthCluster = 8;
 constexpr int kOrthClusterThreads = 256;
 

@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
 
 // S2 on a cluster of kFacCluster CTAs per body, for problems with fewer
 // bodies than SMs (one SM per body would leave most of the chip idle, and
-// one SM issues about one FP64 FMA per clock).  Rows are dealt cyclically:
+// one SM sustains only about 1.7 FP64 FMA per clock).  Rows are dealt cyclically:
 // CTA r holds rows i = r + kFacCluster t of M_p (and of B = K_p) in shared
 // memory.  Per panel of kPanel columns:
 //   (b) every CTA reads the panel's diagonal block and B rows from their

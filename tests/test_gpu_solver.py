@@ -104,6 +104,46 @@ def test_preconditioner_large_bodies_global_path(ctx):
     assert rel_l2(host(UO), UO_ref) <= 1e-8
 
 
+def _many_shells(seed=8, nbod=160):
+    # at least as many bodies as the GPU has SMs: one CTA per body (panels of
+    # 8 columns in shared memory) instead of a cluster per body; 36 rows per
+    # body, so the last panel is ragged
+    return I.sphere_suspension(seed, nbod, 12, 0.3, 48.0, 1.5, 4.0)
+
+
+def test_preconditioner_many_bodies_one_cta_path(ctx):
+    """160 12-blob shells: the preconditioner from the one-CTA-per-body
+    factorisation equals the oracle's per-body direct solve."""
+    s = _many_shells()
+    r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((s.n_blobs, 3))
+    g = rng.standard_normal((s.n_bodies, 6))
+    d = _dev_susp(s)
+    ctx.precond_setup(dev(r), d["q"], d["blob_start"], s.a, 1.0, True)
+    lam, UO = ctx.precond_apply(dev(w), dev(g))
+    lam_ref, UO_ref = O.precond_apply(r, s.q, s.blob_start, s.a, 1.0, True, w, g)
+    assert rel_l2(host(lam), lam_ref) <= 1e-9
+    assert rel_l2(host(UO), UO_ref) <= 1e-9
+
+
+def test_preconditioner_many_bodies_singular_block_reported(ctx):
+    """The one-CTA path reports an indefinite block (a blob at z = a/2) as
+    MB_ESINGULAR naming the body, as the cluster path does."""
+    s = _many_shells()
+    q = s.q.copy()
+    k = 97
+    r = O.blob_positions(q, s.theta, s.blob_start, s.rho)
+    low = np.argmin(r[s.blob_start[k]:s.blob_start[k + 1], 2]) + s.blob_start[k]
+    q[k, 2] -= r[low, 2] - 0.5 * s.a
+    r = O.blob_positions(q, s.theta, s.blob_start, s.rho)
+    d = _dev_susp(s)
+    with pytest.raises(mb.MBError) as ei:
+        ctx.precond_setup(dev(r), dev(q), d["blob_start"], s.a, 1.0, True)
+    assert ei.value.name == "MB_ESINGULAR"
+    assert f"body {k}" in str(ei.value)
+
+
 def _lattice_bodies(shape, nbod, seed):
     """nbod jittered cubic-lattice bodies of prod(shape) blobs (spacing 2.2 a)."""
     g = np.stack(np.meshgrid(*[np.arange(k) for k in shape], indexing="ij"), -1)
