@@ -654,13 +654,19 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
 // pc_factor_kernel.
 constexpr int kFacCluster = 8;
 
-size_t factor_cluster_smem(int nmax)
+size_t factor_cluster_smem(int nmax, bool srows)
 {
     const size_t R = (size_t)(nmax + kFacCluster - 1) / kFacCluster;
-    return sizeof(double) * (R * nmax + 6 * R + nmax + kPanel * kPanel + 6 * kPanel +
-                             (size_t)kPanel * nmax + 72);
+    return sizeof(double) * ((srows ? R * nmax : 0) + 6 * R + nmax + kPanel * kPanel +
+                             6 * kPanel + (size_t)kPanel * nmax + 72);
 }
 
+// SROWS: the rows of M_p sit in the CTAs' shared memory (3 n_p <= 160);
+// otherwise they are factored in place in P_p's lower triangle in global
+// memory, each CTA updating its own rows and reading the others' rows
+// through L2 (ld.global.cg) after the cluster barriers, which order global
+// memory at cluster scope as well.
+template <bool SROWS>
 __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc_factor_cluster_kernel(
     int64_t nb, const double *__restrict__ r, const double *__restrict__ q,
     const int64_t *__restrict__ start, const int64_t *__restrict__ poff, double *__restrict__ P,
@@ -674,8 +680,8 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
     const int R = (nmax + kFacCluster - 1) / kFacCluster;
     extern __shared__ double sm[];
     __shared__ int fail_s, bad;
-    double *Lr = sm;                    // R x nmax: own rows of M_p, becoming L
-    double *Br = Lr + (size_t)R * nmax;  // R x 6: own rows of K_p, becoming G
+    double *Lr = sm;                    // R x nmax: own rows of M_p, becoming L (SROWS)
+    double *Br = SROWS ? Lr + (size_t)R * nmax : sm;  // R x 6: own rows of K_p, becoming G
     double *ils = Br + 6 * R;           // nmax: 1 / L[c][c] (every CTA keeps all)
     double *D = ils + nmax;             // kPanel x kPanel: the panel's diagonal block
     double *Bd = D + kPanel * kPanel;   // kPanel x 6: the panel's rows of B
@@ -690,10 +696,21 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         const int nown = n > rank ? (n - 1 - rank) / kFacCluster + 1 : 0;
         double *Pp = P + poff[p];
         const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
-        for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
-            const int li = e / n, j = e % n, i = rank + kFacCluster * li;
-            if (j <= i) Lr[(size_t)li * nmax + j] = Pp[(size_t)i * m + j];
-        }
+        // own row li (row rank + kFacCluster li), any row for reading, and the read
+        auto own = [&](int li) -> double * {
+            return SROWS ? Lr + (size_t)li * nmax : Pp + (size_t)(rank + kFacCluster * li) * m;
+        };
+        auto row_of = [&](int row) -> const double * {
+            return SROWS ? cluster.map_shared_rank(Lr, row % kFacCluster) +
+                               (size_t)(row / kFacCluster) * nmax
+                         : Pp + (size_t)row * m;
+        };
+        auto rd = [](const double *a) -> double { return SROWS ? *a : __ldcg(a); };
+        if (SROWS)
+            for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
+                const int li = e / n, j = e % n, i = rank + kFacCluster * li;
+                if (j <= i) Lr[(size_t)li * nmax + j] = Pp[(size_t)i * m + j];
+            }
         for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x)
             Br[e] = k_entry(r + 3 * b0, qx, qy, qz, rank + kFacCluster * (e / 6), e % 6);
         int fail = 0;
@@ -708,14 +725,12 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
             if (warp == 0) {
                 double drow[kPanel], brow[6];
                 const int row = c0 + lane;
-                const double *src = lane < w ? cluster.map_shared_rank(Lr, row % kFacCluster) +
-                                                   (size_t)(row / kFacCluster) * nmax + c0
-                                             : nullptr;
+                const double *src = lane < w ? row_of(row) + c0 : nullptr;
                 const double *bsrc =
                     lane < w ? cluster.map_shared_rank(Br, row % kFacCluster) + 6 * (row / kFacCluster)
                              : nullptr;
 #pragma unroll
-                for (int b = 0; b < kPanel; ++b) drow[b] = lane < w && b <= lane ? src[b] : 0.0;
+                for (int b = 0; b < kPanel; ++b) drow[b] = lane < w && b <= lane ? rd(src + b) : 0.0;
 #pragma unroll
                 for (int x = 0; x < 6; ++x) brow[x] = lane < w ? bsrc[x] : 0.0;
                 int f = 0;
@@ -765,7 +780,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
             for (int li = threadIdx.x; li < nown; li += blockDim.x) {
                 const int i = rank + kFacCluster * li;
                 if (i < t0) continue;
-                double *Li = Lr + (size_t)li * nmax + c0;
+                double *Li = own(li) + c0;
                 double x[kPanel];
 #pragma unroll
                 for (int k = 0; k < kPanel; ++k) x[k] = k < w ? Li[k] : 0.0;
@@ -798,8 +813,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                     dst[u] = -1;
                     if (e < total) {
                         const int j = t0 + e / w, k = e % w;
-                        v[u] = cluster.map_shared_rank(Lr, j % kFacCluster)
-                            [(size_t)(j / kFacCluster) * nmax + c0 + k];
+                        v[u] = rd(row_of(j) + c0 + k);
                         dst[u] = k * nmax + j;
                     }
                 }
@@ -809,8 +823,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
             }
             for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
                 const int a = e / w, b = e % w, row = c0 + a;
-                if (row % kFacCluster == rank && b <= a)
-                    Lr[(size_t)(row / kFacCluster) * nmax + c0 + b] = D[a * kPanel + b];
+                if (row % kFacCluster == rank && b <= a) own(row / kFacCluster)[c0 + b] = D[a * kPanel + b];
             }
             for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
                 const int row = c0 + e / 6;
@@ -821,7 +834,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
             for (int li = warp; li < nown; li += nw) {
                 const int i = rank + kFacCluster * li;
                 if (i < t0) continue;
-                double *Li = Lr + (size_t)li * nmax;
+                double *Li = own(li);
                 double lk[kPanel];
 #pragma unroll
                 for (int k = 0; k < kPanel; ++k) lk[k] = k < w ? Li[c0 + k] : 0.0;
@@ -869,7 +882,7 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         double *dW = scr.dW(p), *G = scr.G(p);
         for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
             const int li = e / n, k = e % n, i = rank + kFacCluster * li;
-            if (k <= i) Pp[(size_t)k * m + i] = Lr[(size_t)li * nmax + k];
+            if (k <= i) Pp[(size_t)k * m + i] = own(li)[k];
         }
         for (int li = threadIdx.x; li < nown; li += blockDim.x) {
             const int i = rank + kFacCluster * li;
@@ -1111,14 +1124,15 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
             pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         else
             pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
-        if (lsmem && ng < ctx->sm_count) {
-            // fewer bodies than SMs: a cluster of CTAs per body
-            const size_t csm = factor_cluster_smem(nmax);
-            MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_factor_cluster_kernel,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (ng < ctx->sm_count) {
+            // fewer bodies than SMs: a cluster of CTAs per body, the rows in
+            // shared memory or in place in global memory
+            const size_t csm = factor_cluster_smem(nmax, lsmem);
+            auto fk = lsmem ? pc_factor_cluster_kernel<true> : pc_factor_cluster_kernel<false>;
+            MB_CUDA_TRY(ctx, cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)csm));
-            pc_factor_cluster_kernel<<<(int)ng * kFacCluster, 256, csm, s>>>(
-                ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
+            fk<<<(int)ng * kFacCluster, 256, csm, s>>>(ng, r, q + 3 * g0, st, po, P, scr, flag,
+                                                       flag_slot, g0, schur);
         } else {
             auto factor = lsmem ? pc_factor_kernel<true> : pc_factor_kernel<false>;
             MB_CUDA_TRY(ctx, cudaFuncSetAttribute(factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
