@@ -194,6 +194,8 @@ mb_status mb_context_destroy(mb_context *ctx)
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (DevBuf *b : bufs) release(ctx, *b);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);
+    if (ctx->host_post) cudaFreeHost(ctx->host_post);
+    if (ctx->post_seq_dev) cudaFree(ctx->post_seq_dev);
     for (auto &e : ctx->ev_used) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto &e : ctx->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     delete ctx;

@@ -23,7 +23,9 @@
 // increment runs in FP32; larger corrections (always the first one, which is
 // the whole solution) run in double-float.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -224,9 +226,14 @@ constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one launch
 constexpr int kOrthCluster = 8;
 constexpr int kOrthClusterThreads = 256;
 
+// post (optional): mapped host memory [est, step count]; rank 0 writes the
+// residual estimate, then (after a system-scope fence) the incremented count
+// kept at *seq, so that the host can read the estimate without a stream
+// synchronisation.
 template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
-    orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S)
+    orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
+                        double *__restrict__ post, unsigned long long *__restrict__ seq)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -318,6 +325,13 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             sm[S.g() + j + 1] = -sg * gj;
             sm[S.est()] = fabs(-sg * gj);
             sm[S.nrm2()] = nrm2;
+            if (post) {
+                const unsigned long long q = *seq + 1;
+                *seq = q;
+                post[0] = fabs(-sg * gj);
+                __threadfence_system();
+                *(volatile unsigned long long *)(post + 1) = q;
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
@@ -494,6 +508,30 @@ struct Solver {
         count_launch();
     }
 
+    // The estimate posted by the step just launched: poll the mapped count for
+    // up to 2 ms, then fall back to a stream synchronisation (long steps, or
+    // no mapped memory), which also resynchronises the count.
+    mb_status read_posted_est(double *est)
+    {
+        if (!ctx->host_post) return read_est(est);
+        const unsigned long long want = ++ctx->post_seq;
+        volatile unsigned long long *cnt = (volatile unsigned long long *)(ctx->host_post + 1);
+        const auto t0 = std::chrono::steady_clock::now();
+        for (long it = 0;; ++it) {
+            if (*cnt >= want) {
+                std::atomic_thread_fence(std::memory_order_acquire);
+                *est = *(volatile double *)ctx->host_post;
+                return MB_OK;
+            }
+            if ((it & 255) == 255 &&
+                std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000))
+                break;
+        }
+        MB_TRY(read_est(est));
+        ctx->post_seq = *cnt;
+        return MB_OK;
+    }
+
     mb_status read_est(double *est)
     {
         MB_CUDA_TRY(ctx, cudaMemcpyAsync(hsm, sm + sl.est(), sizeof(double),
@@ -621,6 +659,26 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     MB_TRY(ensure(ctx, ctx->sol_small, sizeof(double) * (sl.total() + (m + 1) * kRedBlocks),
                   "Krylov scalars"));
     if (!ctx->host_small) MB_CUDA_TRY(ctx, cudaMallocHost(&ctx->host_small, 64));
+    if (!ctx->host_post) {
+        // mapped memory for posted estimates; without it the estimates are
+        // read after a stream synchronisation
+        void *hp = nullptr, *dp = nullptr;
+        unsigned long long *sq = nullptr;
+        if (cudaHostAlloc(&hp, 64, cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer(&dp, hp, 0) == cudaSuccess &&
+            cudaMalloc(&sq, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMemset(sq, 0, sizeof(unsigned long long)) == cudaSuccess) {
+            std::memset(hp, 0, 64);
+            ctx->host_post = (double *)hp;
+            ctx->host_post_dev = (double *)dp;
+            ctx->post_seq_dev = sq;
+            ctx->post_seq = 0;
+        } else {
+            if (hp) cudaFreeHost(hp);
+            if (sq) cudaFree(sq);
+            cudaGetLastError();
+        }
+    }
 
     double *r = (double *)ctx->sol_r.ptr;
     MB_TRY(blob_positions(ctx, nb, n, q, theta, blob_start, rho, r, s));
@@ -726,10 +784,10 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         const size_t osm = orth_cluster_smem(m);
                         if (inner == MB_FP32_KAHAN)
                             orth_cluster_kernel<float><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev);
                         else
                             orth_cluster_kernel<double><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev);
                         count_launch();
                         MB_CUDA_TRY(ctx, cudaGetLastError());
                         return MB_OK;
@@ -749,7 +807,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                     }
                     if (!ran) MB_TRY(step(s));
                     double est = 0.0;
-                    MB_TRY(S.read_est(&est));
+                    MB_TRY(S.read_posted_est(&est));
                     if (!(est > inner_abs)) break;
                     continue;
                 }

@@ -97,6 +97,12 @@ struct mb_context {
     mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
     mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)
     void *host_small = nullptr;  // pinned host mirror of small scalars
+    // Arnoldi-step estimates posted by the small-system orthogonalisation:
+    // mapped pinned host memory [est, step count] with its device alias, the
+    // step count kept on the device, and the count the host last asked for
+    double *host_post = nullptr, *host_post_dev = nullptr;
+    unsigned long long *post_seq_dev = nullptr;
+    unsigned long long post_seq = 0;
 
     uint64_t alloc_gen = 0;             // bumped by every workspace (re)allocation
     std::vector<mb::IterGraph> iter_graphs;  // captured Arnoldi steps (any problem, any step)
