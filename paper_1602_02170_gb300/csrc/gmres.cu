@@ -166,13 +166,22 @@ struct Small {
     __host__ __device__ int64_t total() const { return est() + 1; }
 };
 
-// Start a cycle: g = [beta, 0, ...], beta = sqrt(nrm2)
-__global__ void cycle_start_kernel(double *__restrict__ sm, Small L)
+// Start a cycle: g = [beta, 0, ...], beta = sqrt(nrm2); beta is posted like
+// the Arnoldi steps' estimates (post: mapped host memory [value, count])
+__global__ void cycle_start_kernel(double *__restrict__ sm, Small L, double *__restrict__ post,
+                                   unsigned long long *__restrict__ seq)
 {
     const double beta = sqrt(sm[L.nrm2()]);
     for (int i = 0; i <= L.m; ++i) sm[L.g() + i] = 0.0;
     sm[L.g()] = beta;
     sm[L.est()] = beta;
+    if (post) {
+        const unsigned long long q = *seq + 1;
+        *seq = q;
+        post[0] = beta;
+        __threadfence_system();
+        *(volatile unsigned long long *)(post + 1) = q;
+    }
 }
 
 // Column j of H is h[0..j] with H[j+1, j] = sqrt(nrm2); apply the previous
@@ -748,10 +757,10 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                 count_launch();
             }
             S.dots(S.w, 1, S.w, S.sm + sl.nrm2(), 0);
-            cycle_start_kernel<<<1, 1, 0, s>>>(S.sm, sl);
+            cycle_start_kernel<<<1, 1, 0, s>>>(S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev);
             count_launch();
             double beta = 0.0;
-            MB_TRY(S.read_est(&beta));
+            MB_TRY(S.read_posted_est(&beta));
             rel = beta / bnorm;
             if (!std::isfinite(rel))
                 return set_err(ctx, MB_ESINGULAR, "non-finite residual (check blob heights)");
