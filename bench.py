@@ -529,7 +529,7 @@ def bench_resistance(args):
     """Iterations and time of the resistance problem (Eq. resistance_problem)
     beside the mobility problem, for growing suspensions of 42-blob shells in
     an unbounded domain at volume fraction 0.1 (mixed precision, tol 1e-8).
-    Section 4.3 reports resistance iterations growing like N^(1/3) while the
+    Section 4.4 reports resistance iterations growing like N^(1/3) while the
     mobility problem's stay flat; the fitted exponent is printed."""
     import numpy as np
     import torch
@@ -582,7 +582,7 @@ def bench_resistance(args):
 
 def bench_active(args):
     """Active slip on single shells in an unbounded domain: the squirmer's
-    speed against (2/3) B1 (Section 4.2) and the stresslet radius R_s under
+    speed against (2/3) B1 (Section 4.3) and the stresslet radius R_s under
     the strain slip (Section 4.1), with solve times (FP64, tol 1e-10)."""
     import numpy as np
     import torch

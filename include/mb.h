@@ -375,7 +375,7 @@ mb_status mb_solve_mobility_permeable(mb_context *ctx, int64_t n_bodies, int64_t
  * with the wall, or shared per shape without it: params->precond); mixed
  * precision refines like mb_solve_mobility.  The iteration count grows with
  * the linear size of the suspension, unlike the mobility problem's
- * (Section 4.3).
+ * (Section 4.4).
  *
  *   q, theta, blob_start, rho : bodies (device; see mb_blob_positions)
  *   U, Omega : n_b x 3 prescribed velocities (device)

@@ -11,7 +11,7 @@
 // the Arnoldi matvecs use the FP32 pair kernel and the restart residual a
 // higher-precision one, which turns restarts into iterative refinement (the
 // inexact-Krylov remark of Section 2.2.1).  Termination is on the true
-// residual, as right preconditioning allows (Section 3, preconditioner
+// residual, as right preconditioning allows (Section 3.3.3, preconditioner
 // discussion).
 //
 // Mixed precision keeps M lambda as an FP64 running sum y_M: each cycle's

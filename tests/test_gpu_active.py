@@ -1,5 +1,5 @@
 """Active slip on the GPU (the slip right-hand side of Eq. saddle_M): a
-squirmer's swimming speed (Section 4.2) and the stresslet radius under an
+squirmer's swimming speed (Section 4.3) and the stresslet radius under an
 applied strain slip (Section 4.1, Table Stresslets_3D), against the oracle
 and the paper's table."""
 import json

@@ -352,7 +352,7 @@ def test_stresslet_radii_table():
 
 
 def squirmer_slip(rho, B1=1.0):
-    """Tangential slip B1 sin(theta) e_theta of a squirmer (Section 4.2)."""
+    """Tangential slip B1 sin(theta) e_theta of a squirmer (Section 4.3)."""
     th = np.arccos(np.clip(rho[:, 2] / np.linalg.norm(rho, axis=1), -1.0, 1.0))
     ph = np.arctan2(rho[:, 1], rho[:, 0])
     e_th = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], axis=1)
@@ -360,7 +360,7 @@ def squirmer_slip(rho, B1=1.0):
 
 
 def test_squirmer_speed_converges_linearly_in_blob_radius():
-    """Section 4.2: a force- and torque-free squirmer swims along z, and the
+    """Section 4.3: a force- and torque-free squirmer swims along z, and the
     relative error of its speed against (2/3) B1 is linear in a/R_g: halving
     a (162 -> 642 blobs at fixed a/s) halves it, and it vanishes with a."""
     eps = []
