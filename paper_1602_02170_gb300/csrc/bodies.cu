@@ -149,6 +149,84 @@ __global__ void __launch_bounds__(256) KT_apply_block_kernel(
     }
 }
 
+static_assert(kSaddleRowsMaxBodies == kKTBlockBodies,
+              "saddle_rows_kernel reduces K^T lambda with one CTA per body");
+
+// The saddle operator's rows around M lambda in one launch (Eq. saddle_M),
+// from the pair kernel's chunk partials; x = [lambda; U].  Blocks below
+// blob_blocks take blobs, one thread per blob:
+//   y_i = scale * sum_s partial[s][i] - (K U)_i
+// (the sums of reduce_partials_kernel, then K_apply_kernel with alpha = -1,
+// beta = 1); the other blocks take bodies, one CTA per body:
+//   y_(3N + 6p + c) = -(K^T lambda)_p,c
+// (the reduction of KT_apply_block_kernel).  All threads of a block take the
+// same branch, so the barriers of the body branch are uniform.
+__global__ void __launch_bounds__(256) saddle_rows_kernel(
+    const double *__restrict__ partial, int S, double scale, int64_t n, int64_t nb,
+    const double *__restrict__ r, const double *__restrict__ q, const int64_t *__restrict__ start,
+    const double *__restrict__ x, double *__restrict__ y, int blob_blocks)
+{
+    const int64_t m = 3 * n;
+    if ((int)blockIdx.x < blob_blocks) {
+        const double *UO = x + m;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)blob_blocks * blockDim.x) {
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int sc = 0; sc < S; ++sc) {
+                const double *ps = partial + sc * m + 3 * i;
+                acc[0] += ps[0];
+                acc[1] += ps[1];
+                acc[2] += ps[2];
+            }
+            const int64_t p = body_of(start, nb, i);
+            const double dx = r[3 * i] - q[3 * p], dy = r[3 * i + 1] - q[3 * p + 1],
+                         dz = r[3 * i + 2] - q[3 * p + 2];
+            const double *u = UO + 6 * p;
+            const double vx = u[0] + (u[4] * dz - u[5] * dy);
+            const double vy = u[1] + (u[5] * dx - u[3] * dz);
+            const double vz = u[2] + (u[3] * dy - u[4] * dx);
+            // rounded as the two-kernel sequence: u = scale * acc, then u - v
+            y[3 * i] = __dsub_rn(__dmul_rn(scale, acc[0]), vx);
+            y[3 * i + 1] = __dsub_rn(__dmul_rn(scale, acc[1]), vy);
+            y[3 * i + 2] = __dsub_rn(__dmul_rn(scale, acc[2]), vz);
+        }
+        return;
+    }
+    __shared__ double red[8][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int body_blocks = (int)gridDim.x - blob_blocks;
+    for (int64_t p = (int)blockIdx.x - blob_blocks; p < nb; p += body_blocks) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+        for (int64_t i = start[p] + threadIdx.x; i < start[p + 1]; i += blockDim.x) {
+            const double lx = x[3 * i], ly = x[3 * i + 1], lz = x[3 * i + 2];
+            const double dx = r[3 * i] - qx, dy = r[3 * i + 1] - qy, dz = r[3 * i + 2] - qz;
+            acc[0] += lx;
+            acc[1] += ly;
+            acc[2] += lz;
+            acc[3] += dy * lz - dz * ly;
+            acc[4] += dz * lx - dx * lz;
+            acc[5] += dx * ly - dy * lx;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) red[warp][c] = acc[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double v = 0.0;
+            for (int w8 = 0; w8 < 8; ++w8) v += red[w8][threadIdx.x];
+            y[m + 6 * p + threadIdx.x] = -v;
+        }
+    }
+}
+
 int grid_for(int64_t work, int threads)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, threads), 4096));
@@ -173,6 +251,16 @@ void launch_K_apply(int64_t nb, int64_t n, const double *r, const double *q,
 {
     if (n == 0) return;
     K_apply_kernel<<<grid_for(n, 256), 256, 0, s>>>(nb, n, r, q, blob_start, UO, v, alpha, beta);
+    count_launch();
+}
+
+void launch_saddle_rows(const MatvecPartials &mp, int64_t n, int64_t nb, const double *r,
+                        const double *q, const int64_t *blob_start, const double *x, double *y,
+                        cudaStream_t s)
+{
+    const int blob_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024));
+    saddle_rows_kernel<<<blob_blocks + (int)nb, 256, 0, s>>>(mp.partial, mp.S, mp.scale, n, nb, r,
+                                                             q, blob_start, x, y, blob_blocks);
     count_launch();
 }
 

@@ -467,10 +467,19 @@ struct Solver {
     double *V, *Z, *b, *x, *w, *t, *sm, *partial;
     double *hsm;  // pinned host mirror (2 doubles)
 
-    // y = A x with the pair kernel in precision `prec`
+    // y = A x with the pair kernel in precision `prec`.  When the pair
+    // kernel leaves chunk partials, their reduction and both kinematic rows
+    // run as one launch (saddle_rows_kernel) instead of three.
     mb_status apply_A(const double *xin, double *y, mb_precision prec)
     {
-        MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s));
+        MatvecPartials mp;
+        const bool fuse = !shift && !resist && nb >= 1 && nb <= kSaddleRowsMaxBodies;
+        MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s, fuse ? &mp : nullptr));
+        if (mp.S > 0) {
+            launch_saddle_rows(mp, n, nb, r, q, start, xin, y, s);
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+            return MB_OK;
+        }
         if (shift) {
             add_shift_kernel<<<vec_grid(3 * n), 256, 0, s>>>(y, xin, shift, n);
             count_launch();

@@ -145,8 +145,19 @@ mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double
 mb_status render_flow(mb_context *ctx, const double *x, int64_t nt, const double *r,
                       const double *lam, int64_t n, const double *off, int n_sub, double a_sub,
                       double eta, int wall, mb_precision prec, double *v, cudaStream_t s);
+// Chunk partial sums of a matvec whose final reduction the caller takes
+// over: u = scale * sum_{s < S} partial[s * 3N + e].  S = 0 means that the
+// matvec wrote u itself (one chunk, or a kernel without chunks).
+struct MatvecPartials {
+    const double *partial = nullptr;
+    int S = 0;
+    double scale = 0.0;
+};
+// defer (optional): when the chosen kernel writes chunk partials, leave u
+// unwritten and describe the partials there instead of reducing them.
 mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
-                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s,
+                        MatvecPartials *defer = nullptr);
 
 // Bodies (bodies.cu)
 mb_status blob_positions(mb_context *ctx, int64_t nb, int64_t n, const double *q,
@@ -162,6 +173,16 @@ void launch_moments(int64_t nb, const double *r, const double *q, const int64_t 
 // FT = alpha * K^T lambda      (FT: n_b x 6)
 void launch_KT_apply(int64_t nb, const double *r, const double *q, const int64_t *blob_start,
                      const double *lambda, double *FT, double alpha, cudaStream_t s);
+// The rows of the saddle operator of Eq. saddle_M in one launch, from the
+// deferred chunk sums of M lambda: with x = [lambda; U],
+//   y[0, 3N)          = scale * sum_s partial[s] - K U
+//   y[3N, 3N + 6 n_b) = -K^T lambda
+// the arithmetic of reduce_partials_kernel followed by K_apply and the
+// one-CTA-per-body K^T.  For 1 <= nb <= kSaddleRowsMaxBodies.
+constexpr int64_t kSaddleRowsMaxBodies = 256;
+void launch_saddle_rows(const MatvecPartials &mp, int64_t n, int64_t nb, const double *r,
+                        const double *q, const int64_t *blob_start, const double *x, double *y,
+                        cudaStream_t s);
 
 // Preconditioner (precond.cu)
 // schur = 0 keeps only the blob blocks M_pp^-1 (resistance problem).

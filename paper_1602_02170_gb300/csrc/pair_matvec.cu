@@ -380,7 +380,8 @@ void f32_launch(int v, const Plan &p, cudaStream_t s, const float4 *hi, const fl
 
 // One FP32 matvec with variant v (pair kernel + chunk reduction).
 mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, int wall,
-                  double scale, double *u, cudaStream_t s, bool profile)
+                  double scale, double *u, cudaStream_t s, bool profile,
+                  MatvecPartials *defer = nullptr)
 {
     const int res = wall ? f32_resident<true>(ctx, v) : f32_resident<false>(ctx, v);
     if (v == 4) {
@@ -403,6 +404,10 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
         count_launch();
         MB_CUDA_TRY(ctx, cudaGetLastError());
         if (!direct) {
+            if (defer) {
+                *defer = MatvecPartials{out, p.S, scale};
+                return MB_OK;
+            }
             const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
             reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);
             count_launch();
@@ -446,6 +451,10 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
     profile_end(ev, s);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (!direct && defer) {
+        *defer = MatvecPartials{out, p.S, scale};
+        return MB_OK;
+    }
     if (!direct) {
         const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
         reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);
@@ -465,7 +474,7 @@ int tune_key(int64_t n, int wall)
 }
 
 mb_status matvec_f32(mb_context *ctx, const double *f, int64_t n, double a, int wall,
-                     double scale, double *u, cudaStream_t s)
+                     double scale, double *u, cudaStream_t s, MatvecPartials *defer)
 {
     int v = ctx->pair_variant;
     if (v < 0) {
@@ -498,7 +507,7 @@ mb_status matvec_f32(mb_context *ctx, const double *f, int64_t n, double a, int 
             v = best_v;
         }
     }
-    return f32_run(ctx, v, f, n, a, wall, scale, u, s, true);
+    return f32_run(ctx, v, f, n, a, wall, scale, u, s, true, defer);
 }
 
 mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s)
@@ -514,10 +523,12 @@ mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cud
 }
 
 mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64_t n, double a,
-                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s)
+                        double eta, int wall, mb_precision prec, double *u, cudaStream_t s,
+                        MatvecPartials *defer)
 {
     const double scale = 1.0 / (6.0 * kPi * eta * a);
-    if (prec == MB_FP32_KAHAN) return matvec_f32(ctx, f, n, a, wall, scale, u, s);
+    if (defer) *defer = MatvecPartials{};
+    if (prec == MB_FP32_KAHAN) return matvec_f32(ctx, f, n, a, wall, scale, u, s, defer);
     if (prec == MB_DF64) {
         // symmetric double-float kernel: zero u, one launch over the block-pair
         // triangle (32-blob blocks for small problems, so that they spread)
@@ -584,6 +595,10 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
     profile_end(ev, s);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (!direct && defer) {
+        *defer = MatvecPartials{out, p.S, scale};
+        return MB_OK;
+    }
     if (!direct) {
         const int grid = (int)std::min<int64_t>(ceil_div(3 * n, 256), 8 * (int64_t)ctx->sm_count);
         reduce_partials_kernel<<<grid, 256, 0, s>>>(out, n, p.S, scale, u);

@@ -1164,7 +1164,6 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
     MB_TRY(ensure(ctx, tick, (size_t)16 << 20, "server tick buffer"));
     size_t toff = 0;
     mb_status stt = MB_OK;
-    const bool wall = prm.wall != 0;
     const mb_precision inner = inner_precision(prm.prec);
     const mb_precision outer = outer_precision(prm.prec);
 
