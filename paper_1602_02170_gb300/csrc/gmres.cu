@@ -234,6 +234,12 @@ constexpr int64_t kOrthSmallMax = 1 << 18;  // (j + 1) L up to this: one launch
 // SMs shorten the FP64 passes; a cluster barrier costs a few hundred cycles.
 constexpr int kOrthCluster = 8;
 constexpr int kOrthClusterThreads = 256;
+// A CTA's slices of V_0 .. V_{j+1} are staged in its shared memory when they
+// take at most this many doubles (64 KB): all their loads are then in flight
+// at once, and both passes, the norm and the scaling read shared memory
+// instead of walking the slices through L2 one dependent round trip after
+// another.  The arithmetic and its order are the same either way.
+constexpr int64_t kOrthStageDoubles = 8192;
 
 // post (optional): mapped host memory [est, step count]; rank 0 writes the
 // residual estimate, then (after a system-scope fence) the incremented count
@@ -242,14 +248,16 @@ constexpr int kOrthClusterThreads = 256;
 template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
     orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
-                        double *__restrict__ post, unsigned long long *__restrict__ seq)
+                        double *__restrict__ post, unsigned long long *__restrict__ seq,
+                        int stage)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     // shared: part[3][m + 1] partial sums (pass 0, pass 1, |w|^2), hs[m + 1]
     // summed coefficients, hc[m + 2] merged column j of H, cs[m], sn[m]
-    // previous rotations (rank 0), red[32] block partials
+    // previous rotations (rank 0), red[32] block partials, then (stage != 0)
+    // the staged slices sV[(j + 2) x per]
     extern __shared__ double buf[];
     const int m1 = S.m + 1;
     double *part = buf;
@@ -258,21 +266,62 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     double *cs = hc + S.m + 2;
     double *sn = cs + S.m;
     double *red = sn + S.m;
+    double *sV = red + 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t per = (L + kOrthCluster - 1) / kOrthCluster;
     const int64_t e0 = rank * per, e1 = e0 + per < L ? e0 + per : L;
+    const int cnt = e1 > e0 ? (int)(e1 - e0) : 0;  // this CTA's slice length
     double *w = V + (int64_t)(j + 1) * L;
-    if (rank == 0)
+    // the Givens update's inputs from global memory, read up front into
+    // red[16], red[17] (the norm uses red[0, nw))
+    if (rank == 0) {
+        if (threadIdx.x == 0) {
+            const double gj0 = sm[S.g() + j];
+            const unsigned long long q0 = post ? *seq : 0ull;
+            red[16] = gj0;
+            red[17] = __longlong_as_double((long long)q0);
+        }
         for (int i = threadIdx.x; i < j; i += blockDim.x) {
             cs[i] = sm[S.cs() + i];
             sn[i] = sm[S.sn() + i];
         }
+    }
+    if (stage) {
+        // batches of kBatch loads per thread in flight before their stores
+        constexpr int kBatch = 8;
+        const int total = (j + 2) * cnt;
+        for (int x0 = threadIdx.x; x0 < total; x0 += kBatch * (int)blockDim.x) {
+            double v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int x = x0 + u * (int)blockDim.x;
+                if (x < total) {
+                    const int i = x / cnt, k = x - i * cnt;
+                    v[u] = V[(int64_t)i * L + e0 + k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int x = x0 + u * (int)blockDim.x;
+                if (x < total) {
+                    const int i = x / cnt, k = x - i * cnt;
+                    sV[(int64_t)i * per + k] = v[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // element e0 + k of vector i: vs(i)[k], staged or in place
+    auto vs = [&](int i) -> double * {
+        return stage ? sV + (int64_t)i * per : V + (int64_t)i * L + e0;
+    };
+    double *ws = vs(j + 1);
     for (int pass = 0; pass < 2; ++pass) {
         double *pp = part + pass * m1;
         for (int i = warp; i <= j; i += nw) {
-            const double *v = V + (int64_t)i * L;
+            const double *v = vs(i);
             T acc = T(0);
-            for (int64_t e = e0 + lane; e < e1; e += 32) acc += T(v[e]) * T(w[e]);
+            for (int k = lane; k < cnt; k += 32) acc += T(v[k]) * T(ws[k]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) pp[i] = double(acc);
@@ -284,17 +333,17 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             hs[i] = acc;
         }
         __syncthreads();
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            T acc = T(w[e]);
-            for (int i = 0; i <= j; ++i) acc -= T(V[(int64_t)i * L + e]) * T(hs[i]);
-            w[e] = double(acc);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            T acc = T(ws[k]);
+            for (int i = 0; i <= j; ++i) acc -= T(vs(i)[k]) * T(hs[i]);
+            ws[k] = double(acc);
         }
         for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = pass == 0 ? hs[i] : hc[i] + hs[i];
         __syncthreads();  // hs is rewritten by the next pass
     }
     double *pn = part + 2 * m1;
     double acc = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += w[e] * w[e];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) acc += ws[k] * ws[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -321,13 +370,13 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
                 hc[i] = cs[i] * a + sn[i] * b;
                 hc[i + 1] = -sn[i] * a + cs[i] * b;
             }
+            const double gj = red[16];
             const double a = hc[j], b = hc[j + 1];
             const double rr = hypot(a, b);
             const double c = rr > 0.0 ? a / rr : 1.0;
             const double sg = rr > 0.0 ? b / rr : 0.0;
             hc[j] = rr;
             hc[j + 1] = 0.0;
-            const double gj = sm[S.g() + j];
             sm[S.cs() + j] = c;
             sm[S.sn() + j] = sg;
             sm[S.g() + j] = c * gj;
@@ -335,7 +384,7 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             sm[S.est()] = fabs(-sg * gj);
             sm[S.nrm2()] = nrm2;
             if (post) {
-                const unsigned long long q = *seq + 1;
+                const unsigned long long q = (unsigned long long)__double_as_longlong(red[17]) + 1;
                 *seq = q;
                 post[0] = fabs(-sg * gj);
                 __threadfence_system();
@@ -347,11 +396,24 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     }
     const double d = sqrt(nrm2);
     const double inv = d > 0.0 ? 1.0 / d : 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) w[e] *= inv;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = ws[k] * inv;
     cluster.sync();  // no CTA exits while another still reads its partials
 }
 
 size_t orth_cluster_smem(int m) { return sizeof(double) * (7 * (size_t)m + 38); }
+
+// Whether step j stages its slices, and its dynamic shared memory.
+bool orth_cluster_stage(int64_t L, int j)
+{
+    return (int64_t)(j + 2) * ((L + kOrthCluster - 1) / kOrthCluster) <= kOrthStageDoubles;
+}
+size_t orth_cluster_step_smem(int m, int64_t L, int j)
+{
+    return orth_cluster_smem(m) +
+           (orth_cluster_stage(L, j)
+                ? sizeof(double) * (size_t)(j + 2) * (size_t)((L + kOrthCluster - 1) / kOrthCluster)
+                : 0);
+}
 
 // h[i] += y[i] for i <= j: the second CGS pass's coefficients (held in y)
 __global__ void merge_passes_kernel(double *__restrict__ sm, Small L, int j)
@@ -724,6 +786,14 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     const mb_precision inner = inner_precision(p->prec);
     const mb_precision outer = outer_precision(p->prec);
     const int vg = vec_grid(L);
+    if (L <= kOrthSmallMax) {
+        // a step that stages its slices may need more than 48 KB of shared memory
+        const int smax = (int)(orth_cluster_smem(m) + sizeof(double) * kOrthStageDoubles);
+        MB_CUDA_TRY(ctx, cudaFuncSetAttribute(orth_cluster_kernel<float>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+        MB_CUDA_TRY(ctx, cudaFuncSetAttribute(orth_cluster_kernel<double>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    }
 
     if (resist)
         build_rhs_resist_kernel<<<vec_grid(n), 256, 0, s>>>(nb, n, r, q, S.start, in_a, in_b, slip,
@@ -799,13 +869,14 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         const mb_status st = S.apply_A(zj, vn, inner);
                         S.s = s;
                         if (st != MB_OK) return st;
-                        const size_t osm = orth_cluster_smem(m);
+                        const size_t osm = orth_cluster_step_smem(m, L, j);
+                        const int stage = orth_cluster_stage(L, j) ? 1 : 0;
                         if (inner == MB_FP32_KAHAN)
                             orth_cluster_kernel<float><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage);
                         else
                             orth_cluster_kernel<double><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage);
                         count_launch();
                         MB_CUDA_TRY(ctx, cudaGetLastError());
                         return MB_OK;
