@@ -277,17 +277,18 @@ __device__ __forceinline__ void pair_accumulate2(float2 dx, float2 dy, float2 dz
     const float2 p = mul2(hs, ht);
     const float2 T1 = mul2(E, t2);
     const float2 T2 = mul2(E, t4);
+    const float2 hs2 = add2(hs, hs);
     // f1 = -1 - 2p + 2 T1 - 2/3 t2 + 2/3 t4 - 10/3 T2
     const float2 f1 = fma2(k.m10o3, T2, fma2(k.p2o3, t4, fma2(k.m2o3, t2, fma2(k.p2, T1, fma2(k.m2, p, k.m1)))));
     // f2 = -1 + 6p - 10 T1 + 2 t2 + 70/3 T2 - 10/3 t4
     const float2 f2 = fma2(k.m10o3, t4, fma2(k.p70o3, T2, fma2(k.p2, t2, fma2(k.m10, T1, fma2(k.p6, p, k.m1)))));
     // f3 = 2 hs + e3 (20 T1 - 4 t2 + 40/3 t4 - 140/3 T2 - 12 p)
     const float2 in3 = fma2(k.m12, p, fma2(k.m140o3, T2, fma2(k.p40o3, t4, fma2(k.m4, t2, mul2(k.p20, T1)))));
-    const float2 f3 = fma2(k.p2, hs, mul2(e3, in3));
+    const float2 f3 = fma2(e3, in3, hs2);
     // f4 = 2 hs - 20/3 e3 t4
-    const float2 f4 = fma2(k.p2, hs, mul2(k.m20o3, mul2(e3, t4)));
-    // f5 = -4 hs^2 - 4 T1 + 20 T2 - 8/3 t4
-    const float2 f5 = fma2(k.m8o3, t4, fma2(k.p20, T2, fma2(k.m4, T1, mul2(k.m4, mul2(hs, hs)))));
+    const float2 f4 = fma2(k.m20o3, mul2(e3, t4), hs2);
+    // f5 = -4 (hs^2 + T1) + 20 T2 - 8/3 t4
+    const float2 f5 = fma2(k.m4, fma2(hs, hs, T1), fma2(k.p20, T2, mul2(k.m8o3, t4)));
     const float2 eF = mul2(fma2(R3, fz, rf_xy), invR);
     const float2 gw = mul2(fma2(f2, eF, mul2(f3, fz)), invR);
     const float2 kz = fma2(f4, eF, mul2(f5, fz));
@@ -339,31 +340,39 @@ __device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float
     const float2 ht = mul2(zt, invR);
     const float2 e3 = add2(hs, ht);
     const float2 E = mul2(e3, e3);
-    const float2 t2 = mul2(k.a2, mul2(invR, invR));
+    const float2 invR2 = mul2(invR, invR);
+    const float2 t2 = mul2(k.a2, invR2);
     const float2 t4 = mul2(t2, t2);
     const float2 p = mul2(hs, ht);
     const float2 T1 = mul2(E, t2);
     const float2 T2 = mul2(E, t4);
+    const float2 hs2 = add2(hs, hs);
     const float2 f1 = fma2(k.m10o3, T2, fma2(k.p2o3, t4, fma2(k.m2o3, t2, fma2(k.p2, T1, fma2(k.m2, p, k.m1)))));
     const float2 f2 = fma2(k.m10o3, t4, fma2(k.p70o3, T2, fma2(k.p2, t2, fma2(k.m10, T1, fma2(k.p6, p, k.m1)))));
     const float2 in3 = fma2(k.m12, p, fma2(k.m140o3, T2, fma2(k.p40o3, t4, fma2(k.m4, t2, mul2(k.p20, T1)))));
-    const float2 f3 = fma2(k.p2, hs, mul2(e3, in3));
-    const float2 f4 = fma2(k.p2, hs, mul2(k.m20o3, mul2(e3, t4)));
-    const float2 f5 = fma2(k.m8o3, t4, fma2(k.p20, T2, fma2(k.m4, T1, mul2(k.m4, mul2(hs, hs)))));
+    const float2 f3 = fma2(e3, in3, hs2);
+    const float2 f4 = fma2(k.m20o3, mul2(e3, t4), hs2);
+    const float2 f5 = fma2(k.m4, fma2(hs, hs, T1), fma2(k.p20, T2, mul2(k.m8o3, t4)));
     const float2 s = mul2(k.sw, invR);
     const float2 Cx = fma2(s, f1, C);
+    // With R.f = rf_xy + R3 fz (unnormalised), the forms above read
+    // gw = f2 R.f / rho^2 + f3 fz / rho and kz = f4 R.f / rho + f5 fz, so
+    // f2 / rho^2, f3 / rho and f4 / rho serve both directions.
+    const float2 A2 = mul2(f2, invR2);
+    const float2 A3 = mul2(f3, invR);
+    const float2 A4 = mul2(f4, invR);
     // forward: M_ij f_j
-    const float2 eF = mul2(fma2(R3, fz, rf_xy), invR);
-    const float2 gw = mul2(fma2(f2, eF, mul2(f3, fz)), invR);
-    const float2 kz = fma2(f4, eF, mul2(f5, fz));
+    const float2 RF = fma2(R3, fz, rf_xy);
+    const float2 gw = fma2(A2, RF, mul2(A3, fz));
+    const float2 kz = fma2(A4, RF, mul2(f5, fz));
     const float2 Gx = fma2(s, gw, g);
     ux = fma2(Cx, fx, fma2(Gx, dx, ux));
     uy = fma2(Cx, fy, fma2(Gx, dy, uy));
     uz = fma2(Cx, fz, fma2(g, dz, fma2(s, fma2(gw, R3, kz), uz)));
     // reverse: M_ij^T f_i (f3 and f4 exchange roles)
-    const float2 eB = mul2(fma2(R3, fiz, rb_xy), invR);
-    const float2 gwb = mul2(fma2(f2, eB, mul2(f4, fiz)), invR);
-    const float2 kzb = fma2(f3, eB, mul2(f5, fiz));
+    const float2 RB = fma2(R3, fiz, rb_xy);
+    const float2 gwb = fma2(A2, RB, mul2(A4, fiz));
+    const float2 kzb = fma2(A3, RB, mul2(f5, fiz));
     const float2 Gb = fma2(s, gwb, gb);
     rx = fma2(Cx, fix, fma2(Gb, dx, rx));
     ry = fma2(Cx, fiy, fma2(Gb, dy, ry));
