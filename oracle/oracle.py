@@ -69,24 +69,30 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def load(path: str):
+    """ctypes handle of an oracle library built from mb_oracle.c at `path`,
+    with the signatures of its entry points."""
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    L.mbo_rpy_free.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    L.mbo_wall.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    L.mbo_block.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+    L.mbo_src_faxen_fields.argtypes = [dp, dp, ctypes.c_double, dp, dp]
+    L.mbo_matvec.argtypes = [
+        dp, dp, i64, ctypes.POINTER(ctypes.c_int64), i64,
+        ctypes.c_double, ctypes.c_double, ctypes.c_int, dp,
+    ]
+    L.mbo_assemble.argtypes = [dp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+    L.mbo_num_threads.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_SO)
-        dp = ctypes.POINTER(ctypes.c_double)
-        i64 = ctypes.c_int64
-        L.mbo_rpy_free.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
-        L.mbo_wall.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
-        L.mbo_block.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
-        L.mbo_src_faxen_fields.argtypes = [dp, dp, ctypes.c_double, dp, dp]
-        L.mbo_matvec.argtypes = [
-            dp, dp, i64, ctypes.POINTER(ctypes.c_int64), i64,
-            ctypes.c_double, ctypes.c_double, ctypes.c_int, dp,
-        ]
-        L.mbo_assemble.argtypes = [dp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
-        L.mbo_num_threads.restype = ctypes.c_int
-        _lib = L
+        _lib = load(_SO)
     return _lib
 
 
