@@ -43,7 +43,9 @@ typedef enum {
                               or cudaMalloc failed                           */
     MB_ECUDA = 3,          /* a CUDA runtime call failed                      */
     MB_ENOTCONVERGED = 4,  /* Krylov solver hit maxit; best iterate written   */
-    MB_ETIMEOUT = 5,       /* a bounded device wait ran out                   */
+    MB_ETIMEOUT = 5,       /* reserved for a bounded device wait that ran out;
+                              no call returns it: no kernel of this library
+                              waits on the host or on another kernel         */
     MB_ESINGULAR = 6       /* a Cholesky factorisation broke down (a body's
                               mobility block not positive definite, e.g. a
                               blob below z = a)                               */
