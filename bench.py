@@ -34,6 +34,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +70,9 @@ def parse():
                    help="matvec precision (fp32 is the benchmark line; fp64 and df64 for "
                         "profiling the other kernels)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--clocks-csv", default="",
+                   help="keep the nvidia-smi samples of the timed region in this file "
+                        "('{rank}' is replaced by the rank; default: a temporary file)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-solve", action="store_true")
     p.add_argument("--solves", type=int, default=30)
@@ -144,14 +148,16 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(),
+                                         f"mb_bench_clocks_{os.getpid()}_gpu{gpu_index}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
@@ -300,7 +306,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     variant = ctx.pair_variant(n, True) if args.prec == "fp32" else None
 
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank))
+                           if args.clocks_csv else None)
     sampler.start()
     time.sleep(0.3)
     ctx.profile_enable(True)

@@ -1,10 +1,13 @@
-"""bench.py's reference arm on the CPU: the FP64 oracle timed on this host's
-cores prints one JSON line with the keys of the benchmark contract, and
-ranks other than 0 exit quietly (the line is printed once per job)."""
+"""bench.py on the CPU.  The reference arm (the FP64 oracle timed on this
+host's cores) prints one JSON line with the keys of the benchmark contract,
+and ranks other than 0 exit quietly (the line is printed once per job).  The
+clock sampler of the timed region parses nvidia-smi's samples (a stand-in
+script here)."""
 import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CMD = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
@@ -45,3 +48,37 @@ def test_reference_arm_other_ranks_exit_quietly():
                          env=_env(RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"), cwd=ROOT)
     assert res.returncode == 0, res.stderr[-2000:]
     assert not [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+
+
+FAKE_SMI = """#!/bin/sh
+# stands in for nvidia-smi --query-gpu=... --format=csv,noheader,nounits -lms 200
+echo "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+echo "0, 1980, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+echo "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+exec sleep 30
+"""
+
+
+def test_clock_sampler_reads_nvidia_smi_samples(tmp_path, monkeypatch):
+    """The clock record of the timed region: median SM clock, maximum, and the
+    throttle reasons seen, parsed from nvidia-smi's CSV samples."""
+    import bench
+
+    smi = tmp_path / "nvidia-smi"
+    smi.write_text(FAKE_SMI)
+    smi.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    for path in (str(tmp_path / "out" / "clocks.csv"), None):
+        s = bench.ClockSampler(0, path)
+        s.start()
+        deadline = time.time() + 10
+        while time.time() < deadline:
+            if os.path.exists(s.path) and open(s.path).read().count("\n") >= 3:
+                break
+            time.sleep(0.05)
+        rec = s.stop()
+        assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                       "samples": 3}
+        assert os.path.exists(s.path)
+        if path is None:
+            os.remove(s.path)
