@@ -46,3 +46,29 @@ def test_null_context_is_rejected_without_gpu():
     L = mb.load_library()
     assert L.mb_context_destroy(None) == 1  # MB_EINVAL
     assert L.mb_mobility_matvec(None, None, None, 0, 1.0, 1.0, 1, 1, None, None) == 1
+
+
+def test_errors_are_status_codes_without_a_gpu():
+    """On a machine without a GPU the library reports errors, never aborts:
+    creating a context is MB_ECUDA with a message, and the allocation-free
+    matvec checks its arguments on the host (MB_EINVAL) before touching a
+    device; N = 0 is a no-op."""
+    import ctypes
+
+    import pytest
+
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = mb.load_library()
+    h = ctypes.c_void_p()
+    assert L.mb_context_create(ctypes.byref(h), 0, 0) == 3  # MB_ECUDA
+    assert L.mb_last_error(None)
+    i64, dbl = ctypes.c_int64, ctypes.c_double
+    call = L.mb_mobility_matvec_noalloc
+    assert call(None, None, i64(65537), dbl(0.5), dbl(1.0), 1, None, None) == 1
+    assert b"MB_NOALLOC_MAX_BLOBS" in L.mb_last_error(None)
+    assert call(None, None, i64(-1), dbl(0.5), dbl(1.0), 1, None, None) == 1
+    assert call(None, None, i64(10), dbl(0.0), dbl(1.0), 1, None, None) == 1
+    assert call(None, None, i64(10), dbl(0.5), dbl(1.0), 1, None, None) == 1
+    assert call(None, None, i64(0), dbl(0.5), dbl(1.0), 1, None, None) == 0
