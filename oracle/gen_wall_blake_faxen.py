@@ -92,7 +92,8 @@ def emit(name, args, exprs, doc):
     return "\n".join(lines)
 
 
-def main():
+def render() -> str:
+    """The header's text, generated from the definition."""
     args, faxen2, src_img, src_free = build()
     parts = [
         "/* GENERATED by oracle/gen_wall_blake_faxen.py from the definition of the\n"
@@ -121,9 +122,13 @@ def main():
             "8 pi (1 + a^2/6 Lap_y) Oseen(x - y)",
         ),
     ]
+    return "\n\n".join(parts) + "\n"
+
+
+def main():
     out = os.path.join(HERE, "wall_blake_faxen.h")
     with open(out, "w") as fh:
-        fh.write("\n\n".join(parts) + "\n")
+        fh.write(render())
     print("wrote", out, file=sys.stderr)
 
 
