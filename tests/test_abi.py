@@ -72,3 +72,16 @@ def test_errors_are_status_codes_without_a_gpu():
     assert call(None, None, i64(10), dbl(0.0), dbl(1.0), 1, None, None) == 1
     assert call(None, None, i64(10), dbl(0.5), dbl(1.0), 1, None, None) == 1
     assert call(None, None, i64(0), dbl(0.5), dbl(1.0), 1, None, None) == 0
+
+
+def test_binding_declares_every_signature():
+    """The Python binding gives every exported entry point its argument types
+    (so 64-bit sizes and pointers are never passed as default C ints) and an
+    mb_status (int) or documented return type."""
+    import ctypes
+
+    L = mb.load_library()
+    for name in mb.EXPORTED_SYMBOLS:
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, name
+        assert fn.restype in (ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t), name
