@@ -213,34 +213,41 @@ def _place(rng, radii, box, zlo, zhi, gap, rho_of=None, a=0.0, max_tries=2_000_0
     Centres are uniform in [0, box]^2 x [zlo, zhi]; two bodies are accepted
     only if their centres are at least r_p + r_q + gap apart.  When `rho_of`
     is given, each body's orientation is drawn as well and rejected unless
-    every blob stays at height >= a.
+    every blob stays at height >= a.  A centre at least r_p + a above the
+    wall keeps every blob at height >= a whatever the orientation, so the
+    orientation test only runs below that height.
     """
     n = len(radii)
     cell = 2.0 * max(radii) + gap
     grid = _CellGrid(cell)
     centres = np.zeros((n, 3))
+    placed = []  # (x, y, z, r) of accepted bodies, plain floats
     quats = random_unit_quaternions(rng, n)
     tries = 0
     for p in range(n):
+        rp = float(radii[p])
         while True:
             tries += 1
             if tries > max_tries:
                 raise RuntimeError("placement did not converge; domain too dense")
-            c = np.array([rng.uniform(0, box), rng.uniform(0, box), rng.uniform(zlo, zhi)])
+            cx, cy, cz = rng.uniform(0, box), rng.uniform(0, box), rng.uniform(zlo, zhi)
             ok = True
-            for k in grid.neighbours(c):
-                if np.linalg.norm(c - centres[k]) < radii[p] + radii[k] + gap:
+            for k in grid.neighbours((cx, cy)):
+                x, y, z, rk = placed[k]
+                lim = rp + rk + gap
+                if math.sqrt((cx - x) ** 2 + (cy - y) ** 2 + (cz - z) ** 2) < lim:
                     ok = False
                     break
             if not ok:
                 continue
-            if rho_of is not None:
+            if rho_of is not None and cz - rp < a:
                 th = quats[p]
-                if c[2] + _lowest_blob_height(th, rho_of(p)) < a:
+                if cz + _lowest_blob_height(th, rho_of(p)) < a:
                     quats[p] = random_unit_quaternions(rng, 1)[0]
                     continue
-            centres[p] = c
-            grid.add(p, c)
+            centres[p] = (cx, cy, cz)
+            placed.append((cx, cy, cz, rp))
+            grid.add(p, (cx, cy))
             break
     return centres, quats
 
