@@ -887,6 +887,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         sig.gen = ctx->alloc_gen; sig.j = j; sig.m = m; sig.inner = (int)inner;
                         sig.wall = p->wall; sig.variant = ctx->pair_variant;
                         sig.pc_max_np = ctx->pc_max_np; sig.pc_kind = ctx->pc_kind;
+                        sig.pc_factored = ctx->pc_factored;
                         sig.mode = resist;
                         sig.shift = shift;
                         sig.n = n; sig.nb = nb; sig.L = L;

@@ -28,7 +28,8 @@ struct DevBuf {
 // and workspace pointers they read.
 struct IterSig {
     uint64_t gen = 0;
-    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0, mode = 0;
+    int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0, mode = 0,
+        pc_factored = 0;
     const void *shift = nullptr;
     int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
     double a = 0.0, eta = 0.0;
@@ -37,7 +38,7 @@ struct IterSig {
     {
         return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
                variant == o.variant && pc_max_np == o.pc_max_np && pc_kind == o.pc_kind &&
-               mode == o.mode && shift == o.shift &&
+               mode == o.mode && pc_factored == o.pc_factored && shift == o.shift &&
                n == o.n && nb == o.nb &&
                L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
                V == o.V && Z == o.Z && sm == o.sm;
@@ -86,6 +87,8 @@ struct mb_context {
     int pc_max_np = 0;
     int pc_kind = 0;             // mb_precond of the current blocks
     int pc_schur = 1;            // 0: blocks hold M_pp^-1 only (resistance problem)
+    int pc_factored = 0;         // 1: blocks hold L, G = L^-1 K and -N (applied by
+                                 // triangular solves), 0: explicit inverses
     int64_t pc_shapes = 0;       // shared kind: distinct shapes
 
     // solver workspace

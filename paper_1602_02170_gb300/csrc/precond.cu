@@ -25,6 +25,9 @@
 namespace mb {
 namespace {
 
+#ifndef MB_SETUP_SCRATCH_MB
+#define MB_SETUP_SCRATCH_MB 256  // scratch of one group of bodies in the split setup
+#endif
 constexpr int kSetupThreads = 256;
 constexpr int kSmemMaxRows = 160;   // n = 3 n_p rows held in shared memory up to this
 
@@ -547,14 +550,16 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
         // of G = L^-1 K follows from the same pivot row.
         for (int c = 0; c < n; ++c) {
             __syncthreads();  // step c - 1 finished with col
-            for (int k = threadIdx.x; k < c; k += blockDim.x) col[k] = L[(size_t)c * ld + k];
+            // the pivot row with its diagonal entry: every warp reads A[c][c]
+            // from here, since thread 0 overwrites it in L below
+            for (int k = threadIdx.x; k <= c; k += blockDim.x) col[k] = L[(size_t)c * ld + k];
             __syncthreads();
             // pivot d = A[c][c] - |L[c][0:c]|^2, computed by every warp alike
             double acc = 0.0;
             for (int k = lane; k < c; k += 32) acc += col[k] * col[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const double d = L[(size_t)c * ld + c] - acc;
+            const double d = col[c] - acc;
             if (!(d > 0.0)) {  // the same value in every thread
                 fail = 1;
                 break;
@@ -1094,15 +1099,39 @@ __global__ void __launch_bounds__(256) pc_product_kernel(
     }
 }
 
-// Runs S1..S4 over groups of bodies whose scratch fits the cap.
+// S3' for the factored form (instead of S3 and S4): P_p keeps L^T in its
+// upper triangle (written by S2) and receives G = L^-1 K_p in the border
+// columns n..n+5 of rows 0..n-1 and 1 / L_kk in the border row n; the corner
+// already holds -N.  precond_apply_factored_kernel applies it.
+__global__ void __launch_bounds__(256) pc_keep_factor_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr)
+{
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    const int lane = threadIdx.x & 31;
+    for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < nb;
+         p += warps) {
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        double *Pp = P + poff[p];
+        const double *G = scr.G(p), *dW = scr.dW(p);
+        for (int i = lane; i < n; i += 32) {
+#pragma unroll
+            for (int b = 0; b < 6; ++b) Pp[(size_t)i * m + n + b] = G[6 * i + b];
+            Pp[(size_t)n * m + i] = dW[i];
+        }
+    }
+}
+
+// Runs S1..S4 over groups of bodies whose scratch fits the cap (S1, S2, S3'
+// with `factored`).
 mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double *q,
                       const int64_t *start, const int64_t *poff, double *P, int max_np, double a,
                       double eta, int wall, int *flag, int flag_slot, int schur, cudaStream_t s,
-                      const double *shift)
+                      const double *shift, bool factored = false)
 {
     const int nmax = 3 * max_np;
     const int64_t stride = split_stride(nmax);
-    const int64_t cap_bytes = (int64_t)256 << 20;
+    const int64_t cap_bytes = (int64_t)MB_SETUP_SCRATCH_MB << 20;
     const int64_t group = std::max<int64_t>(1, std::min<int64_t>(nb, cap_bytes / (8 * stride)));
     MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * group, "preconditioner scratch"));
     SplitScratch scr{(double *)ctx->sol_dots.ptr, stride, nmax};
@@ -1139,6 +1168,13 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
                                                   (int)fsmem));
             factor<<<(int)std::min<int64_t>(ng, 4 * (int64_t)ctx->sm_count), 256, fsmem, s>>>(
                 ng, r, q + 3 * g0, st, po, P, scr, flag, flag_slot, g0, schur);
+        }
+        if (factored) {
+            pc_keep_factor_kernel<<<(int)std::min<int64_t>(ceil_div(ng, 8), 8 * (int64_t)ctx->sm_count),
+                                    256, 0, s>>>(ng, st, po, P, scr);
+            count_launch(3);
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+            continue;
         }
         const int gt = (int)std::min<int64_t>(ng * col_groups, 16 * (int64_t)ctx->sm_count);
         if (nmax > kSplitMaxRows) {
@@ -1277,11 +1313,16 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
         MB_TRY(ensure(ctx, ctx->sol_dots, sizeof(double) * stride * grid, "Cholesky scratch"));
         scratch = (double *)ctx->sol_dots.ptr;
     }
+    // Many bodies with large blocks keep the factored form: its application
+    // costs the FP64 FMAs of the explicit inverse's GEMV and its setup a third
+    // of the explicit inverse's (no L^-1, no W^T W).  Few or small bodies keep
+    // the explicit inverse, whose application spreads over many CTAs.
+    const bool factored = !lsmem && nmax <= kSplitMaxRowsSmem && nb >= ctx->sm_count;
     auto launch = [&](auto kern) -> mb_status {
         if (nmax <= kSplitMaxRowsSmem)
             return setup_split(ctx, nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
                                (const int64_t *)ctx->pinv_off.ptr, (double *)ctx->pinv.ptr, max_np,
-                               a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s, shift);
+                               a, eta, wall, (int *)ctx->flag.ptr, -1, schur, s, shift, factored);
         MB_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         kern<<<grid, kSetupThreads, smem, s>>>(nb, r, q, (const int64_t *)ctx->blob_start_copy.ptr,
@@ -1309,6 +1350,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     ctx->pc_kind = MB_PRECOND_WALL;
     ctx->pc_shapes = 0;
     ctx->pc_schur = schur;
+    ctx->pc_factored = factored ? 1 : 0;
     if (first_bad != big) {
         ctx->pc_nb = 0;
         return set_err(ctx, MB_ESINGULAR,
@@ -1462,6 +1504,7 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
     ctx->pc_kind = MB_PRECOND_FREE_SHARED;
+    ctx->pc_factored = 0;
     ctx->pc_shapes = ns;
     ctx->pc_schur = schur;
     if (first_bad != big) {
@@ -1471,6 +1514,145 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
                        "positive definite", (long long)rep_body[first_bad]);
     }
     return MB_OK;
+}
+
+// Application of the factored form (see pc_keep_factor_kernel), one CTA per
+// body, x = the body's rows in shared memory:
+//   y = L^-1 w                  forward substitution by panels of kFacPanel
+//                               rows: warp 0 solves the panel's triangle,
+//                               then all threads subtract the panel's columns
+//                               from the rows below (rows of L^T, coalesced);
+//   U = -N (g + G^T y)          the body rows (skipped for the blob block alone);
+//   lambda = L^-T (y + G U)     backward substitution by panels from the
+//                               bottom: the panel's rows first lose their dot
+//                               products with the solved rows (a warp per
+//                               row), then warp 0 solves the panel's triangle.
+// The panel's triangle is staged in shared memory with its columns scaled by
+// 1 / L_kk, so that each step of warp 0's dependent chain is one shuffle and
+// one FMA.  The same FMAs as the explicit inverse's GEMV (n^2 per body).
+constexpr int kFacPanel = 32;
+
+__global__ void __launch_bounds__(256) precond_apply_factored_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    const double *__restrict__ P, const double *__restrict__ w, const double *__restrict__ g,
+    double *__restrict__ lam, double *__restrict__ UO, int body_rows)
+{
+    extern __shared__ double x[];              // n: the body's vector
+    __shared__ double T[kFacPanel * kFacPanel];  // scaled panel triangle
+    __shared__ double red[8 * 6];
+    __shared__ double hU[12];                   // h = g + G^T y, then U
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned full = 0xffffffffu;
+    for (int64_t p = blockIdx.x; p < nb; p += gridDim.x) {
+        const int64_t b0 = start[p];
+        const int n = 3 * (int)(start[p + 1] - b0), m = n + 6;
+        const double *Pp = P + poff[p];
+        const double *dW = Pp + (size_t)n * m;  // border row n: 1 / L_kk
+        __syncthreads();  // the previous body is finished with x, T, hU
+        for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = w[3 * b0 + i];
+        // ---- forward: y = L^-1 w; L[i][k] = Lt[k][i] = Pp[k m + i]
+        for (int c0 = 0; c0 < n; c0 += kFacPanel) {
+            const int pw = min(kFacPanel, n - c0);
+            // T[k][l] = L[c0 + l][c0 + k] / L_kk for k < l (row k of L^T, scaled)
+            for (int e = threadIdx.x; e < pw * pw; e += blockDim.x) {
+                const int k = e / pw, l = e % pw;
+                T[k * kFacPanel + l] = l > k ? Pp[(size_t)(c0 + k) * m + c0 + l] * dW[c0 + k] : 0.0;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // lane l: a = x[c0 + l] minus the panel's earlier columns;
+                // y_k = a_k / L_kk at the end
+                double a = lane < pw ? x[c0 + lane] : 0.0;
+                for (int k = 0; k < pw - 1; ++k) {
+                    const double ak = __shfl_sync(full, a, k);
+                    if (lane > k) a -= T[k * kFacPanel + lane] * ak;
+                }
+                if (lane < pw) x[c0 + lane] = a * dW[c0 + lane];
+            }
+            __syncthreads();
+            for (int i = c0 + pw + threadIdx.x; i < n; i += blockDim.x) {
+                double s0 = x[i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int k = 0;
+                for (; k + 4 <= pw; k += 4) {
+                    s0 -= Pp[(size_t)(c0 + k) * m + i] * x[c0 + k];
+                    s1 -= Pp[(size_t)(c0 + k + 1) * m + i] * x[c0 + k + 1];
+                    s2 -= Pp[(size_t)(c0 + k + 2) * m + i] * x[c0 + k + 2];
+                    s3 -= Pp[(size_t)(c0 + k + 3) * m + i] * x[c0 + k + 3];
+                }
+                for (; k < pw; ++k) s0 -= Pp[(size_t)(c0 + k) * m + i] * x[c0 + k];
+                x[i] = (s0 + s1) + (s2 + s3);
+            }
+            __syncthreads();
+        }
+        // ---- body rows: U = -N (g + G^T y); G[i][b] = Pp[i m + n + b]
+        if (body_rows) {
+            double hb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double yi = x[i];
+#pragma unroll
+                for (int b = 0; b < 6; ++b) hb[b] += Pp[(size_t)i * m + n + b] * yi;
+            }
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                double v = hb[b];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+                if (lane == 0) red[6 * warp + b] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 6) {
+                double h = g[6 * p + threadIdx.x];
+                for (int ww = 0; ww < nw; ++ww) h += red[6 * ww + threadIdx.x];
+                hU[threadIdx.x] = h;
+            }
+            __syncthreads();
+            if (threadIdx.x < 6) {
+                // the corner holds -N
+                double u = 0.0;
+#pragma unroll
+                for (int b = 0; b < 6; ++b) u += Pp[(size_t)(n + threadIdx.x) * m + n + b] * hU[b];
+                hU[6 + threadIdx.x] = u;
+                UO[6 * p + threadIdx.x] = u;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                double v = x[i];
+#pragma unroll
+                for (int b = 0; b < 6; ++b) v += Pp[(size_t)i * m + n + b] * hU[6 + b];
+                x[i] = v;
+            }
+            __syncthreads();
+        }
+        // ---- backward: lambda = L^-T x; row k of L^T is Pp[k m + k ..]
+        for (int c1 = n; c1 > 0; c1 -= kFacPanel) {
+            const int c0 = c1 > kFacPanel ? c1 - kFacPanel : 0, pw = c1 - c0;
+            // the panel's rows lose their products with the solved rows
+            for (int k = warp; k < pw; k += nw) {
+                const double *lr = Pp + (size_t)(c0 + k) * m;
+                double sacc = 0.0;
+                for (int i = c1 + lane; i < n; i += 32) sacc += lr[i] * x[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(full, sacc, o);
+                if (lane == 0) x[c0 + k] -= sacc;
+            }
+            // T[l][k] = Lt[c0 + l][c0 + k] / L_kk for l < k
+            for (int e = threadIdx.x; e < pw * pw; e += blockDim.x) {
+                const int l = e / pw, k = e % pw;
+                T[l * kFacPanel + k] = l < k ? Pp[(size_t)(c0 + l) * m + c0 + k] * dW[c0 + k] : 0.0;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double a = lane < pw ? x[c0 + lane] : 0.0;
+                for (int k = pw - 1; k > 0; --k) {
+                    const double ak = __shfl_sync(full, a, k);
+                    if (lane < k) a -= T[lane * kFacPanel + k] * ak;
+                }
+                if (lane < pw) x[c0 + lane] = a * dW[c0 + lane];
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) lam[3 * b0 + i] = x[i];
+    }
 }
 
 static void precond_apply_impl(mb_context *ctx, const double *w, const double *g, double *lam,
@@ -1487,6 +1669,15 @@ static void precond_apply_impl(mb_context *ctx, const double *w, const double *g
             ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int *)ctx->pc_type.ptr,
             (const int64_t *)ctx->pinv_off.ptr, (const double *)ctx->pinv.ptr,
             (const double *)ctx->pc_theta.ptr, w, g, lam, UO, chunks, rows, body_rows);
+        count_launch();
+        return;
+    }
+    if (ctx->pc_factored) {
+        const int gf = (int)std::min<int64_t>(ctx->pc_nb, 8 * (int64_t)ctx->sm_count);
+        precond_apply_factored_kernel<<<gf, 256, sizeof(double) * 3 * ctx->pc_max_np, s>>>(
+            ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr,
+            (const int64_t *)ctx->pinv_off.ptr, (const double *)ctx->pinv.ptr, w, g, lam, UO,
+            body_rows);
         count_launch();
         return;
     }
