@@ -89,6 +89,33 @@ __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b)
     return a;
 }
 
+// Products and sums with an FP32 operand c (a constant exact in FP32, or a
+// value known to have no low part): the terms of c's absent low part are
+// dropped.  a * c in 3 operations; a * 2^k exactly in 2; a + c in 7 (the
+// sloppy form above with b.lo = 0).
+__device__ __forceinline__ dfl mulf(dfl a, float c)
+{
+    const float p = a.hi * c;
+    float e = fmaf(a.hi, c, -p);
+    e = fmaf(a.lo, c, e);
+    return dfl(p, e);
+}
+
+__device__ __forceinline__ dfl mul_pow2(dfl a, float c) { return dfl(a.hi * c, a.lo * c); }
+
+__device__ __forceinline__ dfl addf(dfl a, float c)
+{
+    const dfl s = two_sum(a.hi, c);
+    return dfl(s.hi, s.lo + a.lo);
+}
+
+// y^2 of an FP32 value as an exact double-float
+__device__ __forceinline__ dfl sqf(float y)
+{
+    const float p = y * y;
+    return dfl(p, fmaf(y, y, -p));
+}
+
 __device__ __forceinline__ bool operator<(dfl a, dfl b)
 {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
@@ -100,10 +127,9 @@ __device__ __forceinline__ dfl mb_rsqrt(dfl x)
 {
     x = fast_two_sum(x.hi, x.lo);  // the FP32 estimate needs the normalised hi
     const float y0 = rsqrtf(x.hi);
-    const dfl y(y0, 0.f);
-    // r = 1 - x y0^2, small; y = y0 + y0 r / 2
-    const dfl r = dfl(1.0) - x * (y * y);
-    return y + dfl(0.5f * y0, 0.f) * r;
+    // r = 1 - x y0^2, small; y = y0 + y0 r / 2 (y0 has no low part)
+    const dfl r = dfl(1.0) - x * sqf(y0);
+    return addf(mulf(r, 0.5f * y0), y0);
 }
 
 __device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }

@@ -187,6 +187,26 @@ __global__ void __launch_bounds__(NT) pair_f64_kernel(
     }
 }
 
+// FP64 kernel for larger problems: symmetric over the upper-triangular
+// pairs of blocks of kNT blobs (one target per thread); see f64sym_item.
+template <bool WALL>
+__global__ void __launch_bounds__(kNT) pair_f64sym_kernel(
+    const double *__restrict__ r, const double *__restrict__ f, int64_t n, int64_t nb,
+    int64_t n_items, PairConsts<double> k, double *__restrict__ u, double scale)
+{
+    __shared__ double sm[9 * kNT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int64_t lo_r = 0, hi_r = nb;
+        while (hi_r - lo_r > 1) {
+            const int64_t mid = (lo_r + hi_r) >> 1;
+            if (mid * nb - mid * (mid - 1) / 2 <= item) lo_r = mid;
+            else hi_r = mid;
+        }
+        const int64_t I = lo_r, J = I + (item - (I * nb - I * (I - 1) / 2));
+        f64sym_item<WALL, kNT>(sm, r, f, n, I, J, k, u, scale);
+    }
+}
+
 // Double-float kernel: symmetric over the upper-triangular pairs of blocks
 // of kNT blobs (one target per thread); see dfsym_item.
 // Flow evaluation at points other than the blobs (targets != sources):
@@ -560,6 +580,25 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         return MB_OK;
     }
     const bool small = n < kSmallN;
+    if (!small) {
+        // symmetric FP64 kernel: zero u, one launch over the block-pair triangle
+        const int res = wall ? resident_ctas(ctx, pair_f64sym_kernel<true>)
+                             : resident_ctas(ctx, pair_f64sym_kernel<false>);
+        const int64_t nb = ceil_div(n, kNT);
+        const int64_t items = nb * (nb + 1) / 2;
+        const int grid = (int)std::min<int64_t>(items, res);
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        auto *ev = profile_begin(ctx, s);
+        const PairConsts<double> k = PairConsts<double>::make(a);
+        if (wall)
+            pair_f64sym_kernel<true><<<grid, kNT, 0, s>>>(r, f, n, nb, items, k, u, scale);
+        else
+            pair_f64sym_kernel<false><<<grid, kNT, 0, s>>>(r, f, n, nb, items, k, u, scale);
+        profile_end(ev, s);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        return MB_OK;
+    }
     Plan p;
     if (small) {
         const int res = wall ? resident_ctas(ctx, pair_f64_kernel<true, kSmallNT>, kSmallNT)
@@ -770,14 +809,18 @@ mb_status noalloc_setup(int dev, NoallocDevice **out)
     return MB_OK;
 }
 
-bool on_device(const void *p)
+// Device memory of device `dev` (the one whose scratch array the call uses),
+// or managed memory.  Memory of another GPU would reach the kernel as a peer
+// pointer, so it is refused on the host instead.
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) ||
+           at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -798,7 +841,7 @@ extern "C" mb_status mb_mobility_matvec_noalloc(const double *r, const double *f
         return MB_EINVAL;
     }
     if (n == 0) return MB_OK;
-    if (!r || !f || !u || !on_device(r) || !on_device(f) || !on_device(u)) {
+    if (!r || !f || !u) {
         set_thread_err("r, f and u must be device pointers");
         return MB_EINVAL;
     }
@@ -807,6 +850,10 @@ extern "C" mb_status mb_mobility_matvec_noalloc(const double *r, const double *f
         cudaGetLastError();
         set_thread_err("cudaGetDevice failed");
         return MB_ECUDA;
+    }
+    if (!on_device(r, dev) || !on_device(f, dev) || !on_device(u, dev)) {
+        set_thread_err("r, f and u must be device pointers on the current device");
+        return MB_EINVAL;
     }
     NoallocDevice *d = nullptr;
     mb_status st = noalloc_setup(dev, &d);

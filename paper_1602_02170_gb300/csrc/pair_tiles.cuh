@@ -303,6 +303,101 @@ __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__res
             atomicAdd(u + 3 * ib + c, scale * ((double)sum[1][c] - (double)comp[1][c]));
 }
 
+// FP64 forms of the FP32-operand operations of df32.cuh, so that the
+// regrouped pair formula below serves FP64 and double-float alike.
+__device__ __forceinline__ double mulf(double a, float c) { return a * (double)c; }
+__device__ __forceinline__ double mul_pow2(double a, float c) { return a * (double)c; }
+__device__ __forceinline__ double addf(double a, float c) { return a + (double)c; }
+
+// pair_sym (both directions of one unordered pair) for FP64 and
+// double-float operands, with the wall polynomials regrouped so that
+// constants exact in FP32 (2, 4, 6, 10, 12, 20, ...) take the cheaper
+// FP32-operand products of df32.cuh and the factors of 1/3 are applied to
+// three shared monomials once:
+//   T1 = E t2,  t4_3 = t4 / 3,  t2_3 = t2 / 3,  T2_3 = E t4 / 3,
+//   f1 = 2 (T1 - p + t4_3 - t2_3) - 10 T2_3 - 1
+//   f2 = 2 (3 p - 5 T1 + t2) + 10 (7 T2_3 - t4_3) - 1
+//   f3 = 2 hs + e3 [4 (5 T1 - t2 - 3 p) + 20 (2 t4_3 - 7 T2_3)]
+//   f4 = 2 hs - 20 e3 t4_3
+//   f5 = 4 (15 T2_3 - 2 t4_3 - hs^2 - T1)
+// (the f1..f5 of rpy_wall.cuh term by term), and f2 / rho^2, f3 / rho,
+// f4 / rho formed once for both directions as in pair_sym2.
+template <bool WALL, typename T>
+__device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, T fy, T fz, T gx,
+                                            T gy, T gz, const PairConsts<T> &k, T &ux, T &uy,
+                                            T &uz, T &vx, T &vy, T &vz)
+{
+    const T dxy2 = dx * dx + dy * dy;
+    const T r2 = mb_max(dz * dz + dxy2, k.tiny);
+    const T inv = mb_rsqrt(r2);
+    const T inv2 = inv * inv;
+    T C = inv * (k.c1 + k.c2 * inv2);
+    T D = inv * inv2 * (k.c3 + k.c4 * inv2);
+    if (r2 < k.four_a2) {
+        C = T(1) - k.k1 * (r2 * inv);
+        D = k.k2 * inv;
+    }
+    const T rf_xy = dx * fx + dy * fy;
+    const T g = D * (rf_xy + dz * fz);
+    const T rb_xy = dx * gx + dy * gy;
+    const T gb = D * (rb_xy + dz * gz);
+    if (!WALL) {
+        ux += C * fx + g * dx;
+        uy += C * fy + g * dy;
+        uz += C * fz + g * dz;
+        vx += C * gx + gb * dx;
+        vy += C * gy + gb * dy;
+        vz += C * gz + gb * dz;
+        return;
+    }
+    constexpr T third(1.0 / 3.0);
+    const T R3 = zi + zj;
+    const T invR = mb_rsqrt(R3 * R3 + dxy2);
+    const T invR2 = invR * invR;
+    const T hs = zj * invR;
+    const T ht = zi * invR;
+    const T e3 = hs + ht;
+    const T E = e3 * e3;
+    const T t2 = k.a2 * invR2;
+    const T t4 = t2 * t2;
+    const T p = hs * ht;
+    const T T1 = E * t2;
+    const T t4_3 = t4 * third;
+    const T t2_3 = t2 * third;
+    const T T2_3 = E * t4_3;
+    const T hs2 = mul_pow2(hs, 2.f);
+    const T f1 = addf(mul_pow2(T1 + (-p) + t4_3 + (-t2_3), 2.f) + mulf(T2_3, -10.f), -1.f);
+    const T f2 = addf(mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f) +
+                            mulf(mulf(T2_3, 7.f) + (-t4_3), 10.f),
+                        -1.f);
+    const T in3 = mul_pow2(mulf(T1, 5.f) + (-t2) + mulf(p, -3.f), 4.f) +
+                    mulf(mul_pow2(t4_3, 2.f) + mulf(T2_3, -7.f), 20.f);
+    const T f3 = hs2 + e3 * in3;
+    const T f4 = hs2 + mulf(e3 * t4_3, -20.f);
+    const T f5 = mul_pow2(mulf(T2_3, 15.f) + mul_pow2(t4_3, -2.f) + (-(hs * hs)) + (-T1), 4.f);
+    const T s = k.sw * invR;
+    const T Cx = C + s * f1;
+    const T A2 = f2 * invR2;
+    const T A3 = f3 * invR;
+    const T A4 = f4 * invR;
+    // forward: M_ij f_j
+    const T RF = rf_xy + R3 * fz;
+    const T gw = A2 * RF + A3 * fz;
+    const T kz = A4 * RF + f5 * fz;
+    const T Gx = g + s * gw;
+    ux += Cx * fx + Gx * dx;
+    uy += Cx * fy + Gx * dy;
+    uz += Cx * fz + g * dz + s * (gw * R3 + kz);
+    // reverse: M_ij^T f_i (f3 and f4 exchange roles)
+    const T RB = rb_xy + R3 * gz;
+    const T gwb = A2 * RB + A4 * gz;
+    const T kzb = A3 * RB + f5 * gz;
+    const T Gb = gb + s * gwb;
+    vx += Cx * gx + Gb * dx;
+    vy += Cx * gy + Gb * dy;
+    vz += Cx * gz + gb * dz + s * (gwb * R3 + kzb);
+}
+
 // Symmetric double-float item over block pair (I, J), I <= J, blocks of NT
 // blobs, one target per thread; the rotating reverse accumulators of
 // x2sym_item in double-float.  Sources are staged as three float4 (x_hi,
@@ -360,9 +455,9 @@ __device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__re
                 const int s = g * 32 + ((lane + t) & 31);
                 const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
                 const dfl zj(B.x, B.y);
-                pair_sym<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
-                                    dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), gx, gy, gz, k, ux,
-                                    uy, uz, vx, vy, vz);
+                pair_sym_rg<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                                  dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), gx, gy, gz, k, ux,
+                                  uy, uz, vx, vy, vz);
                 const int from = (lane + 1) & 31;
                 vx.hi = __shfl_sync(0xffffffffu, vx.hi, from);
                 vx.lo = __shfl_sync(0xffffffffu, vx.lo, from);
@@ -387,6 +482,81 @@ __device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__re
         atomicAdd(u + 3 * i, scale * to_double(ux));
         atomicAdd(u + 3 * i + 1, scale * to_double(uy));
         atomicAdd(u + 3 * i + 2, scale * to_double(uz));
+    }
+}
+
+// FP64 symmetric item over block pair (I, J), I <= J, blocks of NT blobs,
+// one target per thread: the scheme of dfsym_item in FP64.  Sources are
+// staged as six FP64 arrays (lanes read consecutive sources: no bank
+// conflicts); each unordered pair is evaluated once for both blobs, the
+// reverse sums rotate through the warp (lane l holds source l's sum after 32
+// steps) and reach u with FP64 atomics, so u must be zeroed beforehand.
+// Diagonal items run forward only over all ordered pairs.
+template <bool WALL, int NT>
+__device__ __forceinline__ void f64sym_item(double *__restrict__ sm, const double *__restrict__ r,
+                                            const double *__restrict__ f, int64_t n, int64_t I,
+                                            int64_t J, const PairConsts<double> &k,
+                                            double *__restrict__ u, double scale)
+{
+    double *sx = sm, *sy = sm + NT, *sz = sm + 2 * NT, *sfx = sm + 3 * NT, *sfy = sm + 4 * NT,
+           *sfz = sm + 5 * NT, *sRev = sm + 6 * NT;
+    const int lane = threadIdx.x & 31;
+    const bool diag = I == J;
+    const int64_t i = I * NT + threadIdx.x;
+    const int64_t ic = i < n ? i : n - 1;
+    const double xi = r[3 * ic], yi = r[3 * ic + 1], zi = r[3 * ic + 2];
+    const double gx = i < n ? f[3 * i] : 0.0, gy = i < n ? f[3 * i + 1] : 0.0,
+                 gz = i < n ? f[3 * i + 2] : 0.0;
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const int64_t j0 = J * NT;
+    __syncthreads();
+    {
+        const int64_t j = j0 + threadIdx.x;
+        const bool valid = j < n;
+        const int64_t jc = valid ? j : j0;
+        sx[threadIdx.x] = r[3 * jc];
+        sy[threadIdx.x] = r[3 * jc + 1];
+        sz[threadIdx.x] = r[3 * jc + 2];
+        sfx[threadIdx.x] = valid ? f[3 * jc] : 0.0;
+        sfy[threadIdx.x] = valid ? f[3 * jc + 1] : 0.0;
+        sfz[threadIdx.x] = valid ? f[3 * jc + 2] : 0.0;
+        sRev[3 * threadIdx.x] = sRev[3 * threadIdx.x + 1] = sRev[3 * threadIdx.x + 2] = 0.0;
+    }
+    __syncthreads();
+    if (diag) {
+#pragma unroll 1
+        for (int s = 0; s < NT; ++s)
+            pair_accumulate<WALL, double>(xi - sx[s], yi - sy[s], zi - sz[s], zi, sz[s], sfx[s],
+                                          sfy[s], sfz[s], k, ux, uy, uz);
+    } else {
+        for (int g = 0; g < NT / 32; ++g) {
+            double vx = 0.0, vy = 0.0, vz = 0.0;
+#pragma unroll 1
+            for (int t = 0; t < 32; ++t) {
+                const int s = g * 32 + ((lane + t) & 31);
+                pair_sym_rg<WALL, double>(xi - sx[s], yi - sy[s], zi - sz[s], zi, sz[s], sfx[s],
+                                          sfy[s], sfz[s], gx, gy, gz, k, ux, uy, uz, vx, vy, vz);
+                const int from = (lane + 1) & 31;
+                vx = __shfl_sync(0xffffffffu, vx, from);
+                vy = __shfl_sync(0xffffffffu, vy, from);
+                vz = __shfl_sync(0xffffffffu, vz, from);
+            }
+            double *o3 = sRev + 3 * (g * 32 + lane);
+            atomicAdd(o3, vx);
+            atomicAdd(o3 + 1, vy);
+            atomicAdd(o3 + 2, vz);
+        }
+        __syncthreads();
+        const int64_t j = j0 + threadIdx.x;
+        if (j < n) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(u + 3 * j + c, scale * sRev[3 * threadIdx.x + c]);
+        }
+    }
+    if (i < n) {
+        atomicAdd(u + 3 * i, scale * ux);
+        atomicAdd(u + 3 * i + 1, scale * uy);
+        atomicAdd(u + 3 * i + 2, scale * uz);
     }
 }
 
