@@ -1,28 +1,38 @@
 #!/usr/bin/env python
-"""Benchmark of the wall-corrected RPY pair kernel (blob-pair interactions/s).
+"""Benchmark of the wall-corrected RPY pair kernel (blob-pair interactions/s)
+and of the mobility solves built on it (solves/s, p50/p99 latency).
 
-Workload: the wall-RPY mobility product u = M f for N = 65,536 free blobs,
-a = 0.5, x, y ~ U[0, 400], z ~ U[a, 3a], f ~ N(0, 1) (seeded, synthetic).
-One step = one mb_mobility_matvec call (FP32 pair kernel with hi/lo
-positions and Kahan-compensated accumulation) on inputs already in HBM; the
-L2 is flushed (256 MB write) before every timed step.  Pairs per step = N^2
+Workload of the headline: the wall-RPY mobility product u = M f for N = 65,536
+free blobs, a = 0.5, x, y ~ U[0, 400], z ~ U[a, 3a], f ~ N(0, 1) (seeded,
+synthetic).  One step = one mb_mobility_matvec call (FP32 pair kernel with
+hi/lo positions and Kahan-compensated accumulation) on inputs already in HBM;
+the L2 is flushed (256 MB write) before every timed step.  Pairs per step = N^2
 (self pairs included).
 
 Also reported on the same line:
   e2e          the same metric through the C ABI with host buffers (pinned):
                host->device copies of r and f and the device->host copy of u
                inside the timed region of every step
-  roofline     the pair kernel against the FP32 ALU peak (152 SMs x 128 FP32
-               lanes x 2 flop x 2.07 GHz), algorithmic flops per pair as
-               written in the kernel's formula
-  cpu_baseline the FP64 oracle on this host's cores, on a bounded sample
-  solve        mobility solves of 8 x 42-blob shells (the small suspension),
-               solves/s and p50/p99 latency, error vs the oracle
+  roofline     the pair kernel against the FP32 FMA rate measured in this run
+               (mb_measure_fma_rate), with the method's flops per ordered pair
+               (Eq. RPYTensor plus the wall correction, counted as written)
+  cpu_baseline the FP64 oracle on this host's cores, on the 4,096 sampled
+               targets of the workload
+  matvec_err   the FP32 product against the oracle on those 4,096 targets
+               (relative L2 bound 1e-5: the line fails above it)
+  matvec_fp64, matvec_df64   the product in FP64 and in double-float, each
+               timed and compared with the oracle on the same targets
+  solve, solve_fp64   mobility solves of 8 x 42-blob shells (solves/s, p50/p99)
+  monolayer    the 4,096 x 162-blob sedimented monolayer solve (mixed, 1e-8)
+  batch        256 independent mixed suspensions solved together
+  serve        the Poisson serving stream: saturated at 200 req/s, then at
+               0.8 x the measured capacity (p50/p99, served/offered, queue)
 
 --impl reference times the FP64 oracle (the reference arm of this repo) on
 this host's cores on the same workload, a bounded sample of targets per step.
 Multi-GPU: `--gpus N` under torchrun runs N independent replicas (the path is
-not sharded here); value = pairs of all ranks / slowest rank's time.
+not sharded here); value = pairs of all ranks / slowest rank's time.  The
+solve sections run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -41,14 +51,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT = 65536
-# Arithmetic in the kernel's per-pair formula (rpy_wall.cuh, pair_accumulate
-# with the wall, plus the hi/lo separation): multiplies and adds counted
-# separately, rsqrt as one; the rare overlap branch is not counted.
-FLOPS_PER_PAIR = 117
-FP32_LANES_PER_SM = 128
-SMS = 152
+# The method's arithmetic per ordered blob pair, counted from the formulas as
+# written (multiplies and adds separately, rsqrt as one; the rare overlap
+# branch not counted): the free RPY tensor of Eq. RPYTensor applied to f_j
+# (29) and the wall correction with the accumulation into u_i (79).  The FP32
+# kernel adds 9 for the separation of its hi/lo positions, a device of its
+# precision rather than work of the method, so it is not counted.
+FLOPS_PER_PAIR = 108
+FLOPS_BASIS = ("Eq. RPYTensor far branch applied to f_j (29) + wall correction and "
+               "accumulation (79), as written; the FP32 kernel's hi/lo separation (9) "
+               "not counted")
 SM_MAX_MHZ = 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+ORACLE_ROWS = 4096  # the workload's oracle subsample of targets
+MATVEC_TOL = 1e-5
 KERNEL_NAMES = {0: "pair_f32_kernel<wall> (scalar, 1 target/thread)",
                 1: "pair_f32x2_kernel<wall,1> (packed f32x2, 2 targets/thread)",
                 2: "pair_f32x2_kernel<wall,2> (packed f32x2, 4 targets/thread)",
@@ -67,36 +82,45 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df64"],
-                   help="matvec precision (fp32 is the benchmark line; fp64 and df64 for "
-                        "profiling the other kernels)")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+                   help="precision of the timed matvec (fp32 is the benchmark line; fp64 and "
+                        "df64 for profiling the other kernels)")
     p.add_argument("--clocks-csv", default="",
                    help="keep the nvidia-smi samples of the timed region in this file "
                         "('{rank}' is replaced by the rank; default: a temporary file)")
-    p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-solve", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle leg (and with it the accuracy figures)")
+    p.add_argument("--no-solve", action="store_true", help="skip the small-suspension solves")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the FP64/df64 matvecs and the monolayer, batch and serving "
+                        "sections of the default line")
     p.add_argument("--solves", type=int, default=30)
     p.add_argument("--solve-prec", default="mixed", choices=["mixed", "fp32", "fp64", "df64"],
                    help="precision of the --workload small solves")
     p.add_argument("--precond", default="wall", choices=["wall", "free_shared"],
                    help="block preconditioner of the --workload small / monolayer solves")
     p.add_argument("--workload", choices=["matvec", "small", "monolayer", "batch", "serve",
-                                          "resistance", "active", "eval"],
+                                          "resistance", "active", "eval", "setup"],
                    default="matvec",
-                   help="matvec: the benchmark line below; monolayer / batch / serve: the "
-                        "663,552-blob monolayer solve, 256 batched suspensions, and the "
-                        "serving stream, each printing its own JSON line")
-    p.add_argument("--serve-seconds", type=float, default=30.0)
-    p.add_argument("--rate", type=float, default=200.0)
-    p.add_argument("--rates", default="5,8,11,14",
-                   help="serving: comma-separated offered rates (req/s) of the drained runs "
-                        "(empty: 0.5x and 0.8x of the saturated served rate)")
+                   help="matvec: the benchmark line; monolayer / batch / serve: the 663,552-blob "
+                        "monolayer solve, 256 batched suspensions and the serving stream, each "
+                        "printing its own JSON line; setup: the monolayer's preconditioner "
+                        "setup alone")
+    p.add_argument("--rate", type=float, default=200.0, help="serving: saturated offered rate")
+    p.add_argument("--serve-sat-seconds", type=float, default=0.0,
+                   help="serving: arrival window of the saturated run (default 20 s in the "
+                        "default line, 60 s for --workload serve)")
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="serving: arrival window of each sub-saturation run")
+    p.add_argument("--serve-fracs", default="",
+                   help="serving: sub-saturation rates as fractions of the measured capacity "
+                        "(default 0.8 in the default line, 0.5,0.8 for --workload serve)")
+    p.add_argument("--rates", default="",
+                   help="serving: fixed offered rates (req/s) instead of --serve-fracs")
     p.add_argument("--tick-pairs", type=float, default=0.0,
                    help="serving: pair evaluations a request may take per tick in the FP32 "
                         "Arnoldi matvec (0 = engine default, < 0 = no limit)")
-    p.add_argument("--pool", type=int, default=40)
     p.add_argument("--pair-variant", type=int, default=-1,
-                   help="FP32 pair-kernel variant (-1 autotune; 0..3 pin one, e.g. for profiling)")
+                   help="FP32 pair-kernel variant (-1 autotune; 0..4 pin one, e.g. for profiling)")
     return p.parse_args()
 
 
@@ -194,10 +218,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def traffic_for_kernel():
-    """Per-launch DRAM bytes of the pair kernel from the committed ncu summary,
-    only if the kernel source is unchanged since it was captured."""
-    path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+def kernel_record(name="pair_kernel_traffic.json"):
+    """Counters of one kernel from a committed ncu summary (DRAM bytes per
+    launch, FMA-pipe activity), only if the kernel's sources are unchanged
+    since the capture (their SHA-256 is recorded beside the numbers)."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -206,13 +231,13 @@ def traffic_for_kernel():
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest() != rec.get("sha256"):
         return None
-    return rec.get("bytes_per_launch_full_size")
+    return rec
 
 
 # ------------------------------------------------------------------ oracle arm
 def oracle_pairs_per_s(r, f, a, seconds: float, seed: int = 0):
     """Time the FP64 oracle's double loop on a growing target sample until
-    about `seconds` of CPU work; returns (pairs/s, threads, targets)."""
+    about `seconds` of CPU work; returns (pairs/s, threads, targets, s)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -228,6 +253,31 @@ def oracle_pairs_per_s(r, f, a, seconds: float, seed: int = 0):
         if dt >= 0.8 * seconds or nt >= n:
             return len(rows) * n / dt, O.num_threads(), len(rows), dt
         nt = int(min(n, max(2 * nt, nt * seconds / max(dt, 1e-3))))
+
+
+def oracle_rows(r, f, a, n_rows=ORACLE_ROWS, seed=7):
+    """The FP64 oracle's product on a seeded subsample of targets (all
+    sources), timed: (rows, u_ref rows, seconds, threads)."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    rows = np.sort(np.random.default_rng(seed).choice(r.shape[0], min(n_rows, r.shape[0]),
+                                                       replace=False))
+    t0 = time.perf_counter()
+    ref = O.matvec(r, f, a, 1.0, True, targets=rows)
+    return rows, ref, time.perf_counter() - t0, O.num_threads()
+
+
+def compare_rows(u_rows, ref):
+    """Relative L2, max abs and max abs / max |ref| of u against the oracle."""
+    import numpy as np
+
+    d = u_rows - ref
+    return {"rows": int(ref.shape[0]),
+            "rel_l2_vs_oracle": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "max_abs_vs_oracle": float(np.abs(d).max()),
+            "max_abs_over_max_ref": float(np.abs(d).max() / np.abs(ref).max())}
 
 
 def run_reference(args):
@@ -266,6 +316,41 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def measured_peaks(ctx, device):
+    """FP32 and FP64 FMA rates measured on this GPU now (TFLOP/s), and its
+    SM count read from the device."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    return {"fp32_tflops": ctx.measure_fma_rate("fp32") / 1e12,
+            "fp64_tflops": ctx.measure_fma_rate("fp64") / 1e12, "sm_count": sms,
+            "how": "mb_measure_fma_rate: independent FMA chains (f32x2 for FP32) on every SM, "
+                   "best of 3 launches, CUDA events, this run"}
+
+
+def timed_matvec(ctx, r, f, a, prec, steps, warmup, out):
+    """Kernel time (ms, from the library's events on the launching stream)
+    and step time (ms, CUDA events around each call) of `steps` matvecs."""
+    import torch
+
+    for _ in range(warmup):
+        ctx.mobility_matvec(r, f, a, 1.0, True, prec, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx.profile_enable(True)
+    ctx.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.mobility_matvec(r, f, a, 1.0, True, prec, out=out)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    kms, launches, _ = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    return kms / max(1, launches), sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -296,6 +381,7 @@ def run_ours(args):
     u = torch.empty_like(r)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
     stream = torch.cuda.current_stream(device)
+    peaks = measured_peaks(ctx, device)
 
     def barrier():
         if dist is not None:
@@ -331,9 +417,9 @@ def run_ours(args):
     t_local = step_ms / 1e3
     pairs_local = float(n) * float(n) * args.steps
     value, t_max = whole_job_rate(dist, pairs_local, t_local, device)
-    pairs = pairs_local * world
     kernel_avg_s = pair_ms / 1e3 / max(1, pair_launches)
     achieved = FLOPS_PER_PAIR * float(n) * n / kernel_avg_s / 1e12
+    u_fp32 = u.cpu().numpy()
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     r_h = torch.from_numpy(r_np).pin_memory()
@@ -349,36 +435,84 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_value, _ = whole_job_rate(dist, pairs_local, e2e_s, device)
 
+    nominal = peaks["sm_count"] * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    rec = kernel_record() if args.prec == "fp32" and variant == 3 else None
+    if args.prec == "fp32":
+        roofline = {
+            "bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["fp32_tflops"],
+            "traffic": rec.get("bytes_per_launch_full_size") if rec else None,
+            "kernel": KERNEL_NAMES.get(variant, "pair_f32_kernel<wall>"),
+            "kernel_ms_avg": 1e3 * kernel_avg_s, "flops_per_pair": FLOPS_PER_PAIR,
+            "flops_basis": FLOPS_BASIS,
+            "peak_basis": "FP32 FMA rate measured in this run (" + peaks["how"] + "), "
+                          f"{peaks['sm_count']} SMs read from the device",
+            "peak_nominal": nominal, "frac_of_nominal": achieved / nominal,
+            "fma_pipe_active_frac": rec.get("fma_pipe_cycles_active") if rec else None,
+            "fma_pipe_basis": "sm__pipe_fma_cycles_active of the committed ncu capture of this "
+                              "kernel source (null if the source changed since)"}
+    else:
+        roofline = {
+            "bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"],
+            "unit": "TFLOP/s (FP64-equivalent)", "frac": achieved / peaks["fp64_tflops"],
+            "traffic": None, "kernel_ms_avg": 1e3 * kernel_avg_s,
+            "flops_per_pair": FLOPS_PER_PAIR, "flops_basis": FLOPS_BASIS,
+            "peak_basis": "FP64 FMA rate measured in this run"}
+
+    # ---- accuracy and the oracle's own rate on the workload's 4,096 targets
+    cpu = matvec_err = matvec_fp64 = matvec_df64 = None
+    ok = True
+    if rank == 0 and not args.no_cpu_baseline:
+        rows, ref, dt, threads = oracle_rows(r_np, f_np, a)
+        cpu = {"value": len(rows) * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(rows)} random targets x {n} sources ({len(rows) * n:.3g} pairs, "
+                         f"{dt:.1f} s)"}
+        matvec_err = compare_rows(u_fp32[rows], ref)
+        matvec_err.update({"precision": args.prec, "bound_rel_l2": MATVEC_TOL})
+        ok = matvec_err["rel_l2_vs_oracle"] <= MATVEC_TOL if args.prec == "fp32" else True
+        matvec_err["ok"] = bool(ok)
+        if not args.no_extras and args.prec == "fp32":
+            out = torch.empty_like(r)
+            for prec, steps in (("fp64", 3), ("df64", 5)):
+                kms, sms = timed_matvec(ctx, r, f, a, prec, steps, 1, out)
+                ach = FLOPS_PER_PAIR * float(n) * n / (kms / 1e3) / 1e12
+                line = {"pairs_per_s": float(n) * n / (sms / 1e3), "ms_per_matvec": sms,
+                        "kernel_ms_avg": kms, **compare_rows(out.cpu().numpy()[rows], ref),
+                        "roofline": {
+                            "bound": "alu", "achieved": ach, "peak": peaks["fp64_tflops"],
+                            "unit": "TFLOP/s (FP64-equivalent)",
+                            "frac": ach / peaks["fp64_tflops"],
+                            "flops_per_pair": FLOPS_PER_PAIR,
+                            "peak_basis": "FP64 FMA rate measured in this run"}}
+                if prec == "fp64":
+                    line["kernel"] = "pair_f64_kernel<wall> (FP64 pipe, every ordered pair)"
+                    matvec_fp64 = line
+                else:
+                    line["kernel"] = ("pair_df_kernel<wall> (symmetric, double-float arithmetic "
+                                      "on the FP32 pipe)")
+                    line["roofline"]["note"] = (
+                        "the double-float product runs on the FP32 pipe; frac is its "
+                        "FP64-equivalent rate over the FP64 pipe's measured peak, so above 1 "
+                        "it outruns any native FP64 kernel")
+                    line["roofline"]["fp32_peak"] = peaks["fp32_tflops"]
+                    drec = kernel_record("pair_df_kernel_traffic.json")
+                    line["roofline"]["fma_pipe_active_frac"] = (
+                        drec.get("fma_pipe_cycles_active") if drec else None)
+                    matvec_df64 = line
+
     # ---- mobility solves of the small suspension (latency distribution)
     solve = solve_fp64 = None
     if not args.no_solve and rank == 0:
         solve = bench_solves(ctx, args.solves)
         solve_fp64 = bench_solves(ctx, args.solves, "fp64")
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        pps, cores, nt, dt = oracle_pairs_per_s(r_np, f_np, a, args.cpu_seconds)
-        cpu = {"value": pps, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{nt} random targets x {n} sources ({nt * n:.3g} pairs, {dt:.1f} s)"}
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["monolayer"] = monolayer_line(ctx, "wall", peaks)
+        extras["batch"] = batch_line(ctx)
+        extras["serve"] = serve_line(ctx, args, sat_seconds=args.serve_sat_seconds or 20.0,
+                                     fracs=args.serve_fracs or "0.8")
 
-    if args.prec == "fp32":
-        roofline = {
-            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for_kernel(),
-            "kernel": KERNEL_NAMES.get(variant, "pair_f32_kernel<wall>"),
-            "kernel_ms_avg": 1e3 * kernel_avg_s, "flops_per_pair": FLOPS_PER_PAIR,
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
-            "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ))
-            if clocks else None}
-    else:
-        # profiling lines of the other precisions: the FP32 peak does not apply
-        roofline = {
-            "bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
-            "traffic": None,
-            "kernel": ("pair_df_kernel<wall> (symmetric double-float on the FP32 pipe)"
-                       if args.prec == "df64" else "pair_f64_kernel<wall> (FP64 pipe)"),
-            "kernel_ms_avg": 1e3 * kernel_avg_s, "flops_per_pair": FLOPS_PER_PAIR,
-            "note": "117 algorithmic flop/pair carried out in the higher precision"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -399,14 +533,19 @@ def run_ours(args):
             "gpu_launches": int(launches1 - launches0),
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "matvec_err": matvec_err,
+            "matvec_fp64": matvec_fp64,
+            "matvec_df64": matvec_df64,
+            "peaks_measured": peaks,
             "solve": solve,
             "solve_fp64": solve_fp64,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
-    return 0
+    return 0 if ok else 1
 
 
 def bench_solves(ctx, count, prec="mixed", precond="wall"):
@@ -482,30 +621,51 @@ def _dev_problem(s):
                 F=d(s.F), T=d(s.T))
 
 
-def bench_monolayer(args):
+def precond_factored(blob_counts, sm_count):
+    """Whether mb_precond_setup keeps the blocks in factored form: at least
+    as many bodies as SMs and blocks of more than 160 rows (up to 2,048)."""
+    n = 3 * max(blob_counts)
+    return len(blob_counts) >= sm_count and 160 < n <= 2048
+
+
+def setup_flops(blob_counts, factored=False):
+    """FP64 flops of the preconditioner setup (Section 2.2.2), counted per
+    body of n = 3 n_p rows as the algorithm is written: the Cholesky factor
+    M_p = L L^T (n^3 / 3), and for the explicit inverse also W = L^-1
+    (n^3 / 3) and M_p^-1 = W^T W (n^3 / 3)."""
+    chol = sum((3.0 * c) ** 3 / 3.0 for c in blob_counts)
+    return {"cholesky": chol, "total": chol if factored else 3.0 * chol,
+            "form": "factored (L, L^-1 K, N)" if factored else "explicit inverse"}
+
+
+def monolayer_line(ctx, precond="wall", peaks=None):
     """4,096 shells of 162 blobs (N = 663,552) above the wall, mixed precision
     (FP32 pair kernel in the Krylov iteration, double-float restart
     residuals) to a true relative residual of 1e-8."""
     import numpy as np
     import torch
 
-    import paper_1602_02170_gb300 as mb
     from oracle import oracle as O
-    from paper_1602_02170_gb300 import build as B
     from paper_1602_02170_gb300 import inputs as I
 
-    B.build()
-    ctx = mb.Context(0)
     s = I.config_monolayer(1)
     P = _dev_problem(s)
     # size-class autotuning of the FP32 kernel happens on this first matvec
     r = ctx.blob_positions(P["q"], P["theta"], P["blob_start"], P["rho"])
     ctx.mobility_matvec(r, torch.ones_like(r), s.a, 1.0, True, "fp32")
+    # the preconditioner setup alone (FP64), timed on the device
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    if precond == "wall":
+        ctx.precond_setup(r, P["q"], P["blob_start"], s.a, 1.0, True)
+    e1.record()
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1) if precond == "wall" else None
     t0 = time.perf_counter()
     U, W, lam, info = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"],
                                          P["T"], s.a, 1.0, True, tol=1e-8, maxit=300, restart=60,
-                                         prec="mixed", precond=args.precond)
+                                         prec="mixed", precond=precond)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     # fresh residual of the returned solution with one double-float product (untimed)
@@ -522,12 +682,73 @@ def bench_monolayer(args):
     line = {"metric": "mobility solves/s", "workload": "monolayer: 4096 x 162-blob shells, "
             "N=663552, a=0.12, 200x200 patch, z in [1.2,1.6]", "value": 1.0 / dt,
             "unit": "solves/s", "seconds": dt, "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)",
-            "precond": args.precond, "precond_bytes": ctx.workspace_bytes(),
+            "precond": precond, "precond_bytes": ctx.workspace_bytes(),
             "info": info, "pairs_per_matvec": float(s.n_blobs) ** 2,
             "fresh_df64_rel_residual": fresh / bnorm,
             "oracle_sampled_residual_rows_max_over_bnorm": float(np.abs(res).max() / bnorm),
             "oracle_rows": int(len(rows)), "n_gpus": 1}
-    print(json.dumps(line), flush=True)
+    if setup_ms is not None:
+        counts = np.diff(s.blob_start)
+        fl = setup_flops(counts, precond_factored(counts, peaks["sm_count"] if peaks else 152))
+        st = {"ms": setup_ms, "fp64_flops": fl["total"], "cholesky_flops": fl["cholesky"],
+              "form": fl["form"], "achieved_tflops": fl["total"] / (setup_ms / 1e3) / 1e12,
+              "what": "mb_precond_setup alone: assembly, Cholesky with L^-1 K, the Schur "
+                      "complement (and for the explicit form L^-1 and M^-1) of every body, "
+                      "CUDA events"}
+        if peaks:
+            st["fp64_peak_tflops"] = peaks["fp64_tflops"]
+            st["frac"] = st["achieved_tflops"] / peaks["fp64_tflops"]
+        line["precond_setup"] = st
+    return line
+
+
+def bench_monolayer(args):
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+
+    B.build()
+    ctx = mb.Context(0)
+    peaks = measured_peaks(ctx, 0)
+    print(json.dumps(monolayer_line(ctx, args.precond, peaks)), flush=True)
+    ctx.close()
+    return 0
+
+
+def bench_setup(args):
+    """The monolayer's preconditioner setup alone, three times (the command
+    the setup kernels' launch list and captures are taken from)."""
+    import numpy as np
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+    from paper_1602_02170_gb300 import inputs as I
+
+    B.build()
+    ctx = mb.Context(0)
+    peaks = measured_peaks(ctx, 0)
+    s = I.config_monolayer(1)
+    P = _dev_problem(s)
+    r = ctx.blob_positions(P["q"], P["theta"], P["blob_start"], P["rho"])
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.precond_setup(r, P["q"], P["blob_start"], s.a, 1.0, True)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    counts = np.diff(s.blob_start)
+    fl = setup_flops(counts, precond_factored(counts, peaks["sm_count"]))
+    ms = min(times)
+    print(json.dumps({"metric": "preconditioner setup ms", "workload": "monolayer blocks, "
+                      "4096 x 486 rows, wall", "ms": times, "form": fl["form"],
+                      "fp64_flops": fl["total"],
+                      "achieved_tflops": fl["total"] / (ms / 1e3) / 1e12,
+                      "fp64_peak_tflops": peaks["fp64_tflops"],
+                      "frac": fl["total"] / (ms / 1e3) / 1e12 / peaks["fp64_tflops"],
+                      "n_gpus": 1}), flush=True)
     ctx.close()
     return 0
 
@@ -674,31 +895,20 @@ def bench_eval(args):
     return 0
 
 
-def bench_batch(args):
+def batch_line(ctx, dist=None, rank=0, world=1, local=0):
     """256 independent mixed suspensions (42-blob shells and 15-blob
     boomerangs, log-uniform 8..2048 bodies) solved together, mixed precision
     to 1e-8; compared on a random subset with the plain FP64 path solving one
     problem at a time, at the same tolerance.  Under torchrun the problems
     are split into contiguous shares, one per rank (no collective on the data
-    path); the rate is all problems over the slowest rank's time."""
+    path); the rate is all problems over the slowest rank's time.  Returns
+    the line on rank 0 (None elsewhere)."""
     import numpy as np
     import torch
 
-    import paper_1602_02170_gb300 as mb
     from oracle import oracle as O
-    from paper_1602_02170_gb300 import build as B
     from paper_1602_02170_gb300 import inputs as I
 
-    rank, world, local = dist_info()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    B.build()
-    ctx = mb.Context(local)
     t0 = time.perf_counter()
     susp = I.config_batched(1)
     gen_s = time.perf_counter() - t0
@@ -718,9 +928,7 @@ def bench_batch(args):
     res = dict(zip(mine, res_list))
     iters = [r[3]["iters"] for r in res_list]
     if rank != 0:
-        dist.barrier()
-        ctx.close()
-        return 0
+        return None
     rng = np.random.default_rng(5)
     sub = sorted(rng.choice(mine, min(8, len(mine)), replace=False).tolist())
     t0 = time.perf_counter()
@@ -736,7 +944,9 @@ def bench_batch(args):
                                            prec="fp64"))
     torch.cuda.synchronize()
     t_sub_fp64 = time.perf_counter() - t0
-    diff = max(float(((x[0] - y[0]).norm() / y[0].norm()).item()) for x, y in zip(sub_batch, sub_fp64))
+    rel = lambda x, y: float(((x - y).norm() / y.norm()).item())
+    diff_full = max(rel(res[k][0], y[0]) for k, y in zip(sub, sub_fp64))
+    diff_sub = max(rel(x[0], y[0]) for x, y in zip(sub_batch, sub_fp64))
     oracle_err = []
     for k in sub:
         s = susp[k]
@@ -745,117 +955,241 @@ def bench_batch(args):
             Ur, _, _ = O.solve_saddle(rr, s.q, s.blob_start, s.F, s.T, a, 1.0, True)
             oracle_err.append(float(np.linalg.norm(res[k][0].cpu().numpy() - Ur) / np.linalg.norm(Ur)))
     pairs = float(sum(s.n_blobs ** 2 for s in susp))
-    line = {"metric": "mobility solves/s", "workload": "batched: 256 mixed suspensions "
+    return {"metric": "mobility solves/s", "workload": "batched: 256 mixed suspensions "
             "(42-blob shells / 15-blob boomerangs, a=0.1625), bodies log-uniform 8..2048, "
             "z in [1.2,3]", "value": rate, "unit": "solves/s", "seconds": t_batch,
             "tol": 1e-8, "prec": "mixed (fp32 + df64 residual), one batched launch per kernel",
             "n_blobs_total": int(sum(s.n_blobs for s in susp)),
             "n_bodies_total": int(sum(s.n_bodies for s in susp)),
             "pairs_per_batched_matvec": pairs, "iters_median_rank0": float(np.median(iters)),
-            "iters_max_rank0": int(max(iters)), "generation_s": gen_s,
+            "iters_max_rank0": int(max(iters)), "converged_all": all(
+                r[3]["converged"] == 1 for r in res_list), "generation_s": gen_s,
             "subset": {"problems": sub, "batched_mixed_solves_per_s": len(sub) / t_sub_batch,
                        "fp64_one_at_a_time_solves_per_s": len(sub) / t_sub_fp64,
-                       "max_rel_diff_U_batched_vs_fp64": diff,
+                       "max_rel_diff_U_full_batch_vs_fp64": diff_full,
+                       "max_rel_diff_U_subset_batch_vs_fp64": diff_sub,
                        "oracle_rel_err_U_small_problems": oracle_err},
             "n_gpus": world, "scaling": "strong",
             "parallelism": "problems split across ranks" if world > 1 else "single GPU"}
-    print(json.dumps(line), flush=True)
+
+
+def bench_batch(args):
+    import torch
+
+    import paper_1602_02170_gb300 as mb
+    from paper_1602_02170_gb300 import build as B
+
+    rank, world, local = dist_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    B.build()
+    ctx = mb.Context(local)
+    line = batch_line(ctx, dist, rank, world, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
     ctx.close()
     return 0
 
 
-def bench_serve(args):
-    """Poisson stream of mobility solves (mean args.rate requests/s) with blob
-    counts log-uniform in [100, 2e5] (mixed shells and boomerangs), served
-    by the continuous-batching engine; then a sweep at 0.5x and 0.8x of the
-    measured capacity so that p99 latency is meaningful."""
+def _gen_requests(seeds):
+    """Serving requests (one seeded mixed suspension each), generated on the
+    host cores by a pool of spawned processes."""
+    import multiprocessing as mp
+
+    from paper_1602_02170_gb300 import inputs as I
+
+    seeds = [int(x) for x in seeds]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 2))
+    if len(seeds) < 16 or workers == 1:
+        return [I.config_serving_request(x) for x in seeds]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(I.config_serving_request, seeds, chunksize=8)
+
+
+def _serve_run(ctx, a, probs, arrivals, window, drain, tick_pairs, keep_results=False):
+    """Serve `probs` arriving at `arrivals` (seconds) on a fresh server; each
+    request's data goes to the device when it arrives.  Latency runs from the
+    scheduled arrival to the tick that sees the request done."""
+    import numpy as np
+
+    import paper_1602_02170_gb300 as mb
+
+    srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
+                    max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=512,
+                    tick_pairs=tick_pairs)
+    inflight, lat, done_blobs, results, work, its = {}, [], [], {}, 0.0, []
+    nsub = failed = 0
+    queue_at_window = None
+    max_outstanding = 0
+    start = time.perf_counter()
+    ticks = 0
+    while True:
+        now = time.perf_counter() - start
+        while nsub < len(arrivals) and arrivals[nsub] <= now:
+            P = _dev_problem(probs[nsub])
+            t, outs = srv.submit(P)
+            inflight[t] = (arrivals[nsub], nsub, outs)
+            nsub += 1
+        nr, nq = srv.step()
+        ticks += 1
+        now = time.perf_counter() - start
+        for t in srv.finished():
+            st_, info, status = srv.poll(t)
+            arr, k, outs = inflight.pop(t)
+            if st_ == mb.Server.DONE and status == "MB_OK":
+                its.append(info["iters"])
+                lat.append(now - arr)
+                done_blobs.append(probs[k].n_blobs)
+                work += request_work(probs[k].n_blobs, info["iters"])
+                if keep_results:
+                    results[k] = (outs[0].clone(), outs[1].clone())
+            else:
+                failed += 1
+        max_outstanding = max(max_outstanding, len(inflight))
+        if queue_at_window is None and now >= window:
+            queue_at_window = len(inflight) + (len(arrivals) - nsub)
+        if now >= window and (not drain or (not inflight and nsub == len(arrivals))):
+            break
+        if nr == 0 and nq == 0 and nsub < len(arrivals):
+            time.sleep(max(0.0, min(arrivals[nsub] - now, 0.01)))
+    wall = time.perf_counter() - start
+    srv.close()
+    lat_ms = sorted(1e3 * x for x in lat)
+    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(math.ceil(q * len(lat_ms))) - 1)] if lat_ms else None
+    return {"window_s": window, "wall_s": wall, "offered": int(len(arrivals)),
+            "offered_per_s": len(arrivals) / window if window > 0 else None, "served": len(lat),
+            "served_per_s": len(lat) / wall, "failed": failed, "p50_ms": pct(0.5),
+            "p99_ms": pct(0.99), "outstanding_at_window_end": queue_at_window,
+            "max_outstanding": max_outstanding, "unserved_at_end": int(len(arrivals) - len(lat)),
+            "ticks": ticks, "mean_served_blobs": float(np.mean(done_blobs)) if done_blobs else None,
+            "served_work_pairs": work,
+            "iters_median": float(np.median(its)) if its else None,
+            "mean_offered_blobs": float(np.mean([p.n_blobs for p in probs])) if probs else None,
+            "_results": results}
+
+
+# One mixed-precision request costs, in pair evaluations, N^2 per FP32 Krylov
+# iteration plus the double-float product of its first refinement residual,
+# which takes about 8 FP32 matvecs on this GPU (58.5 vs 7.45 ms at N = 65,536).
+DF64_MATVEC_EQUIV = 8.0
+
+
+def request_work(n_blobs, iters):
+    return float(n_blobs) ** 2 * (iters + DF64_MATVEC_EQUIV)
+
+
+def serve_line(ctx, args, sat_seconds, fracs):
+    """The serving stream (Poisson arrivals, blob counts log-uniform in
+    [100, 2e5], mixed shells and boomerangs, one freshly seeded problem per
+    request): saturated at args.rate req/s over `sat_seconds`; the capacity
+    measured by serving 64 requests submitted at once; then drained runs at
+    fractions of that capacity over args.serve_seconds each, with p50/p99
+    latency, served vs offered and the queue at the end of the window; and
+    sampled requests of the last run solved alone against their served
+    result (and the oracle's direct solve for a small one)."""
     import numpy as np
     import torch
 
+    from oracle import oracle as O
+
+    out = {"metric": "mobility solves/s and p99 latency",
+           "workload": "serving: Poisson arrivals, blobs log-uniform 100..2e5 (mixed 42-blob "
+                       "shells / 15-blob boomerangs, a=0.1625), one seeded problem per request",
+           "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)", "tick_pairs": args.tick_pairs,
+           "n_gpus": 1}
+    # saturated: the offered load of the workload
+    rng = np.random.default_rng(1)
+    arr = np.cumsum(rng.exponential(1.0 / args.rate, int(args.rate * sat_seconds * 2) + 16))
+    arr = arr[arr < sat_seconds]
+    t0 = time.perf_counter()
+    probs = _gen_requests(10_000_000 + np.arange(len(arr)))
+    gen_s = time.perf_counter() - t0
+    a = probs[0].a
+    sat = _serve_run(ctx, a, probs, arr, sat_seconds, False, args.tick_pairs)
+    sat.pop("_results")
+    sat["rate_offered"] = args.rate
+    sat["generation_s"] = gen_s
+    out["saturated"] = sat
+    del probs
+    # capacity: the engine's rate of pair work with 64 requests submitted at
+    # once and served to completion, over the mean work of a request of the
+    # offered mix.  Work per request grows like N^2 over a heavy-tailed size
+    # distribution, so a request count from a small sample would misjudge it.
+    cap_probs = _gen_requests(20_000_000 + np.arange(64))
+    cap = _serve_run(ctx, a, cap_probs, np.zeros(64), 0.0, True, args.tick_pairs)
+    cap.pop("_results")
+    work_rate = cap["served_work_pairs"] / cap["wall_s"]
+    mix = _gen_requests(40_000_000 + np.arange(512))
+    iters_typ = cap["iters_median"] or 15.0
+    mean_work = float(np.mean([request_work(p.n_blobs, iters_typ) for p in mix]))
+    capacity = work_rate / mean_work
+    del mix
+    out["capacity"] = {"solves_per_s": capacity, "pair_work_per_s": work_rate,
+                       "mean_work_pairs_per_request": mean_work, "requests": 64,
+                       "wall_s": cap["wall_s"], "iters_median": iters_typ,
+                       "how": "pair work per second (N^2 per Krylov iteration plus 8 N^2 for the "
+                              "double-float residual) of 64 fresh requests submitted at once and "
+                              "served to completion, over the mean work of 512 requests drawn "
+                              "from the offered distribution"}
+    rates = ([float(x) for x in args.rates.split(",")] if args.rates
+             else [float(x) * capacity for x in fracs.split(",")])
+    subs = []
+    for i, rate in enumerate(rates):
+        rng = np.random.default_rng(100 + i)
+        arr = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.serve_seconds * 2) + 16))
+        arr = arr[arr < args.serve_seconds]
+        probs = _gen_requests((30 + i) * 1_000_000 + np.arange(len(arr)))
+        last = i == len(rates) - 1
+        run = _serve_run(ctx, a, probs, arr, args.serve_seconds, True, args.tick_pairs,
+                         keep_results=last)
+        results = run.pop("_results")
+        run["rate_offered"] = rate
+        if not args.rates:
+            run["fraction_of_capacity"] = rate / capacity
+        if last and results:
+            # sampled requests alone vs in the mix: smallest, median and largest served
+            order = sorted(results, key=lambda k: probs[k].n_blobs)
+            picks = sorted({order[0], order[len(order) // 2], order[-1]})
+            worst = 0.0
+            for k in picks:
+                P = _dev_problem(probs[k])
+                U = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"],
+                                       P["T"], a, 1.0, True, tol=1e-8, maxit=300, restart=30,
+                                       prec="mixed")[0]
+                worst = max(worst, float(((results[k][0] - U).norm() / U.norm()).item()))
+            run["alone_vs_served_max_rel_diff_U"] = worst
+            run["alone_vs_served_requests"] = [int(probs[k].n_blobs) for k in picks]
+            s = probs[order[0]]
+            if s.n_blobs <= 1500:
+                rr = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+                Ur, _, _ = O.solve_saddle(rr, s.q, s.blob_start, s.F, s.T, a, 1.0, True)
+                run["oracle_rel_err_U_smallest"] = float(
+                    np.linalg.norm(results[order[0]][0].cpu().numpy() - Ur) / np.linalg.norm(Ur))
+        subs.append(run)
+        del probs
+    torch.cuda.synchronize()
+    out["sub_saturation"] = subs
+    out["value"] = subs[-1]["served_per_s"] if subs else sat["served_per_s"]
+    out["p99_ms"] = subs[-1]["p99_ms"] if subs else sat["p99_ms"]
+    out["unit"] = "solves/s"
+    return out
+
+
+def bench_serve(args):
     import paper_1602_02170_gb300 as mb
     from paper_1602_02170_gb300 import build as B
-    from paper_1602_02170_gb300 import inputs as I
 
     B.build()
     ctx = mb.Context(0)
-    t0 = time.perf_counter()
-    pool = [I.config_serving_request(1000 + k) for k in range(args.pool)]
-    gen_s = time.perf_counter() - t0
-    a = pool[0].a
-    dpool = [_dev_problem(s) for s in pool]
-    sizes = [s.n_blobs for s in pool]
-
-    def run(rate, seconds, seed, drain):
-        srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
-                        max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=512,
-                        tick_pairs=args.tick_pairs)
-        rng = np.random.default_rng(seed)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 2) + 16))
-        arrivals = arrivals[arrivals < seconds]
-        picks = rng.integers(0, len(pool), len(arrivals))
-        inflight, lat, sizes_done = {}, [], []
-        nsub = 0
-        start = time.perf_counter()
-        ticks = 0
-        while True:
-            now = time.perf_counter() - start
-            while nsub < len(arrivals) and arrivals[nsub] <= now:
-                t, outs = srv.submit(dpool[picks[nsub]])
-                inflight[t] = (arrivals[nsub], picks[nsub], outs)
-                nsub += 1
-            nr, nq = srv.step()
-            ticks += 1
-            now = time.perf_counter() - start
-            for t in list(inflight):
-                st_, info, status = srv.poll(t)
-                if st_ in (mb.Server.DONE, mb.Server.FAILED):
-                    arr, k, _ = inflight.pop(t)
-                    if st_ == mb.Server.DONE and status == "MB_OK":
-                        lat.append(now - arr)
-                        sizes_done.append(sizes[k])
-            if now >= seconds and (not drain or (nr == 0 and nq == 0 and nsub == len(arrivals))):
-                break
-            if nr == 0 and nq == 0 and nsub < len(arrivals):
-                time.sleep(max(0.0, min(arrivals[nsub] - now, 0.01)))
-        wall = time.perf_counter() - start
-        srv.close()
-        lat_ms = sorted(1e3 * x for x in lat)
-        pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(math.ceil(q * len(lat_ms))) - 1)] if lat_ms else None
-        return {"rate_offered": rate, "window_s": seconds, "wall_s": wall, "offered": int(len(arrivals)),
-                "served": len(lat), "served_per_s": len(lat) / wall, "p50_ms": pct(0.5),
-                "p99_ms": pct(0.99), "unserved_at_end": int(len(arrivals) - len(lat)),
-                "ticks": ticks, "mean_served_blobs": float(np.mean(sizes_done)) if sizes_done else None}
-
-    # the same request alone vs in the mix
-    check = []
-    for k in np.argsort(sizes)[:3]:
-        P = dpool[k]
-        Ua = ctx.solve_mobility(P["q"], P["theta"], P["blob_start"], P["rho"], P["F"], P["T"], a,
-                                1.0, True, tol=1e-8, prec="mixed")[0]
-        check.append((k, Ua))
-    sat = run(args.rate, args.serve_seconds, 1, drain=False)
-    cap = max(sat["served_per_s"], 1e-3)
-    rates = ([float(x) for x in args.rates.split(",")] if args.rates else [0.5 * cap, 0.8 * cap])
-    sub = [run(rate, max(10.0, args.serve_seconds * 0.6), 2 + i, drain=True)
-           for i, rate in enumerate(rates)]
-    # mix check: serve the three small requests together with a large one
-    srv = mb.Server(ctx, a, tol=1e-8, prec="mixed", restart=30, max_blobs=4_000_000,
-                    max_bodies=150_000, max_precond_bytes=12 << 30, max_requests=64)
-    big = int(np.argmax(sizes))
-    tickets = [srv.submit(dpool[big])[0]] + [srv.submit(dpool[k]) for k, _ in check]
-    srv.run_until_idle()
-    mix_diff = max(float(((t[1][0] - Ua).norm() / Ua.norm()).item())
-                   for t, (k, Ua) in zip(tickets[1:], check))
-    srv.close()
-    line = {"metric": "mobility solves/s and p99 latency", "workload": "serving: Poisson "
-            f"{args.rate:g} req/s, blobs log-uniform 100..2e5 (mixed shells/boomerangs), "
-            f"pool of {len(pool)} seeded requests", "value": sat["served_per_s"], "unit": "solves/s",
-            "tol": 1e-8, "prec": "mixed (fp32 + df64 residual)", "tick_pairs": args.tick_pairs,
-            "saturated": sat,
-            "sub_saturation": sub, "same_alone_and_in_mix_max_rel_diff_U": mix_diff,
-            "pool_generation_s": gen_s, "n_gpus": 1}
+    line = serve_line(ctx, args, sat_seconds=args.serve_sat_seconds or 60.0,
+                      fracs=args.serve_fracs or "0.5,0.8")
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -879,6 +1213,8 @@ def main():
         return bench_batch(args)
     if args.workload == "serve":
         return bench_serve(args)
+    if args.workload == "setup":
+        return bench_setup(args)
     return run_ours(args)
 
 

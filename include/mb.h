@@ -142,6 +142,20 @@ mb_status mb_profile_read(mb_context *ctx, double *pair_kernel_ms, int64_t *pair
                           int64_t *kernel_launches, int reset);
 
 /*
+ * Measured FMA rate of the context's device, the roofline denominator of the
+ * arithmetic-bound kernels (the pair kernel of Section 5's direct summation
+ * and the FP64 factorisations of Section 2.2.2).  prec = MB_FP32_KAHAN
+ * measures the FP32 pipe (paired f32x2 FMAs), MB_FP64 the FP64 pipe.  One
+ * warm-up and three timed launches of a kernel of independent FMA chains
+ * that fills every SM (no memory traffic in its loop); *flops_per_s receives
+ * 2 x FMAs / duration of the fastest launch, at the clocks of the moment.
+ * Takes about 0.15 s; synchronises the stream.  MB_EINVAL for another
+ * precision or a null output.
+ */
+mb_status mb_measure_fma_rate(mb_context *ctx, mb_precision prec, double *flops_per_s,
+                              void *stream);
+
+/*
  * u = M(r) f — product of the blob-blob mobility with blob forces.
  * Section 2.1.1: M_ij is the RPY tensor of Eq. RPYTensor (with its overlap
  * regularisation for r_ij <= 2a; M_ii = I/(6 pi eta a)) plus, if wall != 0,
@@ -216,8 +230,10 @@ mb_status mb_context_pair_variant(const mb_context *ctx, int64_t n, int wall, in
  * the GPU (different streams, or host threads) race on it and must be
  * serialised by the caller.
  *
- * r, f, u: N x 3 device pointers (host pointers are MB_EINVAL); the result
- * is the same product as mb_mobility_matvec (up to FP32 rounding order).
+ * r, f, u: N x 3 device pointers on the device current on the calling
+ * thread (host pointers and memory of another GPU are MB_EINVAL); the
+ * result is the same product as mb_mobility_matvec (up to FP32 rounding
+ * order).
  * Errors are reported through mb_last_error(NULL).
  */
 #define MB_NOALLOC_MAX_BLOBS 65536
@@ -441,9 +457,13 @@ mb_status mb_solve_batch(mb_context *ctx, int n_problems, const mb_problem *prob
  * charged to the context's HBM budget: blob and body slots, preconditioner
  * storage and the Krylov basis of restart length params->restart.  Requests
  * (mb_problem descriptors, device pointers that must stay valid until the
- * request completes) are queued by mb_server_submit and admitted first-come
- * first-served when their blobs, bodies and preconditioner blocks fit in the
- * arena (admission by HBM footprint) and a request slot is free.  Each
+ * request completes) are queued by mb_server_submit and admitted when their
+ * blobs, bodies and preconditioner blocks fit in the arena (admission by HBM
+ * footprint) and a request slot is free.  The queue is scanned in arrival
+ * order and every request that fits is admitted, so small requests are not
+ * held up behind a large one waiting for room; a request that later ones
+ * have overtaken limits->max_bypass times stops the scan until it is
+ * admitted itself, which bounds its wait (aging).  Each
  * mb_server_step is one scheduling tick: it retires finished requests
  * (writing U, Omega and lambda to the request's arrays and freeing its
  * ranges), admits queued ones (blob build, preconditioner factorisation,
@@ -481,6 +501,10 @@ typedef struct {
                                    requests sharing the ticks are not held up
                                    by them; 0 = 1e9 (about 2 ms of the FP32
                                    kernel), < 0 = no limit */
+    int max_bypass;             /* admissions of later requests a queued
+                                   request may be overtaken by before the
+                                   scan stops at it: 0 = 64, < 0 = strict
+                                   first-come first-served */
 } mb_server_limits;
 
 mb_status mb_server_create(mb_context *ctx, const mb_params *params,
@@ -490,6 +514,12 @@ mb_status mb_server_submit(mb_server *server, const mb_problem *problem, int64_t
 mb_status mb_server_step(mb_server *server, void *stream, int *n_running, int *n_queued);
 mb_status mb_server_poll(mb_server *server, int64_t ticket, int *state, mb_info *info,
                          mb_status *result);
+
+/* Tickets of the requests that finished (done or failed) since the last
+ * call, oldest first: up to max_tickets of them are written to `tickets`
+ * (host array) and *count receives how many; the rest stay for the next
+ * call.  Lets a caller with many requests in flight poll only those. */
+mb_status mb_server_finished(mb_server *server, int64_t *tickets, int max_tickets, int *count);
 
 #ifdef __cplusplus
 }

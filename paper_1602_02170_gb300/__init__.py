@@ -50,6 +50,7 @@ EXPORTED_SYMBOLS = [
     "mb_context_pair_variant",
     "mb_profile_enable",
     "mb_profile_read",
+    "mb_measure_fma_rate",
     "mb_mobility_matvec",
     "mb_mobility_matvec_noalloc",
     "mb_blob_positions",
@@ -70,6 +71,7 @@ EXPORTED_SYMBOLS = [
     "mb_server_submit",
     "mb_server_step",
     "mb_server_poll",
+    "mb_server_finished",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +135,7 @@ class ServerLimits(ctypes.Structure):
         ("max_precond_bytes", ctypes.c_int64),
         ("max_requests", ctypes.c_int),
         ("tick_pairs", ctypes.c_double),
+        ("max_bypass", ctypes.c_int),
     ]
 
 
@@ -179,6 +182,7 @@ def load_library():
     L.mb_profile_enable.argtypes = [vp, ci]
     L.mb_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64), ci]
+    L.mb_measure_fma_rate.argtypes = [vp, ci, ctypes.POINTER(dbl), vp]
     L.mb_mobility_matvec.argtypes = [vp, vp, vp, i64, dbl, dbl, ci, ci, vp, vp]
     L.mb_mobility_matvec_noalloc.argtypes = [vp, vp, i64, dbl, dbl, ci, vp, vp]
     L.mb_blob_positions.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
@@ -211,6 +215,7 @@ def load_library():
     L.mb_server_step.argtypes = [vp, vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
     L.mb_server_poll.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(Info),
                                  ctypes.POINTER(ci)]
+    L.mb_server_finished.argtypes = [vp, ctypes.POINTER(i64), ci, ctypes.POINTER(ci)]
     for name in EXPORTED_SYMBOLS:
         if name not in ("mb_status_string", "mb_last_error", "mb_context_workspace_bytes"):
             getattr(L, name).restype = ci  # mb_status
@@ -242,16 +247,21 @@ def mobility_matvec_noalloc(r, f, a, eta=1.0, wall=True, out=None, stream=None):
 
     L = load_library()
     n = int(r.shape[0])
+    if not r.is_cuda:
+        raise ValueError("r must be a CUDA tensor")
     if out is None:
         out = torch.empty((n, 3), dtype=torch.float64, device=r.device)
     for t in (r, f, out):
         if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (n, 3):
             raise ValueError("r, f, out must be contiguous float64 (N, 3)")
-    if stream is None:
-        stream = torch.cuda.current_stream(r.device)
-    st = L.mb_mobility_matvec_noalloc(_ptr(r), _ptr(f), n, float(a), float(eta),
-                                      int(bool(wall)), _ptr(out),
-                                      ctypes.c_void_p(stream.cuda_stream))
+        if t.device != r.device:
+            raise ValueError("r, f and out must be on the same CUDA device")
+    with torch.cuda.device(r.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(r.device)
+        st = L.mb_mobility_matvec_noalloc(_ptr(r), _ptr(f), n, float(a), float(eta),
+                                          int(bool(wall)), _ptr(out),
+                                          ctypes.c_void_p(stream.cuda_stream))
     if st != 0:
         raise MBError(st, L.mb_last_error(None).decode())
     return out
@@ -325,6 +335,14 @@ class Context:
         self._check(self.L.mb_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(pl),
                                            ctypes.byref(kl), int(bool(reset))))
         return ms.value, pl.value, kl.value
+
+    def measure_fma_rate(self, prec="fp32", stream=None) -> float:
+        """Measured FMA rate of the device in flop/s (2 x FMAs per second):
+        prec "fp32" for the FP32 pipe, "fp64" for the FP64 pipe."""
+        v = ctypes.c_double()
+        self._check(self.L.mb_measure_fma_rate(self.handle, _prec(prec), ctypes.byref(v),
+                                               self._stream(stream)))
+        return v.value
 
     def _dev(self, t, shape=None, dtype=None):
         torch = self._torch
@@ -570,20 +588,24 @@ class Server:
     1 running, 2 done, 3 failed.  Results land in the tensors returned by
     submit(); keep the inputs alive until the ticket is done.  tick_pairs
     caps the pair evaluations one request's FP32 Arnoldi matvec takes per
-    tick (0: 1e9, < 0: no cap); larger matvecs are spread over ticks."""
+    tick (0: 1e9, < 0: no cap); larger matvecs are spread over ticks.
+    Admission takes every queued request that fits, in arrival order; one
+    overtaken max_bypass times (0: 64, < 0: strict first come, first served)
+    stops later ones until it is admitted.  finished() lists the tickets
+    done since its last call."""
 
     QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
 
     def __init__(self, ctx, a, eta=1.0, wall=True, tol=1e-10, maxit=200, restart=60,
                  prec="mixed", max_blobs=1 << 20, max_bodies=1 << 16,
-                 max_precond_bytes=4 << 30, max_requests=256, tick_pairs=0.0):
+                 max_precond_bytes=4 << 30, max_requests=256, tick_pairs=0.0, max_bypass=0):
         self.ctx = ctx
         self.L = ctx.L
         self._torch = ctx._torch
         p = Params(float(a), float(eta), int(bool(wall)), float(tol), int(maxit), int(restart),
                    _prec(prec))
         lim = ServerLimits(int(max_blobs), int(max_bodies), int(max_precond_bytes),
-                           int(max_requests), float(tick_pairs))
+                           int(max_requests), float(tick_pairs), int(max_bypass))
         h = ctypes.c_void_p()
         self._check(self.L.mb_server_create(ctx.handle, ctypes.byref(p), ctypes.byref(lim),
                                             ctypes.byref(h)))
@@ -638,6 +660,17 @@ class Server:
         if st.value in (self.DONE, self.FAILED):
             self._keep.pop(int(ticket), None)
         return st.value, info.as_dict(), STATUS.get(res.value, str(res.value))
+
+    def finished(self, max_tickets=4096):
+        """Tickets of the requests finished since the last call (oldest first)."""
+        buf = (ctypes.c_int64 * max_tickets)()
+        n = ctypes.c_int()
+        out = []
+        while True:
+            self._check(self.L.mb_server_finished(self.handle, buf, max_tickets, ctypes.byref(n)))
+            out.extend(buf[k] for k in range(n.value))
+            if n.value < max_tickets:
+                return out
 
     def run_until_idle(self, stream=None, max_ticks=1_000_000):
         for _ in range(max_ticks):

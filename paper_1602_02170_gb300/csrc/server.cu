@@ -4,7 +4,11 @@
 // preconditioner ranges plus Krylov vectors laid out as
 //     x = [lambda of every blob slot (3 N_cap) | (U, Omega) of every body slot (6 B_cap)].
 // A request is admitted when contiguous blob, body and preconditioner ranges
-// fit (first fit), i.e. by its HBM footprint; its positions, right-hand side,
+// fit (first fit), i.e. by its HBM footprint.  The queue is scanned in
+// arrival order and every request that fits is admitted, so a small request
+// does not wait behind a large one that does not fit yet; a queued request
+// that later ones have overtaken max_bypass times stops the scan until it is
+// admitted itself (aging), which bounds its wait.  Its positions, right-hand side,
 // factorised preconditioner blocks and Krylov state then stay on the device
 // until it completes.  Each scheduling tick
 //   1. retires finished requests (results scattered to the caller's arrays,
@@ -763,6 +767,13 @@ struct RangeAlloc {
         }
         return -1;
     }
+    // longest free range (0 if none)
+    int64_t largest() const
+    {
+        int64_t m = 0;
+        for (const auto &kv : free_) m = std::max(m, kv.second);
+        return m;
+    }
     void release(int64_t s, int64_t len)
     {
         if (len <= 0) return;
@@ -808,6 +819,7 @@ struct Engine {
     std::vector<int> free_slots;
     bool mixed = false;
     double tick_pairs = -1;  // per-request pair budget of one tick's Arnoldi matvec (< 0: none)
+    int max_bypass = 64;     // admissions that may overtake a queued request (< 0: none)
     int np_variant = 1;     // FP32 tile shape: 1, 2 = packed with 2 or 4 targets per
                             // thread, 3 = symmetric (autotuned)
     std::map<int, int> tuned_by_class;  // autotuned tile shape per size class of a tick's pairs
@@ -826,8 +838,10 @@ struct Engine {
         mb_info info{};
         int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
         mb_status err = MB_OK;
+        int bypassed = 0;  // later requests admitted while this one waited
     };
     std::deque<Req *> queue;
+    std::deque<int64_t> finished;            // tickets retired since the last mb_server_finished
     std::vector<Req *> running;              // by slot
     std::map<int64_t, Req *> all;            // ticket -> request
     int64_t next_ticket = 1;
@@ -844,11 +858,13 @@ struct Engine {
     }
 
     mb_status create(mb_context *c, const mb_params *p, int64_t max_blobs, int64_t max_bodies,
-                     int64_t max_pc_doubles, int max_requests, double tick_pair_budget = -1)
+                     int64_t max_pc_doubles, int max_requests, double tick_pair_budget = -1,
+                     int bypass_limit = 64)
     {
         ctx = c;
         prm = *p;
         tick_pairs = tick_pair_budget;
+        max_bypass = bypass_limit;
         m = std::max(1, std::min(p->restart, 500));
         L = SL{m};
         n_cap = max_blobs;
@@ -1167,23 +1183,45 @@ mb_status Engine::step(cudaStream_t s, int *n_running, int *n_queued)
     const mb_precision inner = inner_precision(prm.prec);
     const mb_precision outer = outer_precision(prm.prec);
 
-    // ---- 1. admission (first come, first served while ranges fit)
+    // ---- 1. admission: scan the queue in arrival order and admit every
+    // request whose ranges fit.  Requests that do not fit stay queued in
+    // order; each admission behind one counts as a bypass, and a request
+    // bypassed max_bypass times ends the scan (nothing behind it is admitted
+    // until it is), so its wait is bounded by the requests ahead of it
+    // finishing.  max_bypass < 0 gives strict first-come first-served.
     std::vector<Req *> admitted;
-    while (!queue.empty() && !free_slots.empty()) {
-        Req *rq = queue.front();
-        const int64_t bo = blobs.alloc(rq->prob.n_blobs);
-        if (bo < 0) break;
-        const int64_t po = bodies.alloc(rq->prob.n_bodies);
-        if (po < 0) { blobs.release(bo, rq->prob.n_blobs); break; }
-        const int64_t co = pcs.alloc(rq->pc_len);
-        if (co < 0) { blobs.release(bo, rq->prob.n_blobs); bodies.release(po, rq->prob.n_bodies); break; }
-        const int64_t so = starts.alloc(rq->prob.n_bodies + 1);
-        if (so < 0) {
-            blobs.release(bo, rq->prob.n_blobs); bodies.release(po, rq->prob.n_bodies);
-            pcs.release(co, rq->pc_len);
-            break;
+    int64_t big_b = blobs.largest(), big_p = bodies.largest(), big_c = pcs.largest(),
+            big_s = starts.largest();
+    std::vector<Req *> waiting;  // queued requests passed over in this scan
+    for (auto it = queue.begin(); it != queue.end() && !free_slots.empty();) {
+        Req *rq = *it;
+        int64_t bo = -1, po = -1, co = -1, so = -1;
+        const bool may_fit = rq->prob.n_blobs <= big_b && rq->prob.n_bodies <= big_p &&
+                             rq->pc_len <= big_c && rq->prob.n_bodies + 1 <= big_s;
+        if (may_fit && (bo = blobs.alloc(rq->prob.n_blobs)) >= 0) {
+            if ((po = bodies.alloc(rq->prob.n_bodies)) < 0) {
+                blobs.release(bo, rq->prob.n_blobs);
+            } else if ((co = pcs.alloc(rq->pc_len)) < 0) {
+                blobs.release(bo, rq->prob.n_blobs);
+                bodies.release(po, rq->prob.n_bodies);
+            } else if ((so = starts.alloc(rq->prob.n_bodies + 1)) < 0) {
+                blobs.release(bo, rq->prob.n_blobs);
+                bodies.release(po, rq->prob.n_bodies);
+                pcs.release(co, rq->pc_len);
+            }
         }
-        queue.pop_front();
+        if (so < 0) {  // does not fit now
+            if (max_bypass < 0 || rq->bypassed >= max_bypass) break;
+            waiting.push_back(rq);
+            ++it;
+            continue;
+        }
+        it = queue.erase(it);
+        for (Req *w : waiting) ++w->bypassed;
+        big_b = blobs.largest();
+        big_p = bodies.largest();
+        big_c = pcs.largest();
+        big_s = starts.largest();
         rq->blob_off = bo; rq->body_off = po; rq->pc_off = co; rq->start_off = so;
         rq->slot = free_slots.back();
         free_slots.pop_back();
@@ -1586,6 +1624,7 @@ mb_status Engine::retire(Req *rq, int conv, int iters, int restarts, cudaStream_
     running[sl] = nullptr;
     free_slots.push_back(sl);
     rq->slot = -1;
+    finished.push_back(rq->ticket);
     return MB_OK;
 }
 
@@ -1671,8 +1710,10 @@ mb_status mb_server_create(mb_context *ctx, const mb_params *params,
     mb_server *sv = new (std::nothrow) mb_server();
     if (!sv) return MB_ENOMEM;
     const double budget = limits->tick_pairs == 0.0 ? 1e9 : limits->tick_pairs;
+    const int bypass = limits->max_bypass == 0 ? 64 : limits->max_bypass;
     mb_status st = sv->eng.create(ctx, params, limits->max_blobs, limits->max_bodies,
-                                  limits->max_precond_bytes / 8, limits->max_requests, budget);
+                                  limits->max_precond_bytes / 8, limits->max_requests, budget,
+                                  bypass);
     if (st != MB_OK) {
         delete sv;
         return st;
@@ -1707,6 +1748,19 @@ mb_status mb_server_step(mb_server *server, void *stream, int *n_running, int *n
     if (n_running) *n_running = nr;
     if (n_queued) *n_queued = nq;
     return st;
+}
+
+mb_status mb_server_finished(mb_server *server, int64_t *tickets, int max_tickets, int *count)
+{
+    if (!server || !count || max_tickets < 0 || (max_tickets > 0 && !tickets)) return MB_EINVAL;
+    auto &fin = server->eng.finished;
+    int k = 0;
+    while (k < max_tickets && !fin.empty()) {
+        tickets[k++] = fin.front();
+        fin.pop_front();
+    }
+    *count = k;
+    return MB_OK;
 }
 
 mb_status mb_server_poll(mb_server *server, int64_t ticket, int *state, mb_info *info,

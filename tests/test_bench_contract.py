@@ -82,3 +82,38 @@ def test_clock_sampler_reads_nvidia_smi_samples(tmp_path, monkeypatch):
         assert os.path.exists(s.path)
         if path is None:
             os.remove(s.path)
+
+
+def test_accuracy_and_flop_helpers():
+    """The matvec accuracy figures compare against the oracle rows as stated,
+    and the setup flop count is n^3 per body of n = 3 n_p rows (Cholesky,
+    inverse factor and inverse product, n^3 / 3 each)."""
+    import numpy as np
+
+    import bench
+
+    ref = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    got = ref + np.array([[0.0, 1e-6, 0.0], [0.0, 0.0, 0.0]])
+    c = bench.compare_rows(got, ref)
+    assert c["rows"] == 2
+    assert abs(c["rel_l2_vs_oracle"] - 1e-6 / np.sqrt(5.0)) < 1e-15
+    assert abs(c["max_abs_vs_oracle"] - 1e-6) < 1e-18
+    assert abs(c["max_abs_over_max_ref"] - 0.5e-6) < 1e-18
+    f = bench.setup_flops([162, 162])
+    assert f["total"] == 2 * 486.0 ** 3 and f["cholesky"] == 2 * 486.0 ** 3 / 3.0
+
+
+def test_serving_requests_from_the_process_pool_equal_direct_ones():
+    """Serving requests generated by the spawned pool are the seeded
+    requests themselves."""
+    import numpy as np
+
+    import bench
+    from paper_1602_02170_gb300 import inputs as I
+
+    seeds = list(range(500, 520))
+    pooled = bench._gen_requests(seeds)
+    for sd, s in zip(seeds[:4], pooled[:4]):
+        d = I.config_serving_request(sd)
+        for k in ("q", "theta", "blob_start", "rho", "F", "T"):
+            np.testing.assert_array_equal(getattr(s, k), getattr(d, k))

@@ -152,3 +152,78 @@ def test_server_split_matvec_matches_unsplit(ctx):
         r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
         Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
         assert rel_l2(Ub, Ur) <= 1e-6 and rel_l2(Wb, Wr) <= 1e-6
+
+
+def _head_of_line_setup():
+    """A medium request A, then a large request B that cannot fit beside A,
+    then small requests C, D, E that can."""
+    sa, sb = I.mixed_suspension(600, 10), I.mixed_suspension(601, 30)
+    small = [I.mixed_suspension(602 + k, 2) for k in range(3)]
+    cap = max(sb.n_blobs, sa.n_blobs + sum(s.n_blobs for s in small)) + 5
+    assert sa.n_blobs + sb.n_blobs > cap
+    return sa, sb, small, cap
+
+
+def _check_vs_oracle(srv, jobs):
+    for s, t, (U, W, lam) in jobs:
+        state, info, status = srv.poll(t)
+        assert state == mb.Server.DONE and status == "MB_OK", (state, status, info)
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        Ur, Wr, _ = O.solve_saddle(r, s.q, s.blob_start, s.F, s.T, A, 1.0, True)
+        assert rel_l2(host(U), Ur) <= 1e-6 and rel_l2(host(W), Wr) <= 1e-6
+
+
+@pytest.mark.parametrize("max_bypass", [0, -1])
+def test_server_small_request_overtakes_a_waiting_large_one(ctx, max_bypass):
+    """Admission scans the queue in arrival order: a small request queued
+    behind a large one that does not fit yet is admitted first (max_bypass =
+    0, the default limit); with max_bypass < 0 admission is strictly first
+    come, first served and it waits.  Every result matches the oracle."""
+    sa, sb, small, cap = _head_of_line_setup()
+    srv = mb.Server(ctx, A, tol=1e-10, prec="mixed", max_blobs=cap, max_bodies=500,
+                    max_requests=8, max_bypass=max_bypass)
+    tA, oA = srv.submit(_prob(sa))
+    srv.step()
+    tB, oB = srv.submit(_prob(sb))
+    tC, oC = srv.submit(_prob(small[0]))
+    srv.step()
+    assert srv.poll(tA)[0] == mb.Server.RUNNING
+    assert srv.poll(tB)[0] == mb.Server.QUEUED
+    assert srv.poll(tC)[0] == (mb.Server.RUNNING if max_bypass == 0 else mb.Server.QUEUED)
+    srv.run_until_idle()
+    assert sorted(srv.finished()) == sorted([tA, tB, tC])
+    assert srv.finished() == []
+    _check_vs_oracle(srv, [(sa, tA, oA), (sb, tB, oB), (small[0], tC, oC)])
+    srv.close()
+
+
+def test_server_aging_bounds_the_overtaking(ctx):
+    """With max_bypass = 1, once later requests have overtaken the waiting
+    large request, the next arrival queues behind it until it is admitted."""
+    sa, sb, small, cap = _head_of_line_setup()
+    srv = mb.Server(ctx, A, tol=1e-10, prec="mixed", max_blobs=cap, max_bodies=500,
+                    max_requests=8, max_bypass=1)
+    tA, oA = srv.submit(_prob(sa))
+    srv.step()
+    tB, oB = srv.submit(_prob(sb))
+    tC, oC = srv.submit(_prob(small[0]))
+    tD, oD = srv.submit(_prob(small[1]))
+    srv.step()
+    assert srv.poll(tB)[0] == mb.Server.QUEUED
+    assert srv.poll(tC)[0] == mb.Server.RUNNING and srv.poll(tD)[0] == mb.Server.RUNNING
+    tE, oE = srv.submit(_prob(small[2]))
+    srv.step()
+    # B has been overtaken twice: E, which would fit, waits behind it
+    assert srv.poll(tB)[0] == mb.Server.QUEUED and srv.poll(tE)[0] == mb.Server.QUEUED
+    order = []
+    for _ in range(100000):
+        nr, nq = srv.step()
+        for t in (tB, tE):
+            if t not in order and srv.poll(t)[0] != mb.Server.QUEUED:
+                order.append(t)
+        if nr == 0 and nq == 0:
+            break
+    assert order[0] == tB  # B is admitted before (or with) E
+    _check_vs_oracle(srv, [(sa, tA, oA), (sb, tB, oB), (small[0], tC, oC),
+                           (small[1], tD, oD), (small[2], tE, oE)])
+    srv.close()
