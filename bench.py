@@ -119,6 +119,8 @@ def parse():
     p.add_argument("--tick-pairs", type=float, default=0.0,
                    help="serving: pair evaluations a request may take per tick in the FP32 "
                         "Arnoldi matvec (0 = engine default, < 0 = no limit)")
+    p.add_argument("--bodies", type=int, default=4096,
+                   help="setup: monolayer bodies (at the monolayer's area density)")
     p.add_argument("--pair-variant", type=int, default=-1,
                    help="FP32 pair-kernel variant (-1 autotune; 0..4 pin one, e.g. for profiling)")
     return p.parse_args()
@@ -715,8 +717,10 @@ def bench_monolayer(args):
 
 
 def bench_setup(args):
-    """The monolayer's preconditioner setup alone, three times (the command
-    the setup kernels' launch list and captures are taken from)."""
+    """The monolayer's preconditioner setup alone, three times, then ten
+    applications of it (the command the setup and apply kernels' launch list
+    and captures are taken from); --bodies shrinks the patch at the same
+    density."""
     import numpy as np
     import torch
 
@@ -727,7 +731,8 @@ def bench_setup(args):
     B.build()
     ctx = mb.Context(0)
     peaks = measured_peaks(ctx, 0)
-    s = I.config_monolayer(1)
+    s = I.config_monolayer(1, n_bodies=args.bodies,
+                           box=200.0 * math.sqrt(args.bodies / 4096.0))
     P = _dev_problem(s)
     r = ctx.blob_positions(P["q"], P["theta"], P["blob_start"], P["rho"])
     times = []
@@ -742,12 +747,30 @@ def bench_setup(args):
     counts = np.diff(s.blob_start)
     fl = setup_flops(counts, precond_factored(counts, peaks["sm_count"]))
     ms = min(times)
-    print(json.dumps({"metric": "preconditioner setup ms", "workload": "monolayer blocks, "
-                      "4096 x 486 rows, wall", "ms": times, "form": fl["form"],
+    rng = np.random.default_rng(0)
+    w = torch.as_tensor(rng.standard_normal((s.n_blobs, 3))).cuda()
+    g = torch.as_tensor(rng.standard_normal((s.n_bodies, 6))).cuda()
+    ctx.precond_apply(w, g)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        ctx.precond_apply(w, g)
+    e1.record()
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 10
+    nrows = 3.0 * counts
+    apply_fma = float(np.sum((nrows + 6.0) ** 2))
+    print(json.dumps({"metric": "preconditioner setup ms", "workload": f"monolayer blocks, "
+                      f"{s.n_bodies} x 486 rows, wall", "ms": times, "form": fl["form"],
                       "fp64_flops": fl["total"],
                       "achieved_tflops": fl["total"] / (ms / 1e3) / 1e12,
                       "fp64_peak_tflops": peaks["fp64_tflops"],
                       "frac": fl["total"] / (ms / 1e3) / 1e12 / peaks["fp64_tflops"],
+                      "apply_ms": apply_ms,
+                      "apply_tflops": 2.0 * apply_fma / (apply_ms / 1e3) / 1e12,
+                      "apply_frac": 2.0 * apply_fma / (apply_ms / 1e3) / 1e12 / peaks["fp64_tflops"],
+                      "apply_flops_basis": "(n + 6)^2 FP64 FMA per body and application",
                       "n_gpus": 1}), flush=True)
     ctx.close()
     return 0

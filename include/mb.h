@@ -273,12 +273,15 @@ mb_status mb_KT_apply(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const 
  * Block-diagonal preconditioner setup (Section 2.2.2, Eqs.
  * M_tilde_block_diag and indef_block_P): for every body p, assemble its
  * blob mobility block M^(pp) (with the wall if wall != 0), factor it by FP64
- * Cholesky, form the 6 x 6 body Schur complement N~_p =
- * (K_p^T M^(pp)-1 K_p)^-1, and store the body's explicit inverse of the
- * indefinite block [[M^(pp), -K_p], [-K_p^T, 0]] in the context.  r are the
- * blob positions (device, N x 3).  Synchronises the stream; returns
- * MB_ESINGULAR (with the first failing body in mb_last_error) if a block is
- * not positive definite.
+ * Cholesky M^(pp) = L L^T, form the 6 x 6 body Schur complement N~_p =
+ * (K_p^T M^(pp)-1 K_p)^-1, and keep in the context either the body's
+ * explicit inverse of the indefinite block [[M^(pp), -K_p], [-K_p^T, 0]]
+ * (applied as one GEMV), or, when there are at least as many bodies as SMs
+ * and blocks of more than 160 rows (up to 2,048), the factored form L,
+ * L^-1 K_p and N~_p (applied by triangular solves: the same FP64 work per
+ * application, a third of the setup's).  r are the blob positions (device,
+ * N x 3).  Synchronises the stream; returns MB_ESINGULAR (with the first
+ * failing body in mb_last_error) if a block is not positive definite.
  */
 mb_status mb_precond_setup(mb_context *ctx, int64_t n_bodies, int64_t n_blobs, const double *r,
                            const double *q, const int64_t *blob_start, double a, double eta,

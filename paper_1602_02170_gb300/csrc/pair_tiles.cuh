@@ -316,12 +316,14 @@ __device__ __forceinline__ double addf(double a, float c) { return a + (double)c
 // three shared monomials once:
 //   T1 = E t2,  t4_3 = t4 / 3,  t2_3 = t2 / 3,  T2_3 = E t4 / 3,
 //   f1 = 2 (T1 - p + t4_3 - t2_3) - 10 T2_3 - 1
-//   f2 = 2 (3 p - 5 T1 + t2) + 10 (7 T2_3 - t4_3) - 1
-//   f3 = 2 hs + e3 [4 (5 T1 - t2 - 3 p) + 20 (2 t4_3 - 7 T2_3)]
+//   f2 = F2 - 1,  F2 = 2 (3 p - 5 T1 + t2) + 10 (7 T2_3 - t4_3)
+//   f3 = 2 hs + e3 (20 t4_3 - 2 F2)
 //   f4 = 2 hs - 20 e3 t4_3
 //   f5 = 4 (15 T2_3 - 2 t4_3 - hs^2 - T1)
-// (the f1..f5 of rpy_wall.cuh term by term), and f2 / rho^2, f3 / rho,
-// f4 / rho formed once for both directions as in pair_sym2.
+// (the f1..f5 of rpy_wall.cuh term by term; the bracket of f3,
+// t2 (20E - 4) + t4 (40/3 - 140E/3) - 12p, equals 20 t4 / 3 - 2 (f2 + 1)),
+// and f2 / rho^2, f3 / rho, f4 / rho formed once for both directions as in
+// pair_sym2.
 template <bool WALL, typename T>
 __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, T fy, T fz, T gx,
                                             T gy, T gz, const PairConsts<T> &k, T &ux, T &uy,
@@ -367,12 +369,10 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
     const T T2_3 = E * t4_3;
     const T hs2 = mul_pow2(hs, 2.f);
     const T f1 = addf(mul_pow2(T1 + (-p) + t4_3 + (-t2_3), 2.f) + mulf(T2_3, -10.f), -1.f);
-    const T f2 = addf(mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f) +
-                            mulf(mulf(T2_3, 7.f) + (-t4_3), 10.f),
-                        -1.f);
-    const T in3 = mul_pow2(mulf(T1, 5.f) + (-t2) + mulf(p, -3.f), 4.f) +
-                    mulf(mul_pow2(t4_3, 2.f) + mulf(T2_3, -7.f), 20.f);
-    const T f3 = hs2 + e3 * in3;
+    const T F2 = mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f) +
+                 mulf(mulf(T2_3, 7.f) + (-t4_3), 10.f);
+    const T f2 = addf(F2, -1.f);
+    const T f3 = hs2 + e3 * (mulf(t4_3, 20.f) + mul_pow2(F2, -2.f));
     const T f4 = hs2 + mulf(e3 * t4_3, -20.f);
     const T f5 = mul_pow2(mulf(T2_3, 15.f) + mul_pow2(t4_3, -2.f) + (-(hs * hs)) + (-T1), 4.f);
     const T s = k.sw * invR;
