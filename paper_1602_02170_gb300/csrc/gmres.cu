@@ -241,10 +241,30 @@ constexpr int kOrthClusterThreads = 256;
 // another.  The arithmetic and its order are the same either way.
 constexpr int64_t kOrthStageDoubles = 8192;
 
+// 1/sqrt(d) in FP64: the FP32 estimate refined by one FP32 and two FP64
+// Newton-Raphson steps, y <- y (3 - d y^2) / 2 (quadratic convergence: FP64
+// accuracy).  FP64 instructions issue slowly on this chip, so this short
+// sequence replaces the square roots and divisions of the serial parts of
+// the orthogonalisation.  Arguments outside the FP32 range take 1 / sqrt.
+__device__ __forceinline__ double rsqrt_fp64(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    const float df = (float)d;
+    float yf = rsqrtf(df);
+    yf = yf * (1.5f - 0.5f * df * yf * yf);
+    double y = (double)yf;
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y * (1.5 - 0.5 * d * y * y);
+}
+
 // post (optional): mapped host memory [est, step count]; rank 0 writes the
 // residual estimate, then (after a system-scope fence) the incremented count
 // kept at *seq, so that the host can read the estimate without a stream
 // synchronisation.
+//
+// When staged, the slices are held in T (the passes' arithmetic), so that
+// FP32 passes convert each element once instead of at every use, and the
+// merged coefficients of each pass are converted once as well.
 template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
     orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
@@ -256,8 +276,9 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     const int rank = (int)cluster.block_rank();
     // shared: part[3][m + 1] partial sums (pass 0, pass 1, |w|^2), hs[m + 1]
     // summed coefficients, hc[m + 2] merged column j of H, cs[m], sn[m]
-    // previous rotations (rank 0), red[32] block partials, then (stage != 0)
-    // the staged slices sV[(j + 2) x per]
+    // previous rotations (rank 0), red[32] block partials, hT[m + 1] the
+    // summed coefficients in T, then (stage != 0) the staged slices
+    // sV[(j + 2) x per] in T
     extern __shared__ double buf[];
     const int m1 = S.m + 1;
     double *part = buf;
@@ -266,7 +287,8 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     double *cs = hc + S.m + 2;
     double *sn = cs + S.m;
     double *red = sn + S.m;
-    double *sV = red + 32;
+    T *hT = (T *)(red + 32);
+    T *sV = (T *)(red + 32 + m1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t per = (L + kOrthCluster - 1) / kOrthCluster;
     const int64_t e0 = rank * per, e1 = e0 + per < L ? e0 + per : L;
@@ -305,23 +327,25 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
                 const int x = x0 + u * (int)blockDim.x;
                 if (x < total) {
                     const int i = x / cnt, k = x - i * cnt;
-                    sV[(int64_t)i * per + k] = v[u];
+                    sV[(int64_t)i * per + k] = T(v[u]);
                 }
             }
         }
         __syncthreads();
     }
-    // element e0 + k of vector i: vs(i)[k], staged or in place
-    auto vs = [&](int i) -> double * {
-        return stage ? sV + (int64_t)i * per : V + (int64_t)i * L + e0;
+    // element e0 + k of vector i, staged (in T) or in place (FP64)
+    auto ld = [&](int i, int k) -> T {
+        return stage ? sV[(int64_t)i * per + k] : T(V[(int64_t)i * L + e0 + k]);
     };
-    double *ws = vs(j + 1);
+    auto st_w = [&](int k, T v) {
+        if (stage) sV[(int64_t)(j + 1) * per + k] = v;
+        else w[e0 + k] = double(v);
+    };
     for (int pass = 0; pass < 2; ++pass) {
         double *pp = part + pass * m1;
         for (int i = warp; i <= j; i += nw) {
-            const double *v = vs(i);
             T acc = T(0);
-            for (int k = lane; k < cnt; k += 32) acc += T(v[k]) * T(ws[k]);
+            for (int k = lane; k < cnt; k += 32) acc += ld(i, k) * ld(j + 1, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) pp[i] = double(acc);
@@ -331,19 +355,23 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             double acc = 0.0;
             for (int rr = 0; rr < kOrthCluster; ++rr) acc += cluster.map_shared_rank(pp, rr)[i];
             hs[i] = acc;
+            hT[i] = T(acc);
+            hc[i] = pass == 0 ? acc : hc[i] + acc;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            T acc = T(ws[k]);
-            for (int i = 0; i <= j; ++i) acc -= T(vs(i)[k]) * T(hs[i]);
-            ws[k] = double(acc);
+            T acc = ld(j + 1, k);
+            for (int i = 0; i <= j; ++i) acc -= ld(i, k) * hT[i];
+            st_w(k, acc);
         }
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = pass == 0 ? hs[i] : hc[i] + hs[i];
-        __syncthreads();  // hs is rewritten by the next pass
+        __syncthreads();  // hs, hT are rewritten by the next pass; w is final
     }
     double *pn = part + 2 * m1;
     double acc = 0.0;
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) acc += ws[k] * ws[k];
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const double v = double(ld(j + 1, k));
+        acc += v * v;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -358,13 +386,15 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         double t = 0.0;
         for (int rr = 0; rr < kOrthCluster; ++rr) t += cluster.map_shared_rank(pn, rr)[0];
         red[0] = t;
+        red[1] = t > 0.0 ? rsqrt_fp64(t) : 0.0;  // 1 / |w|
     }
     __syncthreads();
-    const double nrm2 = red[0];
+    const double nrm2 = red[0], inv = red[1];
     if (rank == 0) {
         if (threadIdx.x == 0) {
-            // Givens update of column j on the shared copy (as givens_column)
-            hc[j + 1] = sqrt(nrm2);
+            // Givens update of column j on the shared copy (as givens_column,
+            // with the norms from rsqrt_fp64)
+            hc[j + 1] = nrm2 * inv;
             for (int i = 0; i < j; ++i) {
                 const double a = hc[i], b = hc[i + 1];
                 hc[i] = cs[i] * a + sn[i] * b;
@@ -372,10 +402,11 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             }
             const double gj = red[16];
             const double a = hc[j], b = hc[j + 1];
-            const double rr = hypot(a, b);
-            const double c = rr > 0.0 ? a / rr : 1.0;
-            const double sg = rr > 0.0 ? b / rr : 0.0;
-            hc[j] = rr;
+            const double r2 = a * a + b * b;
+            const double ir = r2 > 0.0 ? rsqrt_fp64(r2) : 0.0;
+            const double c = r2 > 0.0 ? a * ir : 1.0;
+            const double sg = r2 > 0.0 ? b * ir : 0.0;
+            hc[j] = r2 * ir;
             hc[j + 1] = 0.0;
             sm[S.cs() + j] = c;
             sm[S.sn() + j] = sg;
@@ -394,13 +425,11 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         __syncthreads();
         for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
     }
-    const double d = sqrt(nrm2);
-    const double inv = d > 0.0 ? 1.0 / d : 0.0;
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = ws[k] * inv;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = double(ld(j + 1, k)) * inv;
     cluster.sync();  // no CTA exits while another still reads its partials
 }
 
-size_t orth_cluster_smem(int m) { return sizeof(double) * (7 * (size_t)m + 38); }
+size_t orth_cluster_smem(int m) { return sizeof(double) * (8 * (size_t)m + 39); }
 
 // Whether step j stages its slices, and its dynamic shared memory.
 bool orth_cluster_stage(int64_t L, int j)

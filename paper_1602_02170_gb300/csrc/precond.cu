@@ -722,22 +722,30 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         for (int c0 = 0; c0 < n; c0 += kPanel) {
             const int w = n - c0 < kPanel ? n - c0 : kPanel, t0 = c0 + w;
             cluster.sync();  // (a) the previous trailing updates are complete
-            // (b) + (c) warp 0: lane a < w reads row a of the diagonal block and
-            // of B from its owner into registers, then the block's Cholesky and
-            // the forward substitution of its B rows run on registers (the
-            // column loop unrolled, the other rows' entries by shuffles); the
-            // factored rows go to D and Bd for the other warps
+            // (b) + (c) warp 0: lane a < w reads row a of the diagonal block
+            // from its owner into registers, then the block's Cholesky runs on
+            // registers (the column loop unrolled, the other rows' entries by
+            // shuffles); the factored rows go to D.  Meanwhile warp 1 fetches
+            // the panel's rows of B (lane x < 6 holds column x), which it
+            // solves against D once D is complete: FP64 instructions issue
+            // slowly on this chip, so the chain of warp 0 carries only the
+            // block's own arithmetic.
+            double bcol[kPanel];
+            if (warp == 1 && lane < 6) {
+#pragma unroll
+                for (int r = 0; r < kPanel; ++r) {
+                    const int row = c0 + r;
+                    bcol[r] = r < w ? cluster.map_shared_rank(Br, row % kFacCluster)
+                                          [6 * (row / kFacCluster) + lane]
+                                    : 0.0;
+                }
+            }
             if (warp == 0) {
-                double drow[kPanel], brow[6];
+                double drow[kPanel];
                 const int row = c0 + lane;
                 const double *src = lane < w ? row_of(row) + c0 : nullptr;
-                const double *bsrc =
-                    lane < w ? cluster.map_shared_rank(Br, row % kFacCluster) + 6 * (row / kFacCluster)
-                             : nullptr;
 #pragma unroll
                 for (int b = 0; b < kPanel; ++b) drow[b] = lane < w && b <= lane ? rd(src + b) : 0.0;
-#pragma unroll
-                for (int x = 0; x < 6; ++x) brow[x] = lane < w ? bsrc[x] : 0.0;
                 int f = 0;
 #pragma unroll
                 for (int c = 0; c < kPanel; ++c) {
@@ -751,16 +759,10 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                             const double il = rsqrt_newton(d);
                             if (lane == 0) ils[c0 + c] = il;
                             drow[c] *= lane >= c ? il : 1.0;  // lane c: sqrt(d)
-                            const double sc = lane == c ? il : 1.0;
-#pragma unroll
-                            for (int x = 0; x < 6; ++x) brow[x] *= sc;
                             const double lac = lane > c && lane < w ? drow[c] : 0.0;
 #pragma unroll
                             for (int b = c + 1; b < kPanel; ++b)
                                 drow[b] -= lac * __shfl_sync(0xffffffffu, drow[c], b);
-#pragma unroll
-                            for (int x = 0; x < 6; ++x)
-                                brow[x] -= lac * __shfl_sync(0xffffffffu, brow[x], c);
                         }
                     }
                 }
@@ -768,8 +770,6 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
 #pragma unroll
                     for (int b = 0; b < kPanel; ++b)
                         if (b <= lane) D[lane * kPanel + b] = drow[b];
-#pragma unroll
-                    for (int x = 0; x < 6; ++x) Bd[6 * lane + x] = brow[x];
                 }
                 if (lane == 0) fail_s = f;
             }
@@ -778,6 +778,21 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 cluster.sync();  // every CTA has finished reading in (b)
                 fail = 1;
                 break;
+            }
+            // warp 1: the panel's B rows by forward substitution against D
+            // (Bd[r] = (B[c0 + r] - sum_{k<r} D[r][k] Bd[k]) / L_rr)
+            if (warp == 1 && lane < 6) {
+#pragma unroll
+                for (int r = 0; r < kPanel; ++r) {
+                    if (r < w) {
+                        double v = bcol[r];
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k)
+                            if (k < r) v -= D[r * kPanel + k] * bcol[k];
+                        bcol[r] = v * ils[c0 + r];
+                        Bd[6 * r + lane] = bcol[r];
+                    }
+                }
             }
             // (d) own rows below the panel: L[i][c0 + k] by forward substitution,
             // column-oriented (each x[k], once known, is subtracted from all
@@ -863,15 +878,20 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                     Li[j] = a0 + a1;
                     if (two) Li[j2] = b0 + b1;
                 }
-                if (lane < 6) {
-                    double a0 = Br[6 * li + lane], a1 = 0.0;
+            }
+            // ... and of the own rows of B, the entries (row, column) spread
+            // over all threads
+            for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x) {
+                const int li = e / 6, x = e - 6 * li;
+                if (rank + kFacCluster * li < t0) continue;
+                const double *Li = own(li) + c0;
+                double a0 = Br[e], a1 = 0.0;
 #pragma unroll
-                    for (int k = 0; k < kPanel; k += 2) {
-                        if (k < w) a0 -= lk[k] * Bd[6 * k + lane];
-                        if (k + 1 < w) a1 -= lk[k + 1] * Bd[6 * (k + 1) + lane];
-                    }
-                    Br[6 * li + lane] = a0 + a1;
+                for (int k = 0; k < kPanel; k += 2) {
+                    if (k < w) a0 -= Li[k] * Bd[6 * k + x];
+                    if (k + 1 < w) a1 -= Li[k + 1] * Bd[6 * (k + 1) + x];
                 }
+                Br[e] = a0 + a1;
             }
         }
         if (fail) {
