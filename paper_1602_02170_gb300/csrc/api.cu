@@ -188,6 +188,8 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
                       &ctx->sol_dx, &ctx->sol_ym, &ctx->pc_type, &ctx->pc_theta, &ctx->pc_ref,
                       &ctx->eval_hi, &ctx->eval_lo, &ctx->render_r, &ctx->render_f,
+                      &ctx->sort_perm, &ctx->sort_key, &ctx->sort_count, &ctx->sort_hi,
+                      &ctx->sort_lo, &ctx->sort_box, &ctx->sort_grid, &ctx->sort_f, &ctx->sort_u,
                       &ctx->batch_ws};
     for (auto &g : ctx->iter_graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);

@@ -160,8 +160,14 @@ static_assert(kSaddleRowsMaxBodies == kKTBlockBodies,
 // beta = 1); the other blocks take bodies, one CTA per body:
 //   y_(3N + 6p + c) = -(K^T lambda)_p,c
 // (the reduction of KT_apply_block_kernel).  All threads of a block take the
-// same branch, so the barriers of the body branch are uniform.
-__global__ void __launch_bounds__(256) saddle_rows_kernel(
+// same branch, so the barriers of the body branch are uniform.  Blocks are
+// small (kSaddleThreads): the per-thread work is a short serial chain of FP64
+// instructions, which issue slowly on this chip, so spreading the warps over
+// more SMs shortens the launch; for bodies of up to 64 blobs the body sums
+// round as with one CTA of 256 threads.
+constexpr int kSaddleThreads = 64;
+
+__global__ void __launch_bounds__(kSaddleThreads) saddle_rows_kernel(
     const double *__restrict__ partial, int S, double scale, int64_t n, int64_t nb,
     const double *__restrict__ r, const double *__restrict__ q, const int64_t *__restrict__ start,
     const double *__restrict__ x, double *__restrict__ y, int blob_blocks)
@@ -192,7 +198,8 @@ __global__ void __launch_bounds__(256) saddle_rows_kernel(
         }
         return;
     }
-    __shared__ double red[8][6];
+    constexpr int kWarps = kSaddleThreads / 32;
+    __shared__ double red[kWarps][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int body_blocks = (int)gridDim.x - blob_blocks;
     for (int64_t p = (int)blockIdx.x - blob_blocks; p < nb; p += body_blocks) {
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(256) saddle_rows_kernel(
         __syncthreads();
         if (threadIdx.x < 6) {
             double v = 0.0;
-            for (int w8 = 0; w8 < 8; ++w8) v += red[w8][threadIdx.x];
+            for (int w8 = 0; w8 < kWarps; ++w8) v += red[w8][threadIdx.x];
             y[m + 6 * p + threadIdx.x] = -v;
         }
     }
@@ -258,9 +265,10 @@ void launch_saddle_rows(const MatvecPartials &mp, int64_t n, int64_t nb, const d
                         const double *q, const int64_t *blob_start, const double *x, double *y,
                         cudaStream_t s)
 {
-    const int blob_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024));
-    saddle_rows_kernel<<<blob_blocks + (int)nb, 256, 0, s>>>(mp.partial, mp.S, mp.scale, n, nb, r,
-                                                             q, blob_start, x, y, blob_blocks);
+    const int blob_blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kSaddleThreads), 4096));
+    saddle_rows_kernel<<<blob_blocks + (int)nb, kSaddleThreads, 0, s>>>(
+        mp.partial, mp.S, mp.scale, n, nb, r, q, blob_start, x, y, blob_blocks);
     count_launch();
 }
 

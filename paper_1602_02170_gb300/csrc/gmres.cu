@@ -451,8 +451,48 @@ __global__ void merge_passes_kernel(double *__restrict__ sm, Small L, int j)
 }
 
 // Back substitution R y = g for the leading k x k triangle.
+// 1/d in FP64: the FP32 reciprocal refined by two FP64 Newton steps
+// y <- y (2 - d y); arguments outside the FP32 range take the division.
+__device__ __forceinline__ double rcp_fp64(double d)
+{
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    double y = (double)(1.0f / (float)d);
+    y = y * (2.0 - d * y);
+    return y * (2.0 - d * y);
+}
+
+// y = R^-1 g for the k x k upper triangle R of H (the least-squares problem
+// of the restart cycle).  For k <= 32 one warp runs it: lane i holds row i,
+// all reciprocals of the diagonal are formed at once, and the back
+// substitution is column-oriented (y_j, once known, is subtracted from every
+// earlier row at once): one shuffle and one FMA per step instead of a
+// division and a dot product.  Larger k take the serial loop on one thread.
 __global__ void solve_triangle_kernel(double *__restrict__ sm, Small L, int k)
 {
+    const int lane = threadIdx.x & 31;
+    if (k <= 32) {
+        if (threadIdx.x >= 32) return;
+        // row `lane` of R in registers first: the loads are all in flight at
+        // once instead of one per step of the chain
+        double h[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = lane < j && j < k ? sm[L.H(lane, j)] : 0.0;
+        const double d = lane < k ? sm[L.H(lane, lane)] : 1.0;
+        const double rinv = d != 0.0 ? rcp_fp64(d) : 0.0;
+        double acc = lane < k ? sm[L.g() + lane] : 0.0;
+#pragma unroll
+        for (int j = 31; j >= 0; --j) {
+            if (j < k) {
+                const double yj = __shfl_sync(0xffffffffu, acc * rinv, j);
+                if (lane == j) acc = yj;
+                else if (lane < j) acc -= h[j] * yj;
+            }
+        }
+        if (lane < k) sm[L.y() + lane] = acc;
+        return;
+    }
+    if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; --i) {
         double acc = sm[L.g() + i];
         for (int j = i + 1; j < k; ++j) acc -= sm[L.H(i, j)] * sm[L.y() + j];
@@ -952,7 +992,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                 MB_TRY(S.read_est(&est));
                 if (!(est > inner_abs)) break;
             }
-            solve_triangle_kernel<<<1, 1, 0, s>>>(S.sm, sl, k);
+            solve_triangle_kernel<<<1, 32, 0, s>>>(S.sm, sl, k);
             count_launch();
             if (mixed)
                 update_span_kernel<<<vg, 256, 0, s>>>(S.Z, L, k, S.sm + sl.y(), S.x, dx, L);

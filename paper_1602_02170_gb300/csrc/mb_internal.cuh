@@ -72,6 +72,13 @@ struct mb_context {
     mb::DevBuf stage_r, stage_f, stage_u;  // staging for host-pointer calls
     mb::DevBuf eval_hi, eval_lo;           // packed flow-evaluation points (FP32 path)
     mb::DevBuf render_r, render_f;         // refined blobs of a flow rendering
+    // spatial order for the symmetric FP32 kernel (matvec_pack_positions):
+    // permutation, its sorted packed positions, the bounding box of every
+    // block of the kernel, per-cell counters, the grid and far threshold,
+    // and the gathered forces / scattered velocities of a matvec
+    mb::DevBuf sort_perm, sort_key, sort_count, sort_hi, sort_lo, sort_box, sort_grid;
+    mb::DevBuf sort_f, sort_u;
+    int64_t sorted_n = 0;                  // N of the current order (0: none)
 
     // preconditioner (last mb_precond_setup / mb_precond_setup_shared)
     mb::DevBuf pinv;             // explicit inverses, (3n_p+6)^2 doubles each: one per
@@ -138,8 +145,10 @@ mb_status matvec_device(mb_context *ctx, const double *r, const double *f, int64
                         double eta, int wall, mb_precision prec, double *u, cudaStream_t s);
 // Autotuner size class of an FP32 matvec (pair_matvec.cu).
 int tune_key(int64_t n, int wall);
-// Pack positions once (FP32 path); the matvec then only reads f.
-mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s);
+// Pack positions once (FP32 path); the matvec then only reads f.  order: also
+// sort them spatially for the symmetric FP32 kernel (N >= 16,384).
+mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s,
+                                bool order = true);
 // u(x_t) = sum_j M(x_t, r_j) f_j at nt points x (targets) from ns blobs.
 mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double *r,
                       const double *f, int64_t ns, double a, double eta, int wall,

@@ -149,13 +149,25 @@ __global__ void __launch_bounds__(NT, NT == kNT ? (NP == 1 ? 3 : 2) : 16) pair_f
 
 // Symmetric packed kernel: persistent loop over the upper-triangular block
 // pairs (I <= J) of blocks of 2*kNT blobs, row by row; see x2sym_item.
+//
+// box (optional): the bounding box of every block, (min x, y, z, max x, y, z),
+// and grid->far2, the squared distance beyond which a block pair is far (see
+// x2sym_item); such pairs take the FAR instance.
+struct SortGrid {
+    float lo[3], inv_h[3];  // cell of x: (x - lo) * inv_h per axis
+    int bits[3];            // bits of the cell index per axis
+    float far2;             // squared box distance of a far block pair
+};
+
 template <bool WALL>
 __global__ void __launch_bounds__(kNT, 2) pair_sym_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
-    int64_t n, int64_t nb, int64_t n_items, PairConsts2 k, double *__restrict__ u, double scale)
+    int64_t n, int64_t nb, int64_t n_items, PairConsts2 k, double *__restrict__ u, double scale,
+    const float *__restrict__ box, const SortGrid *__restrict__ grid)
 {
     __shared__ float4 sP[kX2SmemFloat4PerSource * kNT];
     __shared__ float sRev[3 * kNT * (kNT / 32)];
+    const float far2 = box ? fmaxf(grid->far2, 1.5625f * k.four_a2) : 0.f;
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         // row I holds nb - I items; rowoff(I) = I*nb - I*(I-1)/2
         int64_t lo_r = 0, hi_r = nb;
@@ -166,7 +178,19 @@ __global__ void __launch_bounds__(kNT, 2) pair_sym_kernel(
         }
         const int64_t I = lo_r;
         const int64_t J = I + (item - (I * nb - I * (I - 1) / 2));
-        x2sym_item<WALL, kNT>(sP, sRev, hi, lo, f, n, I, J, k, u, scale);
+        bool far = false;
+        if (box && I != J) {
+            const float *bi = box + 6 * I, *bj = box + 6 * J;
+            float d2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float g = fmaxf(fmaxf(bj[c] - bi[3 + c], bi[c] - bj[3 + c]), 0.f);
+                d2 = fmaf(g, g, d2);
+            }
+            far = d2 > far2;  // the same in every thread
+        }
+        if (far) x2sym_item<WALL, kNT, true>(sP, sRev, hi, lo, f, n, I, J, k, u, scale);
+        else x2sym_item<WALL, kNT, false>(sP, sRev, hi, lo, f, n, I, J, k, u, scale);
     }
 }
 
@@ -398,6 +422,331 @@ void f32_launch(int v, const Plan &p, cudaStream_t s, const float4 *hi, const fl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Spatial order for the symmetric FP32 kernel (N >= kSortMinN).  The blobs are
+// sorted by cell of a grid over their bounding box, cells in Morton order
+// (kSortBits bits, dealt to the axes in proportion to their extents), by a
+// counting sort; the kernel's blocks of 2 kNT consecutive sorted blobs are
+// then compact, and the block pairs far apart take the FAR instance of the
+// pair item.  Each matvec gathers f into the sorted order and scatters u back.
+// The sort is stable (the blobs of a cell keep their index order), so the
+// order, and with it the FP32 rounding of every pair sum, is the same on
+// every call: a tile of consecutive blobs per CTA counts its keys in shared
+// memory, the counts are scanned over tiles and buckets, and one warp per
+// tile deals its blobs out in index order.
+constexpr int64_t kSortMinN = 16384;
+constexpr int kSortBits = 15;
+constexpr int kSortBuckets = 1 << kSortBits;
+constexpr int kSortKeysSmem = 16384;  // keys staged per round of the scatter
+constexpr size_t kSortHistSmem = sizeof(int) * kSortBuckets;
+constexpr size_t kSortScatterSmem = kSortHistSmem + sizeof(unsigned) * kSortKeysSmem;
+
+__device__ __forceinline__ unsigned float_order(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float order_float(unsigned u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// box[0..2] = ordered min, box[3..5] = ordered max (initialised to ~0 / 0)
+__global__ void __launch_bounds__(256) sort_bbox_kernel(const float4 *__restrict__ hi, int64_t n,
+                                                        unsigned *__restrict__ box)
+{
+    unsigned mn[3] = {~0u, ~0u, ~0u}, mx[3] = {0u, 0u, 0u};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 h = hi[i];
+        const unsigned v[3] = {float_order(h.x), float_order(h.y), float_order(h.z)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = min(mn[c], v[c]);
+            mx[c] = max(mx[c], v[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicMin(box + c, mn[c]);
+            atomicMax(box + 3 + c, mx[c]);
+        }
+}
+
+// The grid (bits per axis by repeatedly halving the longest cell side) and
+// the far distance: separations beyond 2^18 ulp of the largest coordinate.
+__global__ void sort_grid_kernel(const unsigned *__restrict__ box, SortGrid *__restrict__ g)
+{
+    float lo[3], ext[3], big = 0.f;
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = order_float(box[c]);
+        const float hi = order_float(box[3 + c]);
+        ext[c] = fmaxf(hi - lo[c], 1e-30f);
+        big = fmaxf(big, fmaxf(fabsf(lo[c]), fabsf(hi)));
+    }
+    int bits[3] = {0, 0, 0};
+    for (int t = 0; t < kSortBits; ++t) {
+        int a = 0;
+        float best = -1.f;
+        for (int c = 0; c < 3; ++c) {
+            const float side = ldexpf(ext[c], -bits[c]);
+            if (side > best) { best = side; a = c; }
+        }
+        ++bits[a];
+    }
+    for (int c = 0; c < 3; ++c) {
+        g->lo[c] = lo[c];
+        g->inv_h[c] = ldexpf(1.f, bits[c]) / ext[c];
+        g->bits[c] = bits[c];
+    }
+    const float d = ldexpf(big, -23 + 18);
+    g->far2 = d * d;
+}
+
+__device__ __forceinline__ unsigned sort_key(float4 h, const SortGrid &g)
+{
+    int q[3];
+    const float x[3] = {h.x, h.y, h.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int top = (1 << g.bits[c]) - 1;
+        q[c] = min(max((int)((x[c] - g.lo[c]) * g.inv_h[c]), 0), top);
+    }
+    unsigned key = 0;
+    for (int l = kSortBits - 1; l >= 0; --l)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (g.bits[c] > l) key = (key << 1) | ((q[c] >> l) & 1);
+    return key;
+}
+
+// tile b = blobs b T .. min(n, (b + 1) T) - 1: keys, and their counts per bucket
+// in row b of H
+__global__ void __launch_bounds__(1024) sort_hist_kernel(const float4 *__restrict__ hi, int64_t n,
+                                                         int64_t T, const SortGrid *__restrict__ grid,
+                                                         unsigned *__restrict__ key,
+                                                         int *__restrict__ H)
+{
+    extern __shared__ int hist[];
+    const SortGrid g = *grid;
+    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) hist[c] = 0;
+    __syncthreads();
+    const int64_t i0 = blockIdx.x * T, i1 = min(n, i0 + T);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const unsigned k = sort_key(hi[i], g);
+        key[i] = k;
+        atomicAdd(hist + k, 1);
+    }
+    __syncthreads();
+    int *row = H + blockIdx.x * (int64_t)kSortBuckets;
+    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) row[c] = hist[c];
+}
+
+// per bucket (one thread each): rows 0..tiles-1 of H become the exclusive
+// prefix over tiles, row `tiles` the bucket's total
+__global__ void __launch_bounds__(256) sort_tile_scan_kernel(int *__restrict__ H, int tiles)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int run = 0;
+    for (int b = 0; b < tiles; ++b) {
+        int *p = H + b * (int64_t)kSortBuckets + c;
+        const int t = *p;
+        *p = run;
+        run += t;
+    }
+    H[tiles * (int64_t)kSortBuckets + c] = run;
+}
+
+// exclusive scan of the 2^kSortBits counters in one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) sort_scan_kernel(int *__restrict__ count)
+{
+    constexpr int kPer = (1 << kSortBits) / 1024;
+    __shared__ int part[1024];
+    int v[kPer], s = 0;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        v[e] = count[threadIdx.x * kPer + e];
+        s += v[e];
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) {
+        count[threadIdx.x * kPer + e] = run;
+        run += v[e];
+    }
+}
+
+// perm[position] = blob.  Tile b's first position in bucket k is start[k] +
+// H[b][k]; warp 0 takes the tile's keys 32 at a time in index order, ranks
+// equal keys among its lanes (match), and advances the bucket's offset in
+// shared memory once per group.
+__global__ void __launch_bounds__(1024) sort_scatter_kernel(const unsigned *__restrict__ key,
+                                                            int64_t n, int64_t T,
+                                                            const int *__restrict__ H, int tiles,
+                                                            int *__restrict__ perm)
+{
+    extern __shared__ int off[];
+    unsigned *sk = (unsigned *)(off + kSortBuckets);
+    const int *row = H + blockIdx.x * (int64_t)kSortBuckets;
+    const int *start = H + tiles * (int64_t)kSortBuckets;
+    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) off[c] = start[c] + row[c];
+    const int64_t i0 = blockIdx.x * T, i1 = min(n, i0 + T);
+    for (int64_t c0 = i0; c0 < i1; c0 += kSortKeysSmem) {
+        const int m = (int)min((int64_t)kSortKeysSmem, i1 - c0);
+        __syncthreads();  // offsets written; warp 0 done with the previous round's keys
+        for (int e = threadIdx.x; e < m; e += blockDim.x) sk[e] = key[c0 + e];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const unsigned lane = threadIdx.x;
+            for (int e0 = 0; e0 < m; e0 += 32) {
+                const int e = e0 + (int)lane;
+                const bool ok = e < m;
+                const unsigned k = ok ? sk[e] : 0xffffffffu;  // no bucket has this key
+                const unsigned same = __match_any_sync(0xffffffffu, k);
+                const int pos = ok ? off[k] + __popc(same & ((1u << lane) - 1u)) : 0;
+                __syncwarp();
+                if (ok && lane == (unsigned)(__ffs(same) - 1)) off[k] += __popc(same);
+                __syncwarp();
+                if (ok) perm[pos] = (int)(c0 + e);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_pack_kernel(const int *__restrict__ perm, int64_t n,
+                                                        const float4 *__restrict__ hi,
+                                                        const float4 *__restrict__ lo,
+                                                        float4 *__restrict__ shi,
+                                                        float4 *__restrict__ slo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = perm[i];
+        shi[i] = hi[j];
+        slo[i] = lo[j];
+    }
+}
+
+// bounding box of block b (sorted blobs b * 2 kNT .. +2 kNT - 1), one CTA each
+__global__ void __launch_bounds__(256) sort_block_box_kernel(const float4 *__restrict__ shi,
+                                                             int64_t n, float *__restrict__ box)
+{
+    __shared__ float red[8][6];
+    const int64_t b = blockIdx.x;
+    float v[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
+    for (int64_t i = b * 2 * kNT + threadIdx.x; i < n && i < (b + 1) * 2 * kNT; i += blockDim.x) {
+        const float4 h = shi[i];
+        v[0] = fminf(v[0], h.x); v[1] = fminf(v[1], h.y); v[2] = fminf(v[2], h.z);
+        v[3] = fmaxf(v[3], h.x); v[4] = fmaxf(v[4], h.y); v[5] = fmaxf(v[5], h.z);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float t = __shfl_xor_sync(0xffffffffu, v[c], o);
+            v[c] = c < 3 ? fminf(v[c], t) : fmaxf(v[c], t);
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) red[threadIdx.x >> 5][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float r = red[0][threadIdx.x];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            r = threadIdx.x < 3 ? fminf(r, red[w][threadIdx.x]) : fmaxf(r, red[w][threadIdx.x]);
+        box[6 * b + threadIdx.x] = r;
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_gather_kernel(const int *__restrict__ perm, int64_t n,
+                                                          const double *__restrict__ f,
+                                                          double *__restrict__ fs)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = perm[i];
+        fs[3 * i] = f[3 * j];
+        fs[3 * i + 1] = f[3 * j + 1];
+        fs[3 * i + 2] = f[3 * j + 2];
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_scatter_u_kernel(const int *__restrict__ perm,
+                                                             int64_t n,
+                                                             const double *__restrict__ us,
+                                                             double *__restrict__ u)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = perm[i];
+        u[3 * j] = us[3 * i];
+        u[3 * j + 1] = us[3 * i + 1];
+        u[3 * j + 2] = us[3 * i + 2];
+    }
+}
+
+// The order of the packed positions (after pack_hilo_kernel), for N >= kSortMinN.
+mb_status sort_positions(mb_context *ctx, int64_t n, cudaStream_t s)
+{
+    const int64_t nb = ceil_div(n, 2 * kNT);
+    // tiles of at least 4,096 blobs, at most one per SM
+    const int tiles = (int)std::min<int64_t>(ceil_div(n, 4096), ctx->sm_count);
+    const int64_t T = ceil_div(n, tiles);
+    MB_TRY(ensure(ctx, ctx->sort_perm, sizeof(int) * (size_t)n, "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_key, sizeof(unsigned) * (size_t)n, "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_count, kSortHistSmem * (size_t)(tiles + 1), "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_hi, sizeof(float4) * (size_t)n, "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_lo, sizeof(float4) * (size_t)n, "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_box, sizeof(float) * 6 * (size_t)nb, "spatial order"));
+    MB_TRY(ensure(ctx, ctx->sort_grid, sizeof(SortGrid) + sizeof(unsigned) * 8, "spatial order"));
+    MB_CUDA_TRY(ctx, cudaFuncSetAttribute(sort_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSortHistSmem));
+    MB_CUDA_TRY(ctx, cudaFuncSetAttribute(sort_scatter_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSortScatterSmem));
+    SortGrid *grid = (SortGrid *)ctx->sort_grid.ptr;
+    unsigned *bbox = (unsigned *)((char *)ctx->sort_grid.ptr + sizeof(SortGrid));
+    const unsigned init[6] = {~0u, ~0u, ~0u, 0u, 0u, 0u};
+    MB_CUDA_TRY(ctx, cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    const float4 *hi = (const float4 *)ctx->pos_hi.ptr, *lo = (const float4 *)ctx->pos_lo.ptr;
+    int *H = (int *)ctx->sort_count.ptr;
+    unsigned *key = (unsigned *)ctx->sort_key.ptr;
+    const int g = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
+    sort_bbox_kernel<<<g, 256, 0, s>>>(hi, n, bbox);
+    sort_grid_kernel<<<1, 1, 0, s>>>(bbox, grid);
+    sort_hist_kernel<<<tiles, 1024, kSortHistSmem, s>>>(hi, n, T, grid, key, H);
+    sort_tile_scan_kernel<<<kSortBuckets / 256, 256, 0, s>>>(H, tiles);
+    sort_scan_kernel<<<1, 1024, 0, s>>>(H + tiles * (int64_t)kSortBuckets);
+    sort_scatter_kernel<<<tiles, 1024, kSortScatterSmem, s>>>(key, n, T, H, tiles,
+                                                              (int *)ctx->sort_perm.ptr);
+    sort_pack_kernel<<<g, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, hi, lo,
+                                       (float4 *)ctx->sort_hi.ptr, (float4 *)ctx->sort_lo.ptr);
+    sort_block_box_kernel<<<(int)nb, 256, 0, s>>>((const float4 *)ctx->sort_hi.ptr, n,
+                                                  (float *)ctx->sort_box.ptr);
+    count_launch(8);
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->sorted_n = n;
+    return MB_OK;
+}
+
 // One FP32 matvec with variant v (pair kernel + chunk reduction).
 mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, int wall,
                   double scale, double *u, cudaStream_t s, bool profile,
@@ -436,21 +785,42 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
         return MB_OK;
     }
     if (v == 3) {
-        // symmetric: zero u, then one launch over the block-pair triangle
+        // symmetric: zero u, then one launch over the block-pair triangle; in
+        // the spatial order when the packing made one (f gathered, u
+        // scattered back)
         const int64_t nb = ceil_div(n, 2 * kNT);
         const int64_t items = nb * (nb + 1) / 2;
         const int grid = (int)std::min<int64_t>(items, res);
-        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        const bool sorted = ctx->sorted_n == n;
+        const float4 *hi = (const float4 *)(sorted ? ctx->sort_hi.ptr : ctx->pos_hi.ptr);
+        const float4 *lo = (const float4 *)(sorted ? ctx->sort_lo.ptr : ctx->pos_lo.ptr);
+        const float *box = sorted ? (const float *)ctx->sort_box.ptr : nullptr;
+        const SortGrid *sg = sorted ? (const SortGrid *)ctx->sort_grid.ptr : nullptr;
+        const double *fk = f;
+        double *uk = u;
+        const int gv = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
+        if (sorted) {
+            MB_TRY(ensure(ctx, ctx->sort_f, sizeof(double) * 3 * (size_t)n, "sorted forces"));
+            MB_TRY(ensure(ctx, ctx->sort_u, sizeof(double) * 3 * (size_t)n, "sorted velocities"));
+            sort_gather_kernel<<<gv, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, f,
+                                                  (double *)ctx->sort_f.ptr);
+            count_launch();
+            fk = (const double *)ctx->sort_f.ptr;
+            uk = (double *)ctx->sort_u.ptr;
+        }
+        MB_CUDA_TRY(ctx, cudaMemsetAsync(uk, 0, sizeof(double) * 3 * (size_t)n, s));
         auto *ev = profile ? profile_begin(ctx, s) : nullptr;
-        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
-        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
         const PairConsts2 k = PairConsts2::make(a);
         if (wall)
-            pair_sym_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_sym_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk, scale, box, sg);
         else
-            pair_sym_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_sym_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk, scale, box, sg);
         profile_end(ev, s);
         count_launch();
+        if (sorted) {
+            sort_scatter_u_kernel<<<gv, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, uk, u);
+            count_launch();
+        }
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
     }
@@ -530,15 +900,18 @@ mb_status matvec_f32(mb_context *ctx, const double *f, int64_t n, double a, int 
     return f32_run(ctx, v, f, n, a, wall, scale, u, s, true, defer);
 }
 
-mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s)
+mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cudaStream_t s,
+                                bool order)
 {
     MB_TRY(ensure(ctx, ctx->pos_hi, sizeof(float4) * (size_t)n, "packed positions"));
     MB_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * (size_t)n, "packed positions"));
+    ctx->sorted_n = 0;
     const int grid = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
     pack_hilo_kernel<<<grid, 256, 0, s>>>(r, n, (float4 *)ctx->pos_hi.ptr,
                                           (float4 *)ctx->pos_lo.ptr);
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
+    if (order && n >= kSortMinN) MB_TRY(sort_positions(ctx, n, s));
     return MB_OK;
 }
 
@@ -689,7 +1062,7 @@ mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double
     if (prec != MB_FP32_KAHAN)
         return set_err(ctx, MB_EINVAL, "flow evaluation supports MB_FP32_KAHAN and MB_FP64");
     // sources packed into the context's position buffers, targets into the eval ones
-    MB_TRY(matvec_pack_positions(ctx, r, ns, s));
+    MB_TRY(matvec_pack_positions(ctx, r, ns, s, false));
     MB_TRY(ensure(ctx, ctx->eval_hi, sizeof(float4) * (size_t)nt, "packed targets"));
     MB_TRY(ensure(ctx, ctx->eval_lo, sizeof(float4) * (size_t)nt, "packed targets"));
     {

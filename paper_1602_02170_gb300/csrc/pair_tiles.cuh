@@ -180,7 +180,12 @@ __device__ __forceinline__ void f64_item(double *__restrict__ sm, const double *
 // and then to u with FP64 atomics.  Diagonal items (I == J) run forward only
 // over all ordered pairs.  u must be zeroed beforehand and receives
 // scale * M f.
-template <bool WALL, int NT>
+//
+// FAR (off-diagonal block pairs whose bounding boxes are farther apart than
+// both 2a and 2^18 ulp of the largest coordinate): the separations take the
+// hi parts alone, whose rounding then moves a separation by at most 2^-18 of
+// itself, and the overlap test is left out.
+template <bool WALL, int NT, bool FAR = false>
 __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__restrict__ sRev,
                                            const float4 *__restrict__ hi,
                                            const float4 *__restrict__ lo,
@@ -249,15 +254,23 @@ __device__ __forceinline__ void x2sym_item(float4 *__restrict__ sP, float *__res
                 for (int t = 0; t < 32; ++t) {
                     const int s = g * 32 + ((lane + t) & 31);
                     const float4 *P = sP + kX2SmemFloat4PerSource * s;
-                    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
-                    const float2 dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
-                    const float2 dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
-                    const float2 dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
+                    const float4 P0 = P[0], P1 = P[1], P3 = P[3], P4 = P[4];
+                    float2 dx, dy, dz;
+                    if (FAR) {
+                        dx = add2(xh, make_float2(P0.x, P0.y));
+                        dy = add2(yh, make_float2(P0.z, P0.w));
+                        dz = add2(zh, make_float2(P1.x, P1.y));
+                    } else {
+                        const float4 P2 = P[2];
+                        dx = add2(add2(xh, make_float2(P0.x, P0.y)), add2(xl, make_float2(P2.x, P2.y)));
+                        dy = add2(add2(yh, make_float2(P0.z, P0.w)), add2(yl, make_float2(P2.z, P2.w)));
+                        dz = add2(add2(zh, make_float2(P1.x, P1.y)), add2(zl, make_float2(P3.x, P3.y)));
+                    }
                     const float2 dxy2 = fma2(dy, dy, fma2(dx, dx, k.tiny));
-                    pair_sym2<WALL>(dx, dy, dz, dxy2, zh, make_float2(P1.z, P1.w),
-                                    make_float2(P3.z, P3.w), make_float2(P4.x, P4.y),
-                                    make_float2(P4.z, P4.w), fix, fiy, fiz, k, ax, ay, az, rx, ry,
-                                    rz);
+                    pair_sym2<WALL, FAR>(dx, dy, dz, dxy2, zh, make_float2(P1.z, P1.w),
+                                         make_float2(P3.z, P3.w), make_float2(P4.x, P4.y),
+                                         make_float2(P4.z, P4.w), fix, fiy, fiz, k, ax, ay, az, rx,
+                                         ry, rz);
                     // hand the accumulator to lane - 1, which meets this source next step
                     const int from = (lane + 1) & 31;
                     rx.x = __shfl_sync(0xffffffffu, rx.x, from);

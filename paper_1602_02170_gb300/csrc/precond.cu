@@ -19,6 +19,7 @@
 
 #include <cooperative_groups.h>
 
+#include "df32.cuh"
 #include "mb_internal.cuh"
 #include "rpy_wall.cuh"
 
@@ -1017,6 +1018,222 @@ __global__ void __launch_bounds__(256) pc_trinv_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// S3 and S4 in double-float for blocks of up to 4 kTile rows.  On this chip an
+// FP64 warp instruction issues about once per 19 SM cycles, so the
+// substitution chains of S3 (a few FP64 instructions per step, one step per
+// row) and the 32 x 32 x 32 tiles of S4 are bound by FP64 issue, not by
+// their arithmetic.  Double-float arithmetic (df32.cuh: about 46 bits, each
+// operation a few FP32 instructions) carries W = L^-1, Q = W^T G, Q N and
+// W^T W - (Q N) Q^T on the FP32 pipes instead; the Cholesky factor, G and N
+// come from the FP64 factorisation, and the stored inverse is FP64.  Its
+// entries then carry a relative error of about 1e-14 (a few double-float
+// roundings per step over n steps) instead of FP64 rounding: the
+// preconditioner changes the iteration count, not the solution, which the
+// flexible GMRES takes from true residuals.
+//
+// S2' converts, in place, the FP64 inputs of S3 to double-float pairs packed
+// in the same 8 bytes: the rows of L^T in P_p's upper triangle, and dW, G and
+// N in the scratch.
+__device__ __forceinline__ double df_pack(dfl v)
+{
+    return __hiloint2double(__float_as_int(v.hi), __float_as_int(v.lo));
+}
+
+__device__ __forceinline__ dfl df_unpack(double d)
+{
+    return dfl(__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d)));
+}
+
+__device__ __forceinline__ dfl df_of(double d)
+{
+    const float h = (float)d;
+    return dfl(h, (float)(d - (double)h));
+}
+
+__global__ void __launch_bounds__(256) pc_to_df_kernel(int64_t nb,
+                                                       const int64_t *__restrict__ start,
+                                                       const int64_t *__restrict__ poff,
+                                                       double *__restrict__ P, SplitScratch scr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t rows = nb * scr.nmax;
+    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); it < rows;
+         it += warps) {
+        const int64_t p = it / scr.nmax;
+        const int k = (int)(it % scr.nmax);
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        if (k >= n) continue;
+        double *Lk = P + poff[p] + (size_t)k * m;
+        for (int i = k + 1 + lane; i < n; i += 32) Lk[i] = df_pack(df_of(Lk[i]));
+        if (lane == 0) scr.dW(p)[k] = df_pack(df_of(scr.dW(p)[k]));
+        if (lane < 6) scr.G(p)[6 * k + lane] = df_pack(df_of(scr.G(p)[6 * k + lane]));
+        if (k == 0)
+            for (int e = lane; e < 36; e += 32) scr.N(p)[e] = df_pack(df_of(scr.N(p)[e]));
+    }
+}
+
+// S3 in double-float: warp per column c of W = L^-1, rows 32 t + lane in
+// registers, as pc_trinv_kernel; W, Q and Q N go to the scratch as packed
+// double-float, the border entries -Q N of P_p in FP64.  1 / L_kk travels
+// through the chain by shuffles from registers.  With STAGE (few bodies,
+// where the chain's latency is the time) the CTA first copies the packed
+// rows of L^T that its eight columns need (from its first column on) and
+// their rows of G into shared memory, so that no step of a chain waits on
+// L2; with many bodies the CTAs stay small and read them from L2.
+template <bool STAGE>
+__global__ void __launch_bounds__(256) pc_trinv_df_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int col_groups)
+{
+    constexpr int R = 4;
+    extern __shared__ double sLt[];  // rows cmin .. n-1 of L^T (packed), row stride n; then G
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
+        const int64_t p = item / col_groups;
+        const int cmin = (int)(item % col_groups) * nw;
+        const int c = cmin + warp;
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        // row k of L^T at Lk + (k - cmin) * ldl, row k of G at Gk + 6 (k - cmin)
+        const double *Lk = P + poff[p] + (size_t)cmin * m, *Gk = scr.G(p) + 6 * cmin;
+        int ldl = m;
+        if constexpr (STAGE) {
+            double *sG = sLt + (size_t)(n - cmin) * n;
+            __syncthreads();  // the previous item is finished with sLt
+            if (cmin < n) {
+                // batches of kBatch loads per thread in flight before their stores
+                constexpr int kBatch = 8;
+                const double *Lg = P + poff[p];
+                const int total = (n - cmin) * n;
+                for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * (int)blockDim.x) {
+                    double v[kBatch];
+#pragma unroll
+                    for (int b = 0; b < kBatch; ++b) {
+                        const int e = e0 + b * (int)blockDim.x;
+                        const int k = cmin + e / n, i = e % n;
+                        v[b] = e < total && i > k ? Lg[(size_t)k * m + i] : 0.0;
+                    }
+#pragma unroll
+                    for (int b = 0; b < kBatch; ++b) {
+                        const int e = e0 + b * (int)blockDim.x;
+                        if (e < total) sLt[e] = v[b];
+                    }
+                }
+                for (int e = threadIdx.x; e < 6 * (n - cmin); e += blockDim.x)
+                    sG[e] = scr.G(p)[6 * cmin + e];
+            }
+            __syncthreads();
+            Lk = sLt;
+            Gk = sG;
+            ldl = n;
+        }
+        if (c >= n) continue;  // warp-uniform
+        double *W = scr.W(p);
+        const double *dW = scr.dW(p), *Nm = scr.N(p);
+        const int ldw = scr.nmax;
+        dfl w[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) w[t] = dfl((32 * t + lane == c) ? 1.f : 0.f, 0.f);
+        // zero the rows of column c that the tiled product reads above the diagonal
+        for (int kk = (c & ~(kTile - 1)) + lane; kk < c; kk += 32) W[(size_t)kk * ldw + c] = 0.0;
+        dfl qa;  // lane b < 6: Q[c][b]
+        // 1 / L_kk of rows 32 t + lane in registers (passed by shuffles in the chain)
+        dfl dwr[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) dwr[t] = 32 * t + lane < n ? df_unpack(dW[32 * t + lane]) : dfl();
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (32 * t + 31 < c) continue;
+            if (32 * t >= n) break;
+            for (int l = 0; l < 32; ++l) {
+                const int k = 32 * t + l;
+                if (k < c) continue;
+                if (k >= n) break;
+                const dfl wl(__shfl_sync(0xffffffffu, w[t].hi, l), __shfl_sync(0xffffffffu, w[t].lo, l));
+                const dfl dk(__shfl_sync(0xffffffffu, dwr[t].hi, l), __shfl_sync(0xffffffffu, dwr[t].lo, l));
+                const dfl wk = wl * dk;
+                if (lane == l) W[(size_t)k * ldw + c] = df_pack(wk);
+                if (lane < 6) qa += wk * df_unpack(Gk[6 * (k - cmin) + lane]);
+                const double *lk = Lk + (size_t)(k - cmin) * ldl;
+#pragma unroll
+                for (int t2 = t; t2 < R; ++t2) {
+                    const int i = 32 * t2 + lane;
+                    if (i > k && i < n) w[t2] = w[t2] - df_unpack(lk[i]) * wk;
+                }
+            }
+        }
+        // QN[c][b] = sum_a Q[c][a] N[a][b]
+        dfl qn;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const dfl qv(__shfl_sync(0xffffffffu, qa.hi, a), __shfl_sync(0xffffffffu, qa.lo, a));
+            if (lane < 6) qn += qv * df_unpack(Nm[a * 6 + lane]);
+        }
+        if (lane < 6) {
+            scr.Q(p)[6 * c + lane] = df_pack(qa);
+            scr.QN(p)[6 * c + lane] = df_pack(qn);
+            const double v = -to_double(qn);
+            P[poff[p] + (size_t)c * m + n + lane] = v;
+            P[poff[p] + (size_t)(n + lane) * m + c] = v;
+        }
+    }
+}
+
+// S4 in double-float: P_p's n x n block = W^T W - (Q N) Q^T in 32 x 32 tiles
+// (as pc_product_kernel), the tiles of W staged in shared memory as
+// double-float, the result stored in FP64.
+__global__ void __launch_bounds__(256) pc_product_df_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int tiles_per_body, int schur)
+{
+    __shared__ dfl Wi[kTile][kTile + 1], Wj[kTile][kTile + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < nb * tiles_per_body; item += gridDim.x) {
+        const int64_t p = item / tiles_per_body;
+        int I, J;
+        tri_index((int)(item % tiles_per_body), I, J);
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        const int i0 = I * kTile, j0 = J * kTile;
+        if (i0 >= n) continue;  // CTA-uniform
+        const double *W = scr.W(p);
+        const int ldw = scr.nmax;
+        dfl acc[4];
+        for (int k0 = i0; k0 < n; k0 += kTile) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+                const int kk = e / kTile, cc = e % kTile;
+                const int k = k0 + kk;
+                Wi[kk][cc] = (k < n && i0 + cc < n) ? df_unpack(W[(size_t)k * ldw + i0 + cc]) : dfl();
+                Wj[kk][cc] = (k < n && j0 + cc < n) ? df_unpack(W[(size_t)k * ldw + j0 + cc]) : dfl();
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < kTile; ++kk) {
+                const dfl wj = Wj[kk][tx];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) acc[rr] += Wi[kk][ty + 8 * rr] * wj;
+            }
+        }
+        const double *Qs = scr.Q(p), *QN = scr.QN(p);
+        double *Pp = P + poff[p];
+        const int j = j0 + tx;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int i = i0 + ty + 8 * rr;
+            if (i >= n || j >= n || (I == J && j > i)) continue;
+            dfl v = acc[rr];
+            if (schur)
+#pragma unroll
+                for (int bb = 0; bb < 6; ++bb)
+                    v = v - df_unpack(QN[6 * i + bb]) * df_unpack(Qs[6 * j + bb]);
+            const double vd = to_double(v);
+            Pp[(size_t)i * m + j] = vd;
+            Pp[(size_t)j * m + i] = vd;
+        }
+    }
+}
+
 // S3 for larger blocks (3 n_p up to kSplitMaxRowsSmem): the same
 // substitution with the warp's column in shared memory instead of registers
 // (n doubles per warp); __syncwarp orders each step's update before the
@@ -1204,9 +1421,25 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
                                                   (int)tsm));
             pc_trinv_smem_kernel<<<gt, 32 * kTrinvSmemWarps, tsm, s>>>(ng, st, po, P, scr,
                                                                       col_groups);
-        } else if (nmax <= 128)
-            pc_trinv_kernel<4><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
-        else if (nmax <= 256)
+        } else if (nmax <= 4 * kTile) {
+            // double-float S3 and S4 (see pc_to_df_kernel)
+            const int gc = (int)std::min<int64_t>(ceil_div(ng * nmax, 8), 8 * (int64_t)ctx->sm_count);
+            pc_to_df_kernel<<<gc, 256, 0, s>>>(ng, st, po, P, scr);
+            if (ng < ctx->sm_count) {
+                const size_t tsm = sizeof(double) * (size_t)nmax * (nmax + 6);
+                MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_trinv_df_kernel<true>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)tsm));
+                pc_trinv_df_kernel<true><<<gt, 256, tsm, s>>>(ng, st, po, P, scr, col_groups);
+            } else {
+                pc_trinv_df_kernel<false><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+            }
+            const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
+            pc_product_df_kernel<<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles, schur);
+            count_launch(5);
+            MB_CUDA_TRY(ctx, cudaGetLastError());
+            continue;
+        } else if (nmax <= 256)
             pc_trinv_kernel<8><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
         else
             pc_trinv_kernel<16><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);

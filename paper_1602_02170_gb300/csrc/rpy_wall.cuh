@@ -305,7 +305,9 @@ __device__ __forceinline__ void pair_accumulate2(float2 dx, float2 dy, float2 dz
 // (rx, ry, rz).  The transpose reuses every coefficient; only
 // the roles of f3 and f4 swap.  Packed over two targets i as in
 // pair_accumulate2; fi* are the targets' forces.
-template <bool WALL>
+// FAR: the caller guarantees that no pair is closer than 2a (block pairs
+// whose bounding boxes are far apart), so the overlap test is left out.
+template <bool WALL, bool FAR = false>
 __device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float2 dxy2, float2 zt,
                                           float2 zj, float2 fx, float2 fy, float2 fz, float2 fix,
                                           float2 fiy, float2 fiz, const PairConsts2 &k, float2 &ux,
@@ -317,7 +319,7 @@ __device__ __forceinline__ void pair_sym2(float2 dx, float2 dy, float2 dz, float
     const float2 inv2 = mul2(inv, inv);
     float2 C = mul2(inv, fma2(k.c2, inv2, k.c1));
     float2 D = mul2(mul2(inv, inv2), fma2(k.c4, inv2, k.c3));
-    if (__any_sync(0xffffffffu, (r2.x < k.four_a2) | (r2.y < k.four_a2))) {
+    if (!FAR && __any_sync(0xffffffffu, (r2.x < k.four_a2) | (r2.y < k.four_a2))) {
         if (r2.x < k.four_a2) { C.x = 1.f - k.k1 * (r2.x * inv.x); D.x = k.k2 * inv.x; }
         if (r2.y < k.four_a2) { C.y = 1.f - k.k1 * (r2.y * inv.y); D.y = k.k2 * inv.y; }
     }

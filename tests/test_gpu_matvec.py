@@ -142,3 +142,36 @@ def test_matvec_empty_and_errors(ctx):
     assert ei.value.name == "MB_EINVAL"
     with pytest.raises(mb.MBError):
         ctx.mobility_matvec(r, r.cpu(), 0.5)
+
+
+@pytest.mark.parametrize("layout", ["monolayer", "line"])
+def test_symmetric_variant_spatial_order(ctx, layout):
+    """From 16,384 blobs the symmetric kernel runs in a spatial order (cells
+    of a grid in Morton order) and lets block pairs far apart skip the lo
+    parts of the separations and the overlap test.  Bodies of the monolayer
+    (clustered blobs, many overlapping pairs within a shell) and blobs spread
+    along one line (one axis takes every bit of the grid) both match the FP64
+    kernel over all rows and the oracle on sampled rows."""
+    if layout == "monolayer":
+        s = I.config_monolayer(13, n_bodies=120, box=200.0 * (120 / 4096.0) ** 0.5)
+        r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
+        a = s.a
+    else:
+        n = 18000
+        rng = np.random.default_rng(14)
+        r = np.stack([np.sort(rng.uniform(-500.0, 900.0, n)), rng.uniform(-1.0, 1.0, n),
+                      rng.uniform(0.6, 1.5, n)], axis=1)
+        a = 0.5
+    f = np.random.default_rng(15).standard_normal(r.shape)
+    assert r.shape[0] >= 16384
+    ctx.set_pair_variant(3)
+    try:
+        got = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp32"))
+    finally:
+        ctx.set_pair_variant(-1)
+    ref64 = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "fp64"))
+    assert rel_l2(got, ref64) <= TOL["fp32"]
+    rows = np.random.default_rng(16).choice(r.shape[0], 1500, replace=False)
+    ref = O.matvec(r, f, a, 1.0, True, targets=rows)
+    assert rel_l2(got[rows], ref) <= TOL["fp32"]
+    assert np.abs(got[rows] - ref).max() <= TOL["fp32"] * np.abs(ref).max()
