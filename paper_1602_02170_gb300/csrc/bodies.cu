@@ -11,19 +11,6 @@
 namespace mb {
 namespace {
 
-__device__ __forceinline__ int64_t body_of(const int64_t *__restrict__ start, int64_t nb, int64_t i)
-{
-    int64_t lo = 0, hi = nb;  // invariant: start[lo] <= i < start[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (start[mid] <= i)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 __global__ void blob_positions_kernel(int64_t nb, int64_t n, const double *__restrict__ q,
                                       const double *__restrict__ theta,
                                       const int64_t *__restrict__ start,

@@ -257,6 +257,75 @@ __device__ __forceinline__ double rsqrt_fp64(double d)
     return y * (1.5 - 0.5 * d * y * y);
 }
 
+// The saddle operator's rows around M x (Eq. saddle_M) from the pair
+// kernel's chunk partials, for the orthogonalisation to form w = A x itself
+// instead of a separate launch: partial == nullptr when w is already formed.
+struct SaddleIn {
+    const double *partial = nullptr;  // S chunk partials of M x_lambda, 3n each
+    int S = 0;
+    double scale = 0.0;
+    int64_t n = 0, nb = 0;
+    const double *r = nullptr, *q = nullptr;
+    const int64_t *start = nullptr;
+    const int *body = nullptr;  // body of every blob (else found by bisection)
+    const double *x = nullptr;  // [lambda; U]
+};
+
+// z_{j+1} = P^-1 v_{j+1} for the next step, formed by the orthogonalisation
+// once v_{j+1} is final: the explicit blocks in an FP32 copy (mixed
+// precision, whose inner iterations run in FP32), bodies dealt to the
+// cluster's CTAs, one warp per row.  P == nullptr: not formed here.
+struct PrecIn {
+    const float *P = nullptr;       // blocks at poff[p], (3 n_p + 6)^2 row-major
+    const int64_t *poff = nullptr;
+    const int64_t *start = nullptr;
+    int64_t n = 0, nb = 0;
+    double *z = nullptr;            // [lambda; U] layout, like v
+    size_t xoff = 0;                // byte offset of the staged input in shared memory
+};
+
+// Row e of w = A x: blob rows scale sum_s partial[s][e] - (K U)_e (one
+// thread each, rounded as saddle_rows_kernel); body rows -(K^T lambda)_p,c
+// (one warp each, lanes over the body's blobs).  Blob rows [b0, b1) are
+// this CTA's; body rows are dealt to the warps of the whole cluster.
+__device__ void saddle_rows_cluster(const SaddleIn &sd, double *__restrict__ w, int64_t b0,
+                                    int64_t b1, int rank)
+{
+    const int64_t m3 = 3 * sd.n;
+    for (int64_t e = b0 + threadIdx.x; e < b1 && e < m3; e += blockDim.x) {
+        double acc = 0.0;
+        for (int sc = 0; sc < sd.S; ++sc) acc += sd.partial[sc * m3 + e];
+        const int64_t i = e / 3;
+        const int c = (int)(e - 3 * i);
+        const int64_t p = sd.body ? (int64_t)sd.body[i] : body_of(sd.start, sd.nb, i);
+        const double dx = sd.r[3 * i] - sd.q[3 * p], dy = sd.r[3 * i + 1] - sd.q[3 * p + 1],
+                     dz = sd.r[3 * i + 2] - sd.q[3 * p + 2];
+        const double *u = sd.x + m3 + 6 * p;
+        const double v = c == 0 ? u[0] + (u[4] * dz - u[5] * dy)
+                       : c == 1 ? u[1] + (u[5] * dx - u[3] * dz)
+                                : u[2] + (u[3] * dy - u[4] * dx);
+        w[e] = __dsub_rn(__dmul_rn(sd.scale, acc), v);
+    }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t row = rank * nw + (threadIdx.x >> 5); row < 6 * sd.nb;
+         row += (int64_t)nw * kOrthCluster) {
+        const int64_t p = row / 6;
+        const int c = (int)(row - 6 * p);
+        const double qx = sd.q[3 * p], qy = sd.q[3 * p + 1], qz = sd.q[3 * p + 2];
+        double acc = 0.0;
+        for (int64_t i = sd.start[p] + lane; i < sd.start[p + 1]; i += 32) {
+            const double lx = sd.x[3 * i], ly = sd.x[3 * i + 1], lz = sd.x[3 * i + 2];
+            const double dx = sd.r[3 * i] - qx, dy = sd.r[3 * i + 1] - qy,
+                         dz = sd.r[3 * i + 2] - qz;
+            acc += c == 0 ? lx : c == 1 ? ly : c == 2 ? lz
+                 : c == 3 ? dy * lz - dz * ly : c == 4 ? dz * lx - dx * lz : dx * ly - dy * lx;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) w[m3 + row] = -acc;
+    }
+}
+
 // post (optional): mapped host memory [est, step count]; rank 0 writes the
 // residual estimate, then (after a system-scope fence) the incremented count
 // kept at *seq, so that the host can read the estimate without a stream
@@ -269,7 +338,7 @@ template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
     orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
                         double *__restrict__ post, unsigned long long *__restrict__ seq,
-                        int stage)
+                        int stage, SaddleIn sd, PrecIn pc)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -294,6 +363,12 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     const int64_t e0 = rank * per, e1 = e0 + per < L ? e0 + per : L;
     const int cnt = e1 > e0 ? (int)(e1 - e0) : 0;  // this CTA's slice length
     double *w = V + (int64_t)(j + 1) * L;
+    if (sd.partial) {
+        // w = A x from the pair kernel's partials; the cluster barrier orders
+        // the body rows (written by any CTA) before every CTA's reads of w
+        saddle_rows_cluster(sd, w, e0, e1, rank);
+        cluster.sync();
+    }
     // the Givens update's inputs from global memory, read up front into
     // red[16], red[17] (the norm uses red[0, nw))
     if (rank == 0) {
@@ -426,7 +501,45 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
     }
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = double(ld(j + 1, k)) * inv;
-    cluster.sync();  // no CTA exits while another still reads its partials
+    cluster.sync();  // no CTA exits while another still reads its partials; w is final
+    if (pc.P) {
+        float *x = (float *)((char *)buf + pc.xoff);
+        const int64_t n3 = 3 * pc.n;
+        for (int64_t p = rank; p < pc.nb; p += kOrthCluster) {
+            const int64_t b0 = pc.start[p];
+            const int np3 = 3 * (int)(pc.start[p + 1] - b0), mp = np3 + 6;
+            __syncthreads();  // the previous body's rows are done with x
+            for (int e = threadIdx.x; e < mp; e += blockDim.x)
+                x[e] = (float)(e < np3 ? w[3 * b0 + e] : w[n3 + 6 * p + (e - np3)]);
+            __syncthreads();
+            const float *Pp = pc.P + pc.poff[p];
+            for (int row = warp; row < mp; row += nw) {
+                const float *pr = Pp + (size_t)row * mp;
+                float acc = 0.f;
+                for (int c = lane; c < mp; c += 32) acc = fmaf(pr[c], x[c], acc);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0)
+                    pc.z[row < np3 ? 3 * b0 + row : n3 + 6 * p + (row - np3)] = (double)acc;
+            }
+        }
+    }
+}
+
+// body of every blob, for the small-system steps
+__global__ void body_map_kernel(const int64_t *__restrict__ start, int64_t nb, int64_t n,
+                                int *__restrict__ body)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        body[i] = (int)body_of(start, nb, i);
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ a, int64_t count, float *__restrict__ b)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
 }
 
 size_t orth_cluster_smem(int m) { return sizeof(double) * (8 * (size_t)m + 39); }
@@ -601,11 +714,20 @@ struct Solver {
     // y = A x with the pair kernel in precision `prec`.  When the pair
     // kernel leaves chunk partials, their reduction and both kinematic rows
     // run as one launch (saddle_rows_kernel) instead of three.
-    mb_status apply_A(const double *xin, double *y, mb_precision prec)
+    // keep (optional): when the rows are fused and the pair kernel left
+    // partials, launch nothing more and describe them there (the caller's
+    // next kernel forms y, see saddle_rows_cluster).
+    mb_status apply_A(const double *xin, double *y, mb_precision prec, SaddleIn *keep = nullptr)
     {
         MatvecPartials mp;
         const bool fuse = !shift && !resist && nb >= 1 && nb <= kSaddleRowsMaxBodies;
         MB_TRY(matvec_packed(ctx, r, xin, n, a, eta, wall, prec, y, s, fuse ? &mp : nullptr));
+        if (mp.S > 0 && keep) {
+            keep->partial = mp.partial; keep->S = mp.S; keep->scale = mp.scale;
+            keep->n = n; keep->nb = nb; keep->r = r; keep->q = q; keep->start = start;
+            keep->x = xin;
+            return MB_OK;
+        }
         if (mp.S > 0) {
             launch_saddle_rows(mp, n, nb, r, q, start, xin, y, s);
             MB_CUDA_TRY(ctx, cudaGetLastError());
@@ -935,17 +1057,20 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                     auto step = [&](cudaStream_t cs) -> mb_status {
                         S.s = cs;
                         S.precond(vj, zj, cs);
-                        const mb_status st = S.apply_A(zj, vn, inner);
+                        SaddleIn sd;
+                        const mb_status st = S.apply_A(zj, vn, inner, &sd);
                         S.s = s;
                         if (st != MB_OK) return st;
                         const size_t osm = orth_cluster_step_smem(m, L, j);
                         const int stage = orth_cluster_stage(L, j) ? 1 : 0;
                         if (inner == MB_FP32_KAHAN)
                             orth_cluster_kernel<float><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
+                                PrecIn{});
                         else
                             orth_cluster_kernel<double><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
+                                PrecIn{});
                         count_launch();
                         MB_CUDA_TRY(ctx, cudaGetLastError());
                         return MB_OK;

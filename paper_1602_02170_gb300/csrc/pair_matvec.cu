@@ -33,9 +33,53 @@ namespace {
 constexpr int kNT = MB_PAIR_NT;   // threads per CTA = sources per shared tile
 constexpr double kPi = 3.14159265358979323846;
 
-__global__ void pack_hilo_kernel(const double *__restrict__ r, int64_t n, float4 *__restrict__ hi,
-                                 float4 *__restrict__ lo)
+// Coordinates as unsigned integers in the order of the floats (for min/max).
+__device__ __forceinline__ unsigned float_order(float x)
 {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float order_float(unsigned u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Block-wide min of v[0..2] and max of v[3..5] (up to 32 warps; red holds
+// 6 x 32) into out[0..5]; every thread of the block must call it.
+__device__ __forceinline__ void minmax_block(unsigned (&v)[6], unsigned *red, unsigned *out)
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned t = __shfl_xor_sync(0xffffffffu, v[c], o);
+            v[c] = c < 3 ? min(v[c], t) : max(v[c], t);
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) red[6 * (threadIdx.x >> 5) + c] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        unsigned r = red[c];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            r = c < 3 ? min(r, red[6 * w + c]) : max(r, red[6 * w + c]);
+        out[c] = r;
+    }
+    __syncthreads();
+}
+
+// Positions split into FP32 hi and lo parts.  BOX: also the CTA's bounding
+// box of the hi parts (ordered integers: min x, y, z, max x, y, z) into
+// part[6 blockIdx.x ..], for the spatial order.
+template <bool BOX>
+__global__ void __launch_bounds__(256) pack_hilo_kernel(const double *__restrict__ r, int64_t n,
+                                                        float4 *__restrict__ hi,
+                                                        float4 *__restrict__ lo,
+                                                        unsigned *__restrict__ part)
+{
+    unsigned v[6] = {~0u, ~0u, ~0u, 0u, 0u, 0u};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double x = r[3 * i], y = r[3 * i + 1], z = r[3 * i + 2];
@@ -43,6 +87,19 @@ __global__ void pack_hilo_kernel(const double *__restrict__ r, int64_t n, float4
         hi[i] = make_float4(xh, yh, zh, 0.f);
         lo[i] = make_float4((float)(x - (double)xh), (float)(y - (double)yh),
                             (float)(z - (double)zh), 0.f);
+        if (BOX) {
+            const unsigned o[3] = {float_order(xh), float_order(yh), float_order(zh)};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = min(v[c], o[c]);
+                v[3 + c] = max(v[3 + c], o[c]);
+            }
+        }
+    }
+    if (BOX) {
+        __shared__ unsigned red[6 * 32], box[6];
+        minmax_block(v, red, box);
+        if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = box[threadIdx.x];
     }
 }
 
@@ -155,7 +212,7 @@ __global__ void __launch_bounds__(NT, NT == kNT ? (NP == 1 ? 3 : 2) : 16) pair_f
 // x2sym_item); such pairs take the FAR instance.
 struct SortGrid {
     float lo[3], inv_h[3];  // cell of x: (x - lo) * inv_h per axis
-    int bits[3];            // bits of the cell index per axis
+    int bits[3];            // bits of the cell index per axis (nbits in all)
     float far2;             // squared box distance of a far block pair
 };
 
@@ -433,59 +490,24 @@ void f32_launch(int v, const Plan &p, cudaStream_t s, const float4 *hi, const fl
 // order, and with it the FP32 rounding of every pair sum, is the same on
 // every call: a tile of consecutive blobs per CTA counts its keys in shared
 // memory, the counts are scanned over tiles and buckets, and one warp per
-// tile deals its blobs out in index order.
+// tile deals its blobs out in index order.  The grid has about N / 8 cells
+// (2^10 .. 2^kSortBits): blocks of 512 blobs span a few dozen cells, and the
+// per-tile count tables stay small.
 constexpr int64_t kSortMinN = 16384;
-constexpr int kSortBits = 15;
-constexpr int kSortBuckets = 1 << kSortBits;
+constexpr int kSortBits = 15;         // most cell bits
 constexpr int kSortKeysSmem = 16384;  // keys staged per round of the scatter
-constexpr size_t kSortHistSmem = sizeof(int) * kSortBuckets;
-constexpr size_t kSortScatterSmem = kSortHistSmem + sizeof(unsigned) * kSortKeysSmem;
 
-__device__ __forceinline__ unsigned float_order(float x)
+int sort_bits(int64_t n)
 {
-    const unsigned u = __float_as_uint(x);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    int b = 10;  // at least 1,024 buckets (sort_scan_kernel's granule)
+    while (b < kSortBits && ((int64_t)8 << b) < n) ++b;
+    return b;
 }
 
-__device__ __forceinline__ float order_float(unsigned u)
-{
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-
-// box[0..2] = ordered min, box[3..5] = ordered max (initialised to ~0 / 0)
-__global__ void __launch_bounds__(256) sort_bbox_kernel(const float4 *__restrict__ hi, int64_t n,
-                                                        unsigned *__restrict__ box)
-{
-    unsigned mn[3] = {~0u, ~0u, ~0u}, mx[3] = {0u, 0u, 0u};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 h = hi[i];
-        const unsigned v[3] = {float_order(h.x), float_order(h.y), float_order(h.z)};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            mn[c] = min(mn[c], v[c]);
-            mx[c] = max(mx[c], v[c]);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
-            mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
-        }
-    }
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            atomicMin(box + c, mn[c]);
-            atomicMax(box + 3 + c, mx[c]);
-        }
-}
-
-// The grid (bits per axis by repeatedly halving the longest cell side) and
-// the far distance: separations beyond 2^18 ulp of the largest coordinate.
-__global__ void sort_grid_kernel(const unsigned *__restrict__ box, SortGrid *__restrict__ g)
+// The grid from the bounding box (ordered integers, as pack_hilo_kernel's
+// partials): bits per axis by repeatedly halving the longest cell side, and
+// the far distance, separations beyond 2^18 ulp of the largest coordinate.
+__device__ void sort_grid_from_box(const unsigned *box, int nbits, SortGrid &g)
 {
     float lo[3], ext[3], big = 0.f;
     for (int c = 0; c < 3; ++c) {
@@ -495,7 +517,7 @@ __global__ void sort_grid_kernel(const unsigned *__restrict__ box, SortGrid *__r
         big = fmaxf(big, fmaxf(fabsf(lo[c]), fabsf(hi)));
     }
     int bits[3] = {0, 0, 0};
-    for (int t = 0; t < kSortBits; ++t) {
+    for (int t = 0; t < nbits; ++t) {
         int a = 0;
         float best = -1.f;
         for (int c = 0; c < 3; ++c) {
@@ -505,12 +527,12 @@ __global__ void sort_grid_kernel(const unsigned *__restrict__ box, SortGrid *__r
         ++bits[a];
     }
     for (int c = 0; c < 3; ++c) {
-        g->lo[c] = lo[c];
-        g->inv_h[c] = ldexpf(1.f, bits[c]) / ext[c];
-        g->bits[c] = bits[c];
+        g.lo[c] = lo[c];
+        g.inv_h[c] = ldexpf(1.f, bits[c]) / ext[c];
+        g.bits[c] = bits[c];
     }
     const float d = ldexpf(big, -23 + 18);
-    g->far2 = d * d;
+    g.far2 = d * d;
 }
 
 __device__ __forceinline__ unsigned sort_key(float4 h, const SortGrid &g)
@@ -531,16 +553,33 @@ __device__ __forceinline__ unsigned sort_key(float4 h, const SortGrid &g)
 }
 
 // tile b = blobs b T .. min(n, (b + 1) T) - 1: keys, and their counts per bucket
-// in row b of H
+// (B = 2^nbits) in row b of H.  Every CTA first reduces the nparts
+// bounding-box partials and forms the grid (CTA 0 also stores it for the
+// pair kernel).
 __global__ void __launch_bounds__(1024) sort_hist_kernel(const float4 *__restrict__ hi, int64_t n,
-                                                         int64_t T, const SortGrid *__restrict__ grid,
+                                                         int64_t T, const unsigned *__restrict__ part,
+                                                         int nparts, int nbits,
+                                                         SortGrid *__restrict__ grid,
                                                          unsigned *__restrict__ key,
                                                          int *__restrict__ H)
 {
     extern __shared__ int hist[];
-    const SortGrid g = *grid;
-    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) hist[c] = 0;
+    __shared__ unsigned red[6 * 32], box[6];
+    __shared__ SortGrid gs;
+    const int B = 1 << nbits;
+    unsigned v[6] = {~0u, ~0u, ~0u, 0u, 0u, 0u};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            v[c] = c < 3 ? min(v[c], part[6 * b + c]) : max(v[c], part[6 * b + c]);
+    minmax_block(v, red, box);
+    if (threadIdx.x == 0) {
+        sort_grid_from_box(box, nbits, gs);
+        if (blockIdx.x == 0) *grid = gs;
+    }
+    for (int c = threadIdx.x; c < B; c += blockDim.x) hist[c] = 0;
     __syncthreads();
+    const SortGrid g = gs;
     const int64_t i0 = blockIdx.x * T, i1 = min(n, i0 + T);
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const unsigned k = sort_key(hi[i], g);
@@ -548,50 +587,76 @@ __global__ void __launch_bounds__(1024) sort_hist_kernel(const float4 *__restric
         atomicAdd(hist + k, 1);
     }
     __syncthreads();
-    int *row = H + blockIdx.x * (int64_t)kSortBuckets;
-    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) row[c] = hist[c];
+    int *row = H + blockIdx.x * (int64_t)B;
+    for (int c = threadIdx.x; c < B; c += blockDim.x) row[c] = hist[c];
 }
 
 // per bucket (one thread each): rows 0..tiles-1 of H become the exclusive
-// prefix over tiles, row `tiles` the bucket's total
-__global__ void __launch_bounds__(256) sort_tile_scan_kernel(int *__restrict__ H, int tiles)
+// prefix over tiles, row `tiles` the bucket's total (the loads of up to 32
+// tiles in flight at once)
+__global__ void __launch_bounds__(256) sort_tile_scan_kernel(int *__restrict__ H, int tiles, int B)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B) return;
     int run = 0;
-    for (int b = 0; b < tiles; ++b) {
-        int *p = H + b * (int64_t)kSortBuckets + c;
-        const int t = *p;
-        *p = run;
-        run += t;
+    for (int b0 = 0; b0 < tiles; b0 += 32) {
+        int t[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) t[u] = b0 + u < tiles ? H[(b0 + u) * (int64_t)B + c] : 0;
+#pragma unroll
+        for (int u = 0; u < 32; ++u)
+            if (b0 + u < tiles) {
+                H[(b0 + u) * (int64_t)B + c] = run;
+                run += t[u];
+            }
     }
-    H[tiles * (int64_t)kSortBuckets + c] = run;
+    H[tiles * (int64_t)B + c] = run;
 }
 
-// exclusive scan of the 2^kSortBits counters in one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) sort_scan_kernel(int *__restrict__ count)
+// exclusive scan of the B counters in one CTA of 1024 threads: the counters
+// staged in shared memory (coalesced; one pad word per 32 so that thread t's
+// run of B / 1024 consecutive counters is free of bank conflicts), a
+// sequential sum per thread, a scan of the 1024 sums, the prefixes written
+// back through shared memory
+__device__ __forceinline__ int scan_pad(int e) { return e + (e >> 5); }
+
+__global__ void __launch_bounds__(1024) sort_scan_kernel(int *__restrict__ count, int B)
 {
-    constexpr int kPer = (1 << kSortBits) / 1024;
-    __shared__ int part[1024];
-    int v[kPer], s = 0;
-#pragma unroll
-    for (int e = 0; e < kPer; ++e) {
-        v[e] = count[threadIdx.x * kPer + e];
-        s += v[e];
-    }
-    part[threadIdx.x] = s;
+    extern __shared__ int sc[];
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = B >> 10;  // B is a power of two >= 1024
+    for (int e = threadIdx.x; e < B; e += 1024) sc[scan_pad(e)] = count[e];
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
-    }
-    int run = part[threadIdx.x] - s;
+    const int e0 = threadIdx.x * per;
+    int tot = 0;
+    for (int k = 0; k < per; ++k) tot += sc[scan_pad(e0 + k)];
+    int x = tot;  // inclusive scan of the per-thread sums
 #pragma unroll
-    for (int e = 0; e < kPer; ++e) {
-        count[threadIdx.x * kPer + e] = run;
-        run += v[e];
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
     }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int y = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        wsum[lane] = y;
+    }
+    __syncthreads();
+    int run = (warp > 0 ? wsum[warp - 1] : 0) + x - tot;
+    for (int k = 0; k < per; ++k) {
+        const int v = sc[scan_pad(e0 + k)];
+        sc[scan_pad(e0 + k)] = run;
+        run += v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B; e += 1024) count[e] = sc[scan_pad(e)];
 }
 
 // perm[position] = blob.  Tile b's first position in bucket k is start[k] +
@@ -601,13 +666,13 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(int *__restrict__ count
 __global__ void __launch_bounds__(1024) sort_scatter_kernel(const unsigned *__restrict__ key,
                                                             int64_t n, int64_t T,
                                                             const int *__restrict__ H, int tiles,
-                                                            int *__restrict__ perm)
+                                                            int B, int *__restrict__ perm)
 {
     extern __shared__ int off[];
-    unsigned *sk = (unsigned *)(off + kSortBuckets);
-    const int *row = H + blockIdx.x * (int64_t)kSortBuckets;
-    const int *start = H + tiles * (int64_t)kSortBuckets;
-    for (int c = threadIdx.x; c < kSortBuckets; c += blockDim.x) off[c] = start[c] + row[c];
+    unsigned *sk = (unsigned *)(off + B);
+    const int *row = H + blockIdx.x * (int64_t)B;
+    const int *start = H + tiles * (int64_t)B;
+    for (int c = threadIdx.x; c < B; c += blockDim.x) off[c] = start[c] + row[c];
     const int64_t i0 = blockIdx.x * T, i1 = min(n, i0 + T);
     for (int64_t c0 = i0; c0 < i1; c0 += kSortKeysSmem) {
         const int m = (int)min((int64_t)kSortKeysSmem, i1 - c0);
@@ -615,45 +680,49 @@ __global__ void __launch_bounds__(1024) sort_scatter_kernel(const unsigned *__re
         for (int e = threadIdx.x; e < m; e += blockDim.x) sk[e] = key[c0 + e];
         __syncthreads();
         if (threadIdx.x < 32) {
+            // the leader of each group of equal keys reads and advances the
+            // bucket's offset and hands the base to its group; the next
+            // chunk's key is loaded one round ahead
             const unsigned lane = threadIdx.x;
+            unsigned k_next = (int)lane < m ? sk[lane] : 0xffffffffu;  // no bucket has this key
             for (int e0 = 0; e0 < m; e0 += 32) {
                 const int e = e0 + (int)lane;
                 const bool ok = e < m;
-                const unsigned k = ok ? sk[e] : 0xffffffffu;  // no bucket has this key
+                const unsigned k = k_next;
+                k_next = e + 32 < m ? sk[e + 32] : 0xffffffffu;
                 const unsigned same = __match_any_sync(0xffffffffu, k);
-                const int pos = ok ? off[k] + __popc(same & ((1u << lane) - 1u)) : 0;
-                __syncwarp();
-                if (ok && lane == (unsigned)(__ffs(same) - 1)) off[k] += __popc(same);
-                __syncwarp();
-                if (ok) perm[pos] = (int)(c0 + e);
+                const int leader = __ffs(same) - 1;
+                int base = 0;
+                if (ok && (int)lane == leader) {
+                    base = off[k];
+                    off[k] = base + __popc(same);
+                }
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (ok) perm[base + __popc(same & ((1u << lane) - 1u))] = (int)(c0 + e);
+                __syncwarp();  // this round's offsets before the next round's reads
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(256) sort_pack_kernel(const int *__restrict__ perm, int64_t n,
-                                                        const float4 *__restrict__ hi,
-                                                        const float4 *__restrict__ lo,
-                                                        float4 *__restrict__ shi,
-                                                        float4 *__restrict__ slo)
+// Block b of the kernel (sorted positions b * 2 kNT .. + 2 kNT - 1), one CTA
+// each: the packed positions in the sorted order, and the block's bounding
+// box (min x, y, z, max x, y, z).
+__global__ void __launch_bounds__(256) sort_pack_box_kernel(const int *__restrict__ perm, int64_t n,
+                                                            const float4 *__restrict__ hi,
+                                                            const float4 *__restrict__ lo,
+                                                            float4 *__restrict__ shi,
+                                                            float4 *__restrict__ slo,
+                                                            float *__restrict__ box)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int j = perm[i];
-        shi[i] = hi[j];
-        slo[i] = lo[j];
-    }
-}
-
-// bounding box of block b (sorted blobs b * 2 kNT .. +2 kNT - 1), one CTA each
-__global__ void __launch_bounds__(256) sort_block_box_kernel(const float4 *__restrict__ shi,
-                                                             int64_t n, float *__restrict__ box)
-{
-    __shared__ float red[8][6];
+    __shared__ float red[32][6];
     const int64_t b = blockIdx.x;
     float v[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
     for (int64_t i = b * 2 * kNT + threadIdx.x; i < n && i < (b + 1) * 2 * kNT; i += blockDim.x) {
-        const float4 h = shi[i];
+        const int j = perm[i];
+        const float4 h = hi[j];
+        shi[i] = h;
+        slo[i] = lo[j];
         v[0] = fminf(v[0], h.x); v[1] = fminf(v[1], h.y); v[2] = fminf(v[2], h.z);
         v[3] = fmaxf(v[3], h.x); v[4] = fmaxf(v[4], h.y); v[5] = fmaxf(v[5], h.z);
     }
@@ -676,9 +745,12 @@ __global__ void __launch_bounds__(256) sort_block_box_kernel(const float4 *__res
     }
 }
 
+// f into the sorted order, and the sorted velocities zeroed (the pair
+// kernel adds into them)
 __global__ void __launch_bounds__(256) sort_gather_kernel(const int *__restrict__ perm, int64_t n,
                                                           const double *__restrict__ f,
-                                                          double *__restrict__ fs)
+                                                          double *__restrict__ fs,
+                                                          double *__restrict__ us)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -686,6 +758,9 @@ __global__ void __launch_bounds__(256) sort_gather_kernel(const int *__restrict_
         fs[3 * i] = f[3 * j];
         fs[3 * i + 1] = f[3 * j + 1];
         fs[3 * i + 2] = f[3 * j + 2];
+        us[3 * i] = 0.0;
+        us[3 * i + 1] = 0.0;
+        us[3 * i + 2] = 0.0;
     }
 }
 
@@ -703,45 +778,47 @@ __global__ void __launch_bounds__(256) sort_scatter_u_kernel(const int *__restri
     }
 }
 
-// The order of the packed positions (after pack_hilo_kernel), for N >= kSortMinN.
-mb_status sort_positions(mb_context *ctx, int64_t n, cudaStream_t s)
+// The order of the packed positions, for N >= kSortMinN: pack_hilo_kernel
+// has left nparts bounding-box partials in the sort_grid buffer (after the
+// SortGrid).
+mb_status sort_positions(mb_context *ctx, int64_t n, int nparts, cudaStream_t s)
 {
     const int64_t nb = ceil_div(n, 2 * kNT);
-    // tiles of at least 4,096 blobs, at most one per SM
-    const int tiles = (int)std::min<int64_t>(ceil_div(n, 4096), ctx->sm_count);
+    // tiles of at least 1,024 blobs, at most one per SM
+    const int tiles = (int)std::min<int64_t>(ceil_div(n, 1024), ctx->sm_count);
     const int64_t T = ceil_div(n, tiles);
     MB_TRY(ensure(ctx, ctx->sort_perm, sizeof(int) * (size_t)n, "spatial order"));
     MB_TRY(ensure(ctx, ctx->sort_key, sizeof(unsigned) * (size_t)n, "spatial order"));
-    MB_TRY(ensure(ctx, ctx->sort_count, kSortHistSmem * (size_t)(tiles + 1), "spatial order"));
+    const int nbits = sort_bits(n), B = 1 << nbits;
+    const size_t hist_smem = sizeof(int) * (size_t)B;
+    const size_t scan_smem = sizeof(int) * (size_t)(B + B / 32);
+    const size_t scatter_smem = hist_smem + sizeof(unsigned) * kSortKeysSmem;
+    MB_TRY(ensure(ctx, ctx->sort_count, hist_smem * (size_t)(tiles + 1), "spatial order"));
     MB_TRY(ensure(ctx, ctx->sort_hi, sizeof(float4) * (size_t)n, "spatial order"));
     MB_TRY(ensure(ctx, ctx->sort_lo, sizeof(float4) * (size_t)n, "spatial order"));
     MB_TRY(ensure(ctx, ctx->sort_box, sizeof(float) * 6 * (size_t)nb, "spatial order"));
-    MB_TRY(ensure(ctx, ctx->sort_grid, sizeof(SortGrid) + sizeof(unsigned) * 8, "spatial order"));
     MB_CUDA_TRY(ctx, cudaFuncSetAttribute(sort_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSortHistSmem));
+                                          (int)hist_smem));
+    MB_CUDA_TRY(ctx, cudaFuncSetAttribute(sort_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)scan_smem));
     MB_CUDA_TRY(ctx, cudaFuncSetAttribute(sort_scatter_kernel,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSortScatterSmem));
+                                          (int)scatter_smem));
     SortGrid *grid = (SortGrid *)ctx->sort_grid.ptr;
-    unsigned *bbox = (unsigned *)((char *)ctx->sort_grid.ptr + sizeof(SortGrid));
-    const unsigned init[6] = {~0u, ~0u, ~0u, 0u, 0u, 0u};
-    MB_CUDA_TRY(ctx, cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    const unsigned *part = (const unsigned *)((char *)ctx->sort_grid.ptr + sizeof(SortGrid));
     const float4 *hi = (const float4 *)ctx->pos_hi.ptr, *lo = (const float4 *)ctx->pos_lo.ptr;
     int *H = (int *)ctx->sort_count.ptr;
     unsigned *key = (unsigned *)ctx->sort_key.ptr;
-    const int g = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
-    sort_bbox_kernel<<<g, 256, 0, s>>>(hi, n, bbox);
-    sort_grid_kernel<<<1, 1, 0, s>>>(bbox, grid);
-    sort_hist_kernel<<<tiles, 1024, kSortHistSmem, s>>>(hi, n, T, grid, key, H);
-    sort_tile_scan_kernel<<<kSortBuckets / 256, 256, 0, s>>>(H, tiles);
-    sort_scan_kernel<<<1, 1024, 0, s>>>(H + tiles * (int64_t)kSortBuckets);
-    sort_scatter_kernel<<<tiles, 1024, kSortScatterSmem, s>>>(key, n, T, H, tiles,
-                                                              (int *)ctx->sort_perm.ptr);
-    sort_pack_kernel<<<g, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, hi, lo,
-                                       (float4 *)ctx->sort_hi.ptr, (float4 *)ctx->sort_lo.ptr);
-    sort_block_box_kernel<<<(int)nb, 256, 0, s>>>((const float4 *)ctx->sort_hi.ptr, n,
-                                                  (float *)ctx->sort_box.ptr);
-    count_launch(8);
+    sort_hist_kernel<<<tiles, 1024, hist_smem, s>>>(hi, n, T, part, nparts, nbits, grid, key, H);
+    sort_tile_scan_kernel<<<(B + 255) / 256, 256, 0, s>>>(H, tiles, B);
+    sort_scan_kernel<<<1, 1024, scan_smem, s>>>(H + tiles * (int64_t)B, B);
+    sort_scatter_kernel<<<tiles, 1024, scatter_smem, s>>>(key, n, T, H, tiles, B,
+                                                          (int *)ctx->sort_perm.ptr);
+    sort_pack_box_kernel<<<(int)nb, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, hi, lo,
+                                                 (float4 *)ctx->sort_hi.ptr,
+                                                 (float4 *)ctx->sort_lo.ptr,
+                                                 (float *)ctx->sort_box.ptr);
+    count_launch(5);
     MB_CUDA_TRY(ctx, cudaGetLastError());
     ctx->sorted_n = n;
     return MB_OK;
@@ -803,12 +880,14 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
             MB_TRY(ensure(ctx, ctx->sort_f, sizeof(double) * 3 * (size_t)n, "sorted forces"));
             MB_TRY(ensure(ctx, ctx->sort_u, sizeof(double) * 3 * (size_t)n, "sorted velocities"));
             sort_gather_kernel<<<gv, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, f,
-                                                  (double *)ctx->sort_f.ptr);
+                                                  (double *)ctx->sort_f.ptr,
+                                                  (double *)ctx->sort_u.ptr);
             count_launch();
             fk = (const double *)ctx->sort_f.ptr;
             uk = (double *)ctx->sort_u.ptr;
+        } else {
+            MB_CUDA_TRY(ctx, cudaMemsetAsync(uk, 0, sizeof(double) * 3 * (size_t)n, s));
         }
-        MB_CUDA_TRY(ctx, cudaMemsetAsync(uk, 0, sizeof(double) * 3 * (size_t)n, s));
         auto *ev = profile ? profile_begin(ctx, s) : nullptr;
         const PairConsts2 k = PairConsts2::make(a);
         if (wall)
@@ -907,11 +986,20 @@ mb_status matvec_pack_positions(mb_context *ctx, const double *r, int64_t n, cud
     MB_TRY(ensure(ctx, ctx->pos_lo, sizeof(float4) * (size_t)n, "packed positions"));
     ctx->sorted_n = 0;
     const int grid = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
-    pack_hilo_kernel<<<grid, 256, 0, s>>>(r, n, (float4 *)ctx->pos_hi.ptr,
-                                          (float4 *)ctx->pos_lo.ptr);
+    const bool sort = order && n >= kSortMinN;
+    if (sort) {
+        MB_TRY(ensure(ctx, ctx->sort_grid, sizeof(SortGrid) + sizeof(unsigned) * 6 * (size_t)grid,
+                      "spatial order"));
+        pack_hilo_kernel<true><<<grid, 256, 0, s>>>(
+            r, n, (float4 *)ctx->pos_hi.ptr, (float4 *)ctx->pos_lo.ptr,
+            (unsigned *)((char *)ctx->sort_grid.ptr + sizeof(SortGrid)));
+    } else {
+        pack_hilo_kernel<false><<<grid, 256, 0, s>>>(r, n, (float4 *)ctx->pos_hi.ptr,
+                                                     (float4 *)ctx->pos_lo.ptr, nullptr);
+    }
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
-    if (order && n >= kSortMinN) MB_TRY(sort_positions(ctx, n, s));
+    if (sort) MB_TRY(sort_positions(ctx, n, grid, s));
     return MB_OK;
 }
 
@@ -1067,8 +1155,8 @@ mb_status matvec_eval(mb_context *ctx, const double *x, int64_t nt, const double
     MB_TRY(ensure(ctx, ctx->eval_lo, sizeof(float4) * (size_t)nt, "packed targets"));
     {
         const int grid = (int)std::min<int64_t>(ceil_div(nt, 256), 8 * (int64_t)ctx->sm_count);
-        pack_hilo_kernel<<<grid, 256, 0, s>>>(x, nt, (float4 *)ctx->eval_hi.ptr,
-                                              (float4 *)ctx->eval_lo.ptr);
+        pack_hilo_kernel<false><<<grid, 256, 0, s>>>(x, nt, (float4 *)ctx->eval_hi.ptr,
+                                                     (float4 *)ctx->eval_lo.ptr, nullptr);
         count_launch();
     }
     const int res = wall ? resident_ctas(ctx, eval_f32x2_kernel<true>)
@@ -1237,7 +1325,7 @@ extern "C" mb_status mb_mobility_matvec_noalloc(const double *r, const double *f
     double *partial = (double *)(d->scratch + 2 * kNoallocPosBytes);
     const double scale = 1.0 / (6.0 * kPi * eta * a);
     const int grid_pack = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
-    pack_hilo_kernel<<<grid_pack, 256, 0, s>>>(r, n, hi, lo);
+    pack_hilo_kernel<false><<<grid_pack, 256, 0, s>>>(r, n, hi, lo, nullptr);
     count_launch();
     const Plan p = make_plan(n, kNT * kTPT, wall ? d->resident_wall : d->resident_free,
                              kNoallocMaxChunks);
