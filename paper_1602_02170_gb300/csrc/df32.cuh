@@ -4,8 +4,8 @@
 // Knuth's two-sum (the exact rounding error of a + b), the fast two-sum of
 // Dekker for |a| >= |b|, and the exact product error of a * b obtained with a
 // fused multiply-add.  The reciprocal square root takes the FP32 estimate and
-// one Newton step y <- y + y (1 - x y^2) / 2 evaluated in double-float, which
-// doubles the number of correct bits.
+// one Newton step y <- y + y (1 - x y^2) / 2, with the residual 1 - x y^2
+// formed from exact products, which doubles the number of correct bits.
 //
 // GB300 runs FP64 at a small fraction of its FP32 rate; the pair kernel in
 // double-float reaches FP64-class accuracy for the refinement residuals of
@@ -127,10 +127,22 @@ __device__ __forceinline__ dfl mb_rsqrt(dfl x)
 {
     x = fast_two_sum(x.hi, x.lo);  // the FP32 estimate needs the normalised hi
     const float y0 = rsqrtf(x.hi);
-    // r = 1 - x y0^2, small; y = y0 + y0 r / 2 (y0 has no low part)
-    const dfl r = dfl(1.0) - x * sqf(y0);
-    return addf(mulf(r, 0.5f * y0), y0);
+    // r = 1 - x y0^2 (about 2^-22) to FP32 accuracy: y0^2 = s + t exactly,
+    // x_hi s = p + e exactly, and 1 - p is exact (p is within 2^-21 of 1)
+    const float s = y0 * y0, t = fmaf(y0, y0, -s);
+    const float p = x.hi * s, e = fmaf(x.hi, s, -p);
+    const float r = ((1.f - p) - e) - fmaf(x.hi, t, x.lo * s);
+    // y = y0 + y0 r / 2
+    return fast_two_sum(y0, (0.5f * y0) * r);
 }
+
+// Accumulation without renormalisation (the sloppy addition): for running
+// sums that are renormalised, or converted to double, within a few dozen
+// terms, so that lo stays within a few dozen ulp of hi.
+__device__ __forceinline__ void acc_add(dfl &a, dfl b) { a = a + b; }
+__device__ __forceinline__ void acc_add(float &a, float b) { a += b; }
+__device__ __forceinline__ void acc_add(double &a, double b) { a += b; }
+__device__ __forceinline__ void renorm(dfl &a) { a = fast_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 

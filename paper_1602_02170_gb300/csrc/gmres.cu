@@ -271,19 +271,6 @@ struct SaddleIn {
     const double *x = nullptr;  // [lambda; U]
 };
 
-// z_{j+1} = P^-1 v_{j+1} for the next step, formed by the orthogonalisation
-// once v_{j+1} is final: the explicit blocks in an FP32 copy (mixed
-// precision, whose inner iterations run in FP32), bodies dealt to the
-// cluster's CTAs, one warp per row.  P == nullptr: not formed here.
-struct PrecIn {
-    const float *P = nullptr;       // blocks at poff[p], (3 n_p + 6)^2 row-major
-    const int64_t *poff = nullptr;
-    const int64_t *start = nullptr;
-    int64_t n = 0, nb = 0;
-    double *z = nullptr;            // [lambda; U] layout, like v
-    size_t xoff = 0;                // byte offset of the staged input in shared memory
-};
-
 // Row e of w = A x: blob rows scale sum_s partial[s][e] - (K U)_e (one
 // thread each, rounded as saddle_rows_kernel); body rows -(K^T lambda)_p,c
 // (one warp each, lanes over the body's blobs).  Blob rows [b0, b1) are
@@ -338,7 +325,7 @@ template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
     orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
                         double *__restrict__ post, unsigned long long *__restrict__ seq,
-                        int stage, SaddleIn sd, PrecIn pc)
+                        int stage, SaddleIn sd)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -502,28 +489,6 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     }
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = double(ld(j + 1, k)) * inv;
     cluster.sync();  // no CTA exits while another still reads its partials; w is final
-    if (pc.P) {
-        float *x = (float *)((char *)buf + pc.xoff);
-        const int64_t n3 = 3 * pc.n;
-        for (int64_t p = rank; p < pc.nb; p += kOrthCluster) {
-            const int64_t b0 = pc.start[p];
-            const int np3 = 3 * (int)(pc.start[p + 1] - b0), mp = np3 + 6;
-            __syncthreads();  // the previous body's rows are done with x
-            for (int e = threadIdx.x; e < mp; e += blockDim.x)
-                x[e] = (float)(e < np3 ? w[3 * b0 + e] : w[n3 + 6 * p + (e - np3)]);
-            __syncthreads();
-            const float *Pp = pc.P + pc.poff[p];
-            for (int row = warp; row < mp; row += nw) {
-                const float *pr = Pp + (size_t)row * mp;
-                float acc = 0.f;
-                for (int c = lane; c < mp; c += 32) acc = fmaf(pr[c], x[c], acc);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0)
-                    pc.z[row < np3 ? 3 * b0 + row : n3 + 6 * p + (row - np3)] = (double)acc;
-            }
-        }
-    }
 }
 
 // body of every blob, for the small-system steps
@@ -535,12 +500,6 @@ __global__ void body_map_kernel(const int64_t *__restrict__ start, int64_t nb, i
         body[i] = (int)body_of(start, nb, i);
 }
 
-__global__ void to_f32_kernel(const double *__restrict__ a, int64_t count, float *__restrict__ b)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
-         e += (int64_t)gridDim.x * blockDim.x)
-        b[e] = (float)a[e];
-}
 
 size_t orth_cluster_smem(int m) { return sizeof(double) * (8 * (size_t)m + 39); }
 
@@ -977,6 +936,16 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     const mb_precision inner = inner_precision(p->prec);
     const mb_precision outer = outer_precision(p->prec);
     const int vg = vec_grid(L);
+    // small systems: the body of every blob, for the saddle rows formed in the
+    // orthogonalisation
+    const int *body_map = nullptr;
+    if (L <= kOrthSmallMax && !resist) {
+        MB_TRY(ensure(ctx, ctx->sol_body, sizeof(int) * (size_t)n, "blob bodies"));
+        body_map_kernel<<<vec_grid(n), 256, 0, s>>>(S.start, nb, n, (int *)ctx->sol_body.ptr);
+        count_launch();
+        MB_CUDA_TRY(ctx, cudaGetLastError());
+        body_map = (const int *)ctx->sol_body.ptr;
+    }
     if (L <= kOrthSmallMax) {
         // a step that stages its slices may need more than 48 KB of shared memory
         const int smax = (int)(orth_cluster_smem(m) + sizeof(double) * kOrthStageDoubles);
@@ -1061,16 +1030,15 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         const mb_status st = S.apply_A(zj, vn, inner, &sd);
                         S.s = s;
                         if (st != MB_OK) return st;
+                        sd.body = body_map;
                         const size_t osm = orth_cluster_step_smem(m, L, j);
                         const int stage = orth_cluster_stage(L, j) ? 1 : 0;
                         if (inner == MB_FP32_KAHAN)
                             orth_cluster_kernel<float><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
-                                PrecIn{});
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd);
                         else
                             orth_cluster_kernel<double><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
-                                PrecIn{});
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd);
                         count_launch();
                         MB_CUDA_TRY(ctx, cudaGetLastError());
                         return MB_OK;

@@ -29,7 +29,7 @@ struct DevBuf {
 struct IterSig {
     uint64_t gen = 0;
     int j = -1, m = 0, inner = 0, wall = 0, variant = 0, pc_max_np = 0, pc_kind = 0, mode = 0,
-        pc_factored = 0, pc_fused = 0;
+        pc_factored = 0;
     const void *shift = nullptr;
     int64_t n = 0, nb = 0, L = 0, pc_nb = 0;
     double a = 0.0, eta = 0.0;
@@ -38,8 +38,7 @@ struct IterSig {
     {
         return gen == o.gen && j == o.j && m == o.m && inner == o.inner && wall == o.wall &&
                variant == o.variant && pc_max_np == o.pc_max_np && pc_kind == o.pc_kind &&
-               mode == o.mode && pc_factored == o.pc_factored && pc_fused == o.pc_fused &&
-               shift == o.shift &&
+               mode == o.mode && pc_factored == o.pc_factored && shift == o.shift &&
                n == o.n && nb == o.nb &&
                L == o.L && pc_nb == o.pc_nb && a == o.a && eta == o.eta && q == o.q &&
                V == o.V && Z == o.Z && sm == o.sm;
@@ -98,7 +97,6 @@ struct mb_context {
     int pc_factored = 0;         // 1: blocks hold L, G = L^-1 K and -N (applied by
                                  // triangular solves), 0: explicit inverses
     int64_t pc_shapes = 0;       // shared kind: distinct shapes
-    int64_t pc_doubles = 0;      // doubles of pinv in use (explicit wall blocks)
 
     // solver workspace
     mb::DevBuf sol_r;            // blob positions
@@ -107,7 +105,6 @@ struct mb_context {
     mb::DevBuf sol_dx, sol_ym;   // mixed precision: cycle correction, running M lambda
     mb::DevBuf sol_small;        // Hessenberg, Givens, dots (doubles)
     mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
-    mb::DevBuf sol_pc32;         // FP32 copy of small explicit blocks (mixed precision)
     mb::DevBuf sol_body;         // int body of every blob (small-system steps)
     mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)
     void *host_small = nullptr;  // pinned host mirror of small scalars

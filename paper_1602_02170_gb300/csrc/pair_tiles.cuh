@@ -357,12 +357,12 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
     const T rb_xy = dx * gx + dy * gy;
     const T gb = D * (rb_xy + dz * gz);
     if (!WALL) {
-        ux += C * fx + g * dx;
-        uy += C * fy + g * dy;
-        uz += C * fz + g * dz;
-        vx += C * gx + gb * dx;
-        vy += C * gy + gb * dy;
-        vz += C * gz + gb * dz;
+        acc_add(ux, C * fx + g * dx);
+        acc_add(uy, C * fy + g * dy);
+        acc_add(uz, C * fz + g * dz);
+        acc_add(vx, C * gx + gb * dx);
+        acc_add(vy, C * gy + gb * dy);
+        acc_add(vz, C * gz + gb * dz);
         return;
     }
     constexpr T third(1.0 / 3.0);
@@ -398,17 +398,17 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
     const T gw = A2 * RF + A3 * fz;
     const T kz = A4 * RF + f5 * fz;
     const T Gx = g + s * gw;
-    ux += Cx * fx + Gx * dx;
-    uy += Cx * fy + Gx * dy;
-    uz += Cx * fz + g * dz + s * (gw * R3 + kz);
+    acc_add(ux, Cx * fx + Gx * dx);
+    acc_add(uy, Cx * fy + Gx * dy);
+    acc_add(uz, Cx * fz + g * dz + s * (gw * R3 + kz));
     // reverse: M_ij^T f_i (f3 and f4 exchange roles)
     const T RB = rb_xy + R3 * gz;
     const T gwb = A2 * RB + A4 * gz;
     const T kzb = A3 * RB + f5 * gz;
     const T Gb = gb + s * gwb;
-    vx += Cx * gx + Gb * dx;
-    vy += Cx * gy + Gb * dy;
-    vz += Cx * gz + gb * dz + s * (gwb * R3 + kzb);
+    acc_add(vx, Cx * gx + Gb * dx);
+    acc_add(vy, Cx * gy + Gb * dy);
+    acc_add(vz, Cx * gz + gb * dz + s * (gwb * R3 + kzb));
 }
 
 // Symmetric double-float item over block pair (I, J), I <= J, blocks of NT
@@ -483,6 +483,10 @@ __device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__re
             atomicAdd(o3, to_double(vx));
             atomicAdd(o3 + 1, to_double(vy));
             atomicAdd(o3 + 2, to_double(vz));
+            // the forward sums take sloppy additions: renormalised every 32 terms
+            renorm(ux);
+            renorm(uy);
+            renorm(uz);
         }
         __syncthreads();
         const int64_t j = j0 + threadIdx.x;

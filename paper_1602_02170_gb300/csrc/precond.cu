@@ -1600,7 +1600,6 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     ctx->pc_nb = nb;
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
-    ctx->pc_doubles = off[nb];
     ctx->pc_kind = MB_PRECOND_WALL;
     ctx->pc_shapes = 0;
     ctx->pc_schur = schur;
@@ -1758,7 +1757,6 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
     ctx->pc_kind = MB_PRECOND_FREE_SHARED;
-    ctx->pc_doubles = 0;
     ctx->pc_factored = 0;
     ctx->pc_shapes = ns;
     ctx->pc_schur = schur;
