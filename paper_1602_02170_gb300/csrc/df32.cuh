@@ -145,5 +145,6 @@ __device__ __forceinline__ void acc_add(double &a, double b) { a += b; }
 __device__ __forceinline__ void renorm(dfl &a) { a = fast_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ float hi_part(dfl a) { return a.hi; }
 
 }  // namespace mb

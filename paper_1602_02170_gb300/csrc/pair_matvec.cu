@@ -348,14 +348,18 @@ __global__ void refine_blobs_kernel(const double *__restrict__ r, const double *
     }
 }
 
+// box (optional, spatial order): the bounding boxes of the sort's blocks of
+// 2 kNT blobs (two blocks of this kernel each); block pairs whose boxes are
+// 64 a or more apart take the FAR instance of the item.
 template <bool WALL, int NT = kNT>
 __global__ void __launch_bounds__(NT) pair_df_kernel(
     const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
     int64_t n, int64_t nb, int64_t n_items, PairConsts<dfl> k, double *__restrict__ u,
-    double scale)
+    double scale, const float *__restrict__ box, float far2)
 {
     __shared__ float4 sD[3 * NT];
     __shared__ double sRev[3 * NT];
+    constexpr int kPer = 2 * kNT / NT;  // this kernel's blocks per box
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         int64_t lo_r = 0, hi_r = nb;
         while (hi_r - lo_r > 1) {
@@ -364,7 +368,19 @@ __global__ void __launch_bounds__(NT) pair_df_kernel(
             else hi_r = mid;
         }
         const int64_t I = lo_r, J = I + (item - (I * nb - I * (I - 1) / 2));
-        dfsym_item<WALL, NT>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
+        bool far = false;
+        if (box && I / kPer != J / kPer) {
+            const float *bi = box + 6 * (I / kPer), *bj = box + 6 * (J / kPer);
+            float d2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float g = fmaxf(fmaxf(bj[c] - bi[3 + c], bi[c] - bj[3 + c]), 0.f);
+                d2 = fmaf(g, g, d2);
+            }
+            far = d2 > far2;  // the same in every thread
+        }
+        if (far) dfsym_item<WALL, NT, true>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
+        else dfsym_item<WALL, NT, false>(sD, sRev, hi, lo, f, n, I, J, k, u, scale);
     }
 }
 
@@ -1022,21 +1038,48 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         const int64_t nb = ceil_div(n, nt);
         const int64_t items = nb * (nb + 1) / 2;
         const int grid = (int)std::min<int64_t>(items, res);
-        MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        // in the spatial order when the packing made one (f gathered, u
+        // scattered back): far block pairs take the cheaper FAR item
+        const bool sorted = !small && ctx->sorted_n == n;
+        const float4 *hi = (const float4 *)(sorted ? ctx->sort_hi.ptr : ctx->pos_hi.ptr);
+        const float4 *lo = (const float4 *)(sorted ? ctx->sort_lo.ptr : ctx->pos_lo.ptr);
+        const float *box = sorted ? (const float *)ctx->sort_box.ptr : nullptr;
+        const float dfar = (float)(64.0 * a);
+        const double *fk = f;
+        double *uk = u;
+        const int gv = (int)std::min<int64_t>(ceil_div(n, 256), 8 * (int64_t)ctx->sm_count);
+        if (sorted) {
+            MB_TRY(ensure(ctx, ctx->sort_f, sizeof(double) * 3 * (size_t)n, "sorted forces"));
+            MB_TRY(ensure(ctx, ctx->sort_u, sizeof(double) * 3 * (size_t)n, "sorted velocities"));
+            sort_gather_kernel<<<gv, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, f,
+                                                  (double *)ctx->sort_f.ptr,
+                                                  (double *)ctx->sort_u.ptr);
+            count_launch();
+            fk = (const double *)ctx->sort_f.ptr;
+            uk = (double *)ctx->sort_u.ptr;
+        } else {
+            MB_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(double) * 3 * (size_t)n, s));
+        }
         auto *ev = profile_begin(ctx, s);
-        const float4 *hi = (const float4 *)ctx->pos_hi.ptr;
-        const float4 *lo = (const float4 *)ctx->pos_lo.ptr;
         const PairConsts<dfl> k = PairConsts<dfl>::make(a);
         if (small && wall)
-            pair_df_kernel<true, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_df_kernel<true, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk,
+                                                                    scale, nullptr, 0.f);
         else if (small)
-            pair_df_kernel<false, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_df_kernel<false, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, fk, n, nb, items, k,
+                                                                     uk, scale, nullptr, 0.f);
         else if (wall)
-            pair_df_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_df_kernel<true><<<grid, kNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk, scale, box,
+                                                      dfar * dfar);
         else
-            pair_df_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, f, n, nb, items, k, u, scale);
+            pair_df_kernel<false><<<grid, kNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk, scale, box,
+                                                       dfar * dfar);
         profile_end(ev, s);
         count_launch();
+        if (sorted) {
+            sort_scatter_u_kernel<<<gv, 256, 0, s>>>((const int *)ctx->sort_perm.ptr, n, uk, u);
+            count_launch();
+        }
         MB_CUDA_TRY(ctx, cudaGetLastError());
         return MB_OK;
     }

@@ -337,7 +337,13 @@ __device__ __forceinline__ double addf(double a, float c) { return a + (double)c
 // t2 (20E - 4) + t4 (40/3 - 140E/3) - 12p, equals 20 t4 / 3 - 2 (f2 + 1)),
 // and f2 / rho^2, f3 / rho, f4 / rho formed once for both directions as in
 // pair_sym2.
-template <bool WALL, typename T>
+//
+// FAR (double-float, block pairs whose boxes are at least 64 a apart, so
+// that t4 = (a / rho)^4 < 2^-24 and no pair overlaps): the terms carrying t4
+// are summed in FP32 and added to the double-float rest once per
+// polynomial; their rounding is then below 2^-24 t4 of the polynomial,
+// under the double-float rounding of the other terms.
+template <bool WALL, typename T, bool FAR = false>
 __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, T fy, T fz, T gx,
                                             T gy, T gz, const PairConsts<T> &k, T &ux, T &uy,
                                             T &uz, T &vx, T &vy, T &vz)
@@ -348,7 +354,7 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
     const T inv2 = inv * inv;
     T C = inv * (k.c1 + k.c2 * inv2);
     T D = inv * inv2 * (k.c3 + k.c4 * inv2);
-    if (r2 < k.four_a2) {
+    if (!FAR && r2 < k.four_a2) {
         C = T(1) - k.k1 * (r2 * inv);
         D = k.k2 * inv;
     }
@@ -374,20 +380,32 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
     const T e3 = hs + ht;
     const T E = e3 * e3;
     const T t2 = k.a2 * invR2;
-    const T t4 = t2 * t2;
     const T p = hs * ht;
     const T T1 = E * t2;
-    const T t4_3 = t4 * third;
     const T t2_3 = t2 * third;
-    const T T2_3 = E * t4_3;
     const T hs2 = mul_pow2(hs, 2.f);
-    const T f1 = addf(mul_pow2(T1 + (-p) + t4_3 + (-t2_3), 2.f) + mulf(T2_3, -10.f), -1.f);
-    const T F2 = mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f) +
-                 mulf(mulf(T2_3, 7.f) + (-t4_3), 10.f);
+    T f1, F2, f3, f4, f5;
+    if constexpr (FAR) {
+        // the t4 terms in FP32 (t4 / 3, E t4 / 3 from the high parts)
+        const float t4_3f = hi_part(t2) * hi_part(t2) * (1.f / 3.f);
+        const float T2_3f = hi_part(E) * t4_3f, e3t4_3f = hi_part(e3) * t4_3f;
+        f1 = addf(addf(mul_pow2(T1 + (-p) + (-t2_3), 2.f), -1.f), 2.f * t4_3f - 10.f * T2_3f);
+        F2 = addf(mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f), 10.f * (7.f * T2_3f - t4_3f));
+        f3 = addf(hs2 + e3 * mul_pow2(F2, -2.f), 20.f * e3t4_3f);
+        f4 = addf(hs2, -20.f * e3t4_3f);
+        f5 = addf(mul_pow2((-(hs * hs)) + (-T1), 4.f), 4.f * (15.f * T2_3f - 2.f * t4_3f));
+    } else {
+        const T t4 = t2 * t2;
+        const T t4_3 = t4 * third;
+        const T T2_3 = E * t4_3;
+        f1 = addf(mul_pow2(T1 + (-p) + t4_3 + (-t2_3), 2.f) + mulf(T2_3, -10.f), -1.f);
+        F2 = mul_pow2(mulf(p, 3.f) + mulf(T1, -5.f) + t2, 2.f) +
+             mulf(mulf(T2_3, 7.f) + (-t4_3), 10.f);
+        f3 = hs2 + e3 * (mulf(t4_3, 20.f) + mul_pow2(F2, -2.f));
+        f4 = hs2 + mulf(e3 * t4_3, -20.f);
+        f5 = mul_pow2(mulf(T2_3, 15.f) + mul_pow2(t4_3, -2.f) + (-(hs * hs)) + (-T1), 4.f);
+    }
     const T f2 = addf(F2, -1.f);
-    const T f3 = hs2 + e3 * (mulf(t4_3, 20.f) + mul_pow2(F2, -2.f));
-    const T f4 = hs2 + mulf(e3 * t4_3, -20.f);
-    const T f5 = mul_pow2(mulf(T2_3, 15.f) + mul_pow2(t4_3, -2.f) + (-(hs * hs)) + (-T1), 4.f);
     const T s = k.sw * invR;
     const T Cx = C + s * f1;
     const T A2 = f2 * invR2;
@@ -418,7 +436,7 @@ __device__ __forceinline__ void pair_sym_rg(T dx, T dy, T dz, T zi, T zj, T fx, 
 // fz_lo): a 48-byte stride, so the rotated reads stay conflict-free.
 // sRev holds NT * 3 doubles: each warp adds its per-source sums with shared-
 // memory atomics.  u must be zeroed and receives scale * M f.
-template <bool WALL, int NT>
+template <bool WALL, int NT, bool FAR = false>
 __device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__restrict__ sRev,
                                            const float4 *__restrict__ hi,
                                            const float4 *__restrict__ lo,
@@ -468,7 +486,7 @@ __device__ __forceinline__ void dfsym_item(float4 *__restrict__ sD, double *__re
                 const int s = g * 32 + ((lane + t) & 31);
                 const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
                 const dfl zj(B.x, B.y);
-                pair_sym_rg<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                pair_sym_rg<WALL, dfl, FAR>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
                                   dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), gx, gy, gz, k, ux,
                                   uy, uz, vx, vy, vz);
                 const int from = (lane + 1) & 31;

@@ -146,12 +146,14 @@ def test_matvec_empty_and_errors(ctx):
 
 @pytest.mark.parametrize("layout", ["monolayer", "line"])
 def test_symmetric_variant_spatial_order(ctx, layout):
-    """From 16,384 blobs the symmetric kernel runs in a spatial order (cells
-    of a grid in Morton order) and lets block pairs far apart skip the lo
-    parts of the separations and the overlap test.  Bodies of the monolayer
-    (clustered blobs, many overlapping pairs within a shell) and blobs spread
-    along one line (one axis takes every bit of the grid) both match the FP64
-    kernel over all rows and the oracle on sampled rows."""
+    """From 16,384 blobs the symmetric kernels run in a spatial order (cells
+    of a grid in Morton order).  In FP32 block pairs far apart skip the lo
+    parts of the separations and the overlap test; in double-float, block
+    pairs 64 a apart sum the t4 terms of the wall polynomials in FP32.
+    Bodies of the monolayer (clustered blobs, many overlapping pairs within a
+    shell) and blobs spread along one line (one axis takes every bit of the
+    grid) both match the FP64 kernel over all rows and the oracle on sampled
+    rows, each precision at its own bound."""
     if layout == "monolayer":
         s = I.config_monolayer(13, n_bodies=120, box=200.0 * (120 / 4096.0) ** 0.5)
         r = O.blob_positions(s.q, s.theta, s.blob_start, s.rho)
@@ -175,3 +177,8 @@ def test_symmetric_variant_spatial_order(ctx, layout):
     ref = O.matvec(r, f, a, 1.0, True, targets=rows)
     assert rel_l2(got[rows], ref) <= TOL["fp32"]
     assert np.abs(got[rows] - ref).max() <= TOL["fp32"] * np.abs(ref).max()
+    # the double-float kernel in the same order: block pairs 64 a apart sum
+    # their t4 terms in FP32; the agreement stays at double-float rounding
+    got_df = host(ctx.mobility_matvec(dev(r), dev(f), a, 1.0, True, "df64"))
+    assert rel_l2(got_df, ref64) <= 1e-12
+    assert rel_l2(got_df[rows], ref) <= 1e-12
