@@ -487,7 +487,7 @@ def run_ours(args):
                             "flops_per_pair": FLOPS_PER_PAIR,
                             "peak_basis": "FP64 FMA rate measured in this run"}}
                 if prec == "fp64":
-                    line["kernel"] = "pair_f64_kernel<wall> (FP64 pipe, every ordered pair)"
+                    line["kernel"] = "pair_f64sym_kernel<wall> (FP64 pipe, each unordered pair once)"
                     matvec_fp64 = line
                 else:
                     line["kernel"] = ("pair_df_kernel<wall> (symmetric, double-float arithmetic "
