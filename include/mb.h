@@ -43,9 +43,10 @@ typedef enum {
                               or cudaMalloc failed                           */
     MB_ECUDA = 3,          /* a CUDA runtime call failed                      */
     MB_ENOTCONVERGED = 4,  /* Krylov solver hit maxit; best iterate written   */
-    MB_ETIMEOUT = 5,       /* reserved for a bounded device wait that ran out;
-                              no call returns it: no kernel of this library
-                              waits on the host or on another kernel         */
+    MB_ETIMEOUT = 5,       /* a host wait for the stream ran past the limit
+                              set by mb_context_set_wait_limit (no kernel of
+                              this library waits on the host or on another
+                              kernel; the work already enqueued still runs) */
     MB_ESINGULAR = 6       /* a Cholesky factorisation broke down (a body's
                               mobility block not positive definite, e.g. a
                               blob below z = a)                               */
@@ -201,6 +202,21 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
  * their FP32 pair launches too (variant 0 runs as 1 there, 4 as 3).
  */
 mb_status mb_context_set_pair_variant(mb_context *ctx, int variant);
+
+/* Bound the host waits of mb_solve_mobility, mb_solve_mobility_permeable,
+ * mb_solve_resistance, mb_precond_setup and mb_mobility_matvec with host
+ * pointers: a wait for the caller's stream (a synchronisation, or the poll
+ * of a residual estimate the device posts) that has not finished after
+ * `seconds` returns MB_ETIMEOUT instead of blocking.  None of the library's
+ * kernels waits on anything, so a wait runs long only behind other work on
+ * the stream or a device that stopped answering.  seconds <= 0 (the
+ * default) waits without limit.  After MB_ETIMEOUT the work already
+ * enqueued on the stream still runs and writes the context's workspace and
+ * the call's outputs: the caller synchronises the stream before the next
+ * call on this context.  The batched and serving engines keep their waits
+ * unbounded (their host bookkeeping follows each wait).  Returns MB_EINVAL
+ * for a non-finite limit. */
+mb_status mb_context_set_wait_limit(mb_context *ctx, double seconds);
 
 /* The FP32 pair-kernel variant this context uses for N blobs with or
  * without the wall: the fixed variant if one was set, else the autotuner's

@@ -47,6 +47,7 @@ EXPORTED_SYMBOLS = [
     "mb_context_destroy",
     "mb_context_workspace_bytes",
     "mb_context_set_pair_variant",
+    "mb_context_set_wait_limit",
     "mb_context_pair_variant",
     "mb_profile_enable",
     "mb_profile_read",
@@ -178,6 +179,7 @@ def load_library():
     L.mb_context_workspace_bytes.restype = ctypes.c_size_t
     L.mb_context_workspace_bytes.argtypes = [vp]
     L.mb_context_set_pair_variant.argtypes = [vp, ci]
+    L.mb_context_set_wait_limit.argtypes = [vp, dbl]
     L.mb_context_pair_variant.argtypes = [vp, i64, ci, ctypes.POINTER(ci)]
     L.mb_profile_enable.argtypes = [vp, ci]
     L.mb_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
@@ -311,6 +313,11 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.L.mb_context_workspace_bytes(self.handle))
+
+    def set_wait_limit(self, seconds: float):
+        """Bound the host waits of solves, preconditioner setup and host-pointer
+        matvecs (MB_ETIMEOUT past it); <= 0 waits without limit."""
+        self._check(self.L.mb_context_set_wait_limit(self.handle, float(seconds)))
 
     def set_pair_variant(self, variant: int):
         """-1 autotune (default), 0 scalar, 1 packed x2, 2 packed x4, 3 symmetric,

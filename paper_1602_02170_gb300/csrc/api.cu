@@ -1,7 +1,9 @@
 // C ABI of libmb.so (declared in include/mb.h): argument checks, context and
 // workspace management, host-pointer staging, dispatch to the kernels.
+#include <chrono>
 #include <cmath>
 #include <new>
+#include <thread>
 
 #include <initializer_list>
 
@@ -24,6 +26,29 @@ mb_status cuda_err(mb_context *ctx, cudaError_t e, const char *what)
 {
     return set_err(ctx, e == cudaErrorMemoryAllocation ? MB_ENOMEM : MB_ECUDA, "%s: %s (%s)", what,
                    cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+mb_status wait_stream(mb_context *ctx, cudaStream_t s, const char *what)
+{
+    if (!(ctx->wait_limit_s > 0.0)) {
+        const cudaError_t e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? MB_OK : cuda_err(ctx, e, what);
+    }
+    // poll: spin for the first 100 us (short steps), then sleep between queries
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return MB_OK;
+        if (e != cudaErrorNotReady) return cuda_err(ctx, e, what);
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > ctx->wait_limit_s)
+            return set_err(ctx, MB_ETIMEOUT,
+                           "%s: the stream had not finished after %.3g s (wait limit); the "
+                           "enqueued work still runs, synchronise the stream before the next call",
+                           what, ctx->wait_limit_s);
+        if (el > 1e-4) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what)
@@ -207,6 +232,14 @@ mb_status mb_context_destroy(mb_context *ctx)
 
 size_t mb_context_workspace_bytes(const mb_context *ctx) { return ctx ? ctx->held : 0; }
 
+mb_status mb_context_set_wait_limit(mb_context *ctx, double seconds)
+{
+    MB_TRY(check_ctx(ctx));
+    if (!std::isfinite(seconds)) return set_err(ctx, MB_EINVAL, "wait limit must be finite");
+    ctx->wait_limit_s = seconds;
+    return MB_OK;
+}
+
 mb_status mb_context_set_pair_variant(mb_context *ctx, int variant)
 {
     MB_TRY(check_ctx(ctx));
@@ -285,7 +318,7 @@ mb_status mb_mobility_matvec(mb_context *ctx, const double *r, const double *f, 
     MB_TRY(matvec_device(ctx, (const double *)ctx->stage_r.ptr, (const double *)ctx->stage_f.ptr,
                          n, a, eta, wall, prec, (double *)ctx->stage_u.ptr, s));
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(u, ctx->stage_u.ptr, bytes, cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "host-pointer matvec"));
     return MB_OK;
 }
 

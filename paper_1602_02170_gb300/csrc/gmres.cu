@@ -753,12 +753,19 @@ struct Solver {
                 *est = *(volatile double *)ctx->host_post;
                 return MB_OK;
             }
-            if ((it & 255) == 255 &&
-                std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(2000))
-                break;
+            if ((it & 255) == 255) {
+                const double el = std::chrono::duration<double>(
+                                      std::chrono::steady_clock::now() - t0).count();
+                if (ctx->wait_limit_s > 0.0 && el > ctx->wait_limit_s)
+                    return set_err(ctx, MB_ETIMEOUT,
+                                   "Krylov step: no estimate posted after %.3g s (wait limit); "
+                                   "the enqueued work still runs, synchronise the stream before "
+                                   "the next call", ctx->wait_limit_s);
+                if (el > 2e-3) break;
+            }
         }
         MB_TRY(read_est(est));
-        ctx->post_seq = *cnt;
+        ctx->post_seq = *cnt;  // the stream is idle: every posting has arrived
         return MB_OK;
     }
 
@@ -766,7 +773,7 @@ struct Solver {
     {
         MB_CUDA_TRY(ctx, cudaMemcpyAsync(hsm, sm + sl.est(), sizeof(double),
                                          cudaMemcpyDeviceToHost, s));
-        MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        MB_TRY(wait_stream(ctx, s, "Krylov step"));
         *est = hsm[0];
         return MB_OK;
     }
@@ -918,8 +925,11 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
         MB_TRY(precond_setup(ctx, nb, n, r, q, blob_start, p->a, p->eta, p->wall, s, !resist,
                              shift));
     if (p->prec != MB_FP64) MB_TRY(matvec_pack_positions(ctx, r, n, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "solver setup"));
     const auto t1 = clk::now();
+    // the stream is idle, so every posting of earlier calls has arrived (an
+    // earlier call that ran out of its wait limit may have left some behind)
+    if (ctx->host_post) ctx->post_seq = *(volatile unsigned long long *)(ctx->host_post + 1);
 
     Solver S;
     S.resist = resist != 0;
@@ -970,7 +980,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     double bnorm2 = 0.0;
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(S.hsm, S.sm + sl.nrm2(), sizeof(double),
                                      cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "right-hand side norm"));
     bnorm2 = S.hsm[0];
     const double bnorm = std::sqrt(bnorm2);
 
@@ -1106,7 +1116,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     }
     count_launch();
     MB_CUDA_TRY(ctx, cudaGetLastError());
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "solution"));
     const auto t2 = clk::now();
     if (info) {
         info->iters = iters;

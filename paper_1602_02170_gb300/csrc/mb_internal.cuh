@@ -122,6 +122,7 @@ struct mb_context {
                                              // stream may be the legacy one)
 
     // FP32 pair-kernel variant: -1 = autotune per (size class, wall), else fixed
+    double wait_limit_s = 0.0;  // host waits for the stream: <= 0 without limit
     int pair_variant = -1;
     std::map<int, int> tuned;   // size-class key -> fastest variant
 
@@ -136,6 +137,8 @@ mb_status set_err(mb_context *ctx, mb_status s, const char *fmt, ...);
 // Message for calls without a context (read back by mb_last_error(NULL)).
 void set_thread_err(const char *msg);
 mb_status cuda_err(mb_context *ctx, cudaError_t e, const char *what);
+// Wait for stream s, within the context's wait limit (MB_ETIMEOUT past it).
+mb_status wait_stream(mb_context *ctx, cudaStream_t s, const char *what);
 // Make `buf` hold at least `bytes`; respects the context budget.
 mb_status ensure(mb_context *ctx, DevBuf &buf, size_t bytes, const char *what);
 void release(mb_context *ctx, DevBuf &buf);

@@ -1528,7 +1528,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     std::vector<int64_t> hstart(nb + 1);
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(hstart.data(), blob_start, sizeof(int64_t) * (nb + 1),
                                      cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "preconditioner setup"));
     if (hstart[0] != 0 || hstart[nb] != n)
         return set_err(ctx, MB_EINVAL, "blob_start[0] must be 0 and blob_start[n_b] = N");
     std::vector<int64_t> off(nb + 1);
@@ -1596,7 +1596,7 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     int first_bad = big;
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(&first_bad, ctx->flag.ptr, sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "preconditioner setup"));
     ctx->pc_nb = nb;
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
@@ -1663,7 +1663,7 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
                                      cudaMemcpyDeviceToHost, s));
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * 3 * (size_t)n,
                                      cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "preconditioner setup"));
     if (hstart[0] != 0 || hstart[nb] != n)
         return set_err(ctx, MB_EINVAL, "blob_start[0] must be 0 and blob_start[n_b] = N");
     // shape of every body: bodies with the same blob count and bitwise equal
@@ -1752,7 +1752,7 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
     int first_bad = big;
     MB_CUDA_TRY(ctx, cudaMemcpyAsync(&first_bad, ctx->flag.ptr, sizeof(int),
                                      cudaMemcpyDeviceToHost, s));
-    MB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    MB_TRY(wait_stream(ctx, s, "preconditioner setup"));
     ctx->pc_nb = nb;
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;

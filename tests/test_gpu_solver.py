@@ -331,6 +331,33 @@ def test_repeated_and_interleaved_solves_replay_captured_steps(ctx):
                         assert rel_l2(x, y) <= 1e-9
 
 
+def test_wait_limit_returns_timeout_and_context_recovers(ctx):
+    """With a host-wait limit far below a Krylov step (1 us), the solve
+    returns MB_ETIMEOUT while its enqueued work still runs.  After a
+    synchronisation and with the limit lifted, the same context solves the
+    problem to the result it gave before.  A non-finite limit is refused."""
+    s = I.config_small_suspension(1)
+    d = _dev_susp(s)
+    args = (d["q"], d["theta"], d["blob_start"], d["rho"], d["F"], d["T"], s.a, s.eta, True)
+    U0, W0, lam0, _ = ctx.solve_mobility(*args, tol=1e-10, prec="mixed")
+    with pytest.raises(mb.MBError) as ei:
+        ctx.set_wait_limit(float("nan"))
+    assert ei.value.name == "MB_EINVAL"
+    ctx.set_wait_limit(1e-6)
+    try:
+        with pytest.raises(mb.MBError) as ei:
+            ctx.solve_mobility(*args, tol=1e-10, prec="mixed")
+        assert ei.value.name == "MB_ETIMEOUT"
+    finally:
+        torch.cuda.synchronize()
+        ctx.set_wait_limit(0.0)
+    for _ in range(2):
+        U, W, lam, info = ctx.solve_mobility(*args, tol=1e-10, prec="mixed")
+        assert info["converged"] == 1
+        for x, y in zip((U, W, lam), (U0, W0, lam0)):
+            assert rel_l2(host(x), host(y)) <= 1e-9
+
+
 def test_solve_fp32_small_suspension(ctx):
     _solve_and_compare(ctx, I.config_small_suspension(2), "fp32", 1e-6, 1e-5)
 
