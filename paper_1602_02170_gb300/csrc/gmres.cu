@@ -313,6 +313,15 @@ __device__ void saddle_rows_cluster(const SaddleIn &sd, double *__restrict__ w, 
     }
 }
 
+// 1 / sqrt(x) in the passes' arithmetic: FP64 as rsqrt_fp64, FP32 as the
+// hardware estimate refined by one Newton step
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt_fp64(x); }
+__device__ __forceinline__ float rsqrt_t(float x)
+{
+    const float y = rsqrtf(x);
+    return y * (1.5f - 0.5f * x * y * y);
+}
+
 // post (optional): mapped host memory [est, step count]; rank 0 writes the
 // residual estimate, then (after a system-scope fence) the incremented count
 // kept at *seq, so that the host can read the estimate without a stream
@@ -330,19 +339,24 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    // shared: part[3][m + 1] partial sums (pass 0, pass 1, |w|^2), hs[m + 1]
-    // summed coefficients, hc[m + 2] merged column j of H, cs[m], sn[m]
+    // shared (slots of 8 bytes): part[3][m + 1] partial sums (pass 0, pass 1,
+    // |w|^2), one spare row, hc[m + 2] merged column j of H, cs[m], sn[m]
     // previous rotations (rank 0), red[32] block partials, hT[m + 1] the
-    // summed coefficients in T, then (stage != 0) the staged slices
-    // sV[(j + 2) x per] in T
+    // summed coefficients, then (stage != 0) the staged slices sV[(j + 2) x
+    // per].  The partial sums, H's column, the rotations and the block
+    // partials are held in T: with FP32 inner iterations (mixed precision)
+    // the serial sums, the norm and the Givens update then run on the FP32
+    // pipe, where a dependent operation takes a few cycles instead of the
+    // ~64 of FP64 on this chip; the Hessenberg entries have the FP32
+    // accuracy of the dot products they come from.
     extern __shared__ double buf[];
     const int m1 = S.m + 1;
     double *part = buf;
-    double *hs = part + 3 * m1;
-    double *hc = hs + m1;
-    double *cs = hc + S.m + 2;
-    double *sn = cs + S.m;
-    double *red = sn + S.m;
+    T *hc = (T *)(part + 4 * m1);
+    T *cs = (T *)(part + 4 * m1 + S.m + 2);
+    T *sn = (T *)(part + 4 * m1 + 2 * S.m + 2);
+    double *red = part + 4 * m1 + 3 * S.m + 2;
+    T *redT = (T *)red;
     T *hT = (T *)(red + 32);
     T *sV = (T *)(red + 32 + m1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -366,8 +380,8 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             red[17] = __longlong_as_double((long long)q0);
         }
         for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            cs[i] = sm[S.cs() + i];
-            sn[i] = sm[S.sn() + i];
+            cs[i] = T(sm[S.cs() + i]);
+            sn[i] = T(sm[S.sn() + i]);
         }
     }
     if (stage) {
@@ -404,20 +418,19 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         else w[e0 + k] = double(v);
     };
     for (int pass = 0; pass < 2; ++pass) {
-        double *pp = part + pass * m1;
+        T *pp = (T *)(part + pass * m1);
         for (int i = warp; i <= j; i += nw) {
             T acc = T(0);
             for (int k = lane; k < cnt; k += 32) acc += ld(i, k) * ld(j + 1, k);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) pp[i] = double(acc);
+            if (lane == 0) pp[i] = acc;
         }
         cluster.sync();  // every CTA's partials of this pass are written
         for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-            double acc = 0.0;
+            T acc = T(0);
             for (int rr = 0; rr < kOrthCluster; ++rr) acc += cluster.map_shared_rank(pp, rr)[i];
-            hs[i] = acc;
-            hT[i] = T(acc);
+            hT[i] = acc;
             hc[i] = pass == 0 ? acc : hc[i] + acc;
         }
         __syncthreads();
@@ -428,48 +441,50 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         }
         __syncthreads();  // hs, hT are rewritten by the next pass; w is final
     }
-    double *pn = part + 2 * m1;
-    double acc = 0.0;
+    T *pn = (T *)(part + 2 * m1);
+    T acc = T(0);
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const double v = double(ld(j + 1, k));
+        const T v = ld(j + 1, k);
         acc += v * v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
+    if (lane == 0) redT[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < nw; ++k) t += red[k];
+        T t = T(0);
+        for (int k = 0; k < nw; ++k) t += redT[k];
         pn[0] = t;
     }
     cluster.sync();  // every CTA's |w|^2 partial is written
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        T t = T(0);
         for (int rr = 0; rr < kOrthCluster; ++rr) t += cluster.map_shared_rank(pn, rr)[0];
-        red[0] = t;
-        red[1] = t > 0.0 ? rsqrt_fp64(t) : 0.0;  // 1 / |w|
+        const T y = t > T(0) ? rsqrt_t(t) : T(0);  // 1 / |w|
+        red[0] = double(t);
+        red[1] = double(y);
     }
     __syncthreads();
     const double nrm2 = red[0], inv = red[1];
     if (rank == 0) {
         if (threadIdx.x == 0) {
             // Givens update of column j on the shared copy (as givens_column,
-            // with the norms from rsqrt_fp64)
-            hc[j + 1] = nrm2 * inv;
+            // with the norms from reciprocal square roots), in T
+            const T t = T(nrm2), yi = T(inv);
+            hc[j + 1] = t * yi;
             for (int i = 0; i < j; ++i) {
-                const double a = hc[i], b = hc[i + 1];
+                const T a = hc[i], b = hc[i + 1];
                 hc[i] = cs[i] * a + sn[i] * b;
                 hc[i + 1] = -sn[i] * a + cs[i] * b;
             }
             const double gj = red[16];
-            const double a = hc[j], b = hc[j + 1];
-            const double r2 = a * a + b * b;
-            const double ir = r2 > 0.0 ? rsqrt_fp64(r2) : 0.0;
-            const double c = r2 > 0.0 ? a * ir : 1.0;
-            const double sg = r2 > 0.0 ? b * ir : 0.0;
+            const T a = hc[j], b = hc[j + 1];
+            const T r2 = a * a + b * b;
+            const T ir = r2 > T(0) ? rsqrt_t(r2) : T(0);
+            const double c = r2 > T(0) ? double(a * ir) : 1.0;
+            const double sg = r2 > T(0) ? double(b * ir) : 0.0;
             hc[j] = r2 * ir;
-            hc[j + 1] = 0.0;
+            hc[j + 1] = T(0);
             sm[S.cs() + j] = c;
             sm[S.sn() + j] = sg;
             sm[S.g() + j] = c * gj;
@@ -485,7 +500,7 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = hc[i];
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = double(hc[i]);
     }
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = double(ld(j + 1, k)) * inv;
     cluster.sync();  // no CTA exits while another still reads its partials; w is final
