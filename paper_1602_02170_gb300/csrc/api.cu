@@ -208,7 +208,7 @@ mb_status mb_context_destroy(mb_context *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ctx->pos_hi, &ctx->pos_lo, &ctx->partial, &ctx->stage_r, &ctx->stage_f,
-                      &ctx->stage_u, &ctx->pinv, &ctx->pinv_off, &ctx->blob_start_copy,
+                      &ctx->stage_u, &ctx->pinv, &ctx->pinv32, &ctx->pinv_off, &ctx->blob_start_copy,
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
                       &ctx->sol_body,

@@ -673,6 +673,7 @@ __global__ void split_ft_kernel(int64_t nb, const double *__restrict__ FT, doubl
 struct Solver {
     mb_context *ctx;
     bool resist = false;  // A = M alone (resistance problem), L = 3N
+    bool pc_f32 = false;  // apply the preconditioner from its FP32 copy (FP32 inner iterations)
     const double *shift = nullptr;  // per-blob diagonal addition to M, or null
     cudaStream_t s;
     int64_t n, nb, L;
@@ -740,7 +741,7 @@ struct Solver {
     void precond(const double *v, double *z, cudaStream_t cs)
     {
         if (resist) precond_apply_blobs(ctx, v, z, cs);
-        else precond_apply_packed(ctx, v, z, cs);
+        else precond_apply_packed(ctx, v, z, cs, pc_f32);
     }
 
     // out[0..nk) = V[0..nk) . w  (accumulate: out += ...)
@@ -961,6 +962,12 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     const mb_precision inner = inner_precision(p->prec);
     const mb_precision outer = outer_precision(p->prec);
     const int vg = vec_grid(L);
+    // FP32 inner iterations apply the explicit blocks from an FP32 copy (the
+    // flexible GMRES keeps the z_j it was given)
+    if (inner == MB_FP32_KAHAN && !resist && p->precond != MB_PRECOND_FREE_SHARED) {
+        MB_TRY(precond_make_f32(ctx, s));
+        S.pc_f32 = ctx->pc_f32_ready;
+    }
     // small systems: the body of every blob, for the saddle rows formed in the
     // orthogonalisation
     const int *body_map = nullptr;

@@ -83,6 +83,7 @@ struct mb_context {
     // preconditioner (last mb_precond_setup / mb_precond_setup_shared)
     mb::DevBuf pinv;             // explicit inverses, (3n_p+6)^2 doubles each: one per
                                  // body (wall kind) or one per body shape (shared kind)
+    mb::DevBuf pinv32;           // FP32 copy of the explicit blocks (FP32 inner iterations)
     mb::DevBuf pinv_off;         // int64 offsets into pinv (bodies or shapes, + 1)
     mb::DevBuf blob_start_copy;  // int64 copy of blob_start used by apply
     mb::DevBuf flag;             // int status flags written by kernels
@@ -97,6 +98,8 @@ struct mb_context {
     int pc_factored = 0;         // 1: blocks hold L, G = L^-1 K and -N (applied by
                                  // triangular solves), 0: explicit inverses
     int64_t pc_shapes = 0;       // shared kind: distinct shapes
+    int64_t pc_doubles = 0;      // entries of the explicit wall blocks in pinv
+    bool pc_f32_ready = false;   // pinv32 holds the current explicit blocks in FP32
 
     // solver workspace
     mb::DevBuf sol_r;            // blob positions
@@ -232,7 +235,10 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
                                const int64_t *blob_start, const double *rho, double a,
                                double eta, cudaStream_t s, int schur = 1);
 // z = P^-1 v where v = [w (3N); g (6 n_b)] packed contiguously, same for z.
-void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s);
+// f32: from the FP32 copy of the explicit blocks when precond_make_f32 made one
+void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s,
+                          bool f32 = false);
+mb_status precond_make_f32(mb_context *ctx, cudaStream_t s);
 // z = M~^-1 w with the blob blocks alone (w, z: 3N), for the resistance problem.
 void precond_apply_blobs(mb_context *ctx, const double *w, double *z, cudaStream_t s);
 

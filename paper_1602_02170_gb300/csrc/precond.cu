@@ -283,14 +283,26 @@ __global__ void __launch_bounds__(kSetupThreads) precond_setup_kernel(
 // with `chunks` chunks of `rows` rows per body (one chunk when bodies are
 // plentiful, several when few bodies would leave SMs idle); one warp per
 // output row, lanes across the row.
+__global__ void pc_to_f32_kernel(const double *__restrict__ a, int64_t count, float *__restrict__ b)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+// TP: the blocks' type, FP64, or FP32 (an FP32 copy of the explicit blocks
+// for the FP32 inner iterations of mixed precision; products and sums in
+// FP32 too).
+template <typename TP>
 __global__ void __launch_bounds__(256) precond_apply_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
-    const double *__restrict__ P, const double *__restrict__ w, const double *__restrict__ g,
+    const TP *__restrict__ P, const double *__restrict__ w, const double *__restrict__ g,
     double *__restrict__ lam, double *__restrict__ UO, int chunks, int rows, int body_rows)
 {
     // body_rows = 6: the indefinite block on [w_p; g_p]; 0: the blob block
     // M_pp^-1 alone on w_p (the resistance problem's preconditioner)
-    extern __shared__ double xs[];
+    extern __shared__ double xs_raw[];
+    TP *xs = (TP *)xs_raw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t item = blockIdx.x; item < nb * chunks; item += gridDim.x) {
         const int64_t p = item / chunks;
@@ -302,18 +314,18 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(
         if (r0 >= me) continue;  // uniform over the CTA
         __syncthreads();
         for (int e = threadIdx.x; e < me; e += blockDim.x)
-            xs[e] = e < n ? w[3 * b0 + e] : g[6 * p + (e - n)];
+            xs[e] = TP(e < n ? w[3 * b0 + e] : g[6 * p + (e - n)]);
         __syncthreads();
-        const double *Pp = P + poff[p];
+        const TP *Pp = P + poff[p];
         for (int row = r0 + warp; row < r1; row += nw) {
-            const double *pr = Pp + (size_t)row * m;
-            double acc = 0.0;
+            const TP *pr = Pp + (size_t)row * m;
+            TP acc = TP(0);
             for (int c = lane; c < me; c += 32) acc += pr[c] * xs[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) {
-                if (row < n) lam[3 * b0 + row] = acc;
-                else UO[6 * p + (row - n)] = acc;
+                if (row < n) lam[3 * b0 + row] = double(acc);
+                else UO[6 * p + (row - n)] = double(acc);
             }
         }
     }
@@ -1600,6 +1612,8 @@ mb_status precond_setup(mb_context *ctx, int64_t nb, int64_t n, const double *r,
     ctx->pc_nb = nb;
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
+    ctx->pc_doubles = off[nb];
+    ctx->pc_f32_ready = false;
     ctx->pc_kind = MB_PRECOND_WALL;
     ctx->pc_shapes = 0;
     ctx->pc_schur = schur;
@@ -1757,6 +1771,8 @@ mb_status precond_setup_shared(mb_context *ctx, int64_t nb, int64_t n, const dou
     ctx->pc_n = n;
     ctx->pc_max_np = max_np;
     ctx->pc_kind = MB_PRECOND_FREE_SHARED;
+    ctx->pc_doubles = 0;
+    ctx->pc_f32_ready = false;
     ctx->pc_factored = 0;
     ctx->pc_shapes = ns;
     ctx->pc_schur = schur;
@@ -1909,7 +1925,7 @@ __global__ void __launch_bounds__(256) precond_apply_factored_kernel(
 }
 
 static void precond_apply_impl(mb_context *ctx, const double *w, const double *g, double *lam,
-                               double *UO, cudaStream_t s, int body_rows = 6)
+                               double *UO, cudaStream_t s, int body_rows = 6, bool f32 = false)
 {
     const int m = 3 * ctx->pc_max_np + body_rows;
     // few bodies: split each body's rows so that about two CTAs per SM have work
@@ -1935,16 +1951,40 @@ static void precond_apply_impl(mb_context *ctx, const double *w, const double *g
         return;
     }
     const int rows = (int)ceil_div(m, chunks);
-    precond_apply_kernel<<<grid, 256, sizeof(double) * m, s>>>(
-        ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr, (const int64_t *)ctx->pinv_off.ptr,
-        (const double *)ctx->pinv.ptr, w, g, lam, UO, chunks, rows, body_rows);
+    if (f32)
+        precond_apply_kernel<float><<<grid, 256, sizeof(float) * m, s>>>(
+            ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr,
+            (const int64_t *)ctx->pinv_off.ptr, (const float *)ctx->pinv32.ptr, w, g, lam, UO,
+            chunks, rows, body_rows);
+    else
+        precond_apply_kernel<double><<<grid, 256, sizeof(double) * m, s>>>(
+            ctx->pc_nb, (const int64_t *)ctx->blob_start_copy.ptr,
+            (const int64_t *)ctx->pinv_off.ptr, (const double *)ctx->pinv.ptr, w, g, lam, UO,
+            chunks, rows, body_rows);
     count_launch();
 }
 
-void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s)
+void precond_apply_packed(mb_context *ctx, const double *v, double *z, cudaStream_t s, bool f32)
 {
     const int64_t n3 = 3 * ctx->pc_n;
-    precond_apply_impl(ctx, v, v + n3, z, z + n3, s);
+    precond_apply_impl(ctx, v, v + n3, z, z + n3, s, 6, f32 && ctx->pc_f32_ready);
+}
+
+// The FP32 copy of the explicit wall blocks (precond_apply_packed with
+// f32), for the FP32 inner iterations; does nothing for the other kinds.
+mb_status precond_make_f32(mb_context *ctx, cudaStream_t s)
+{
+    ctx->pc_f32_ready = false;
+    if (ctx->pc_nb == 0 || ctx->pc_kind != MB_PRECOND_WALL || ctx->pc_factored || ctx->pc_doubles == 0)
+        return MB_OK;
+    MB_TRY(ensure(ctx, ctx->pinv32, sizeof(float) * (size_t)ctx->pc_doubles, "FP32 preconditioner"));
+    const int grid = (int)std::min<int64_t>(ceil_div(ctx->pc_doubles, 256), 8 * (int64_t)ctx->sm_count);
+    pc_to_f32_kernel<<<grid, 256, 0, s>>>((const double *)ctx->pinv.ptr, ctx->pc_doubles,
+                                          (float *)ctx->pinv32.ptr);
+    count_launch();
+    MB_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->pc_f32_ready = true;
+    return MB_OK;
 }
 
 void precond_apply_blobs(mb_context *ctx, const double *w, double *z, cudaStream_t s)
