@@ -211,7 +211,7 @@ mb_status mb_context_destroy(mb_context *ctx)
                       &ctx->stage_u, &ctx->pinv, &ctx->pinv32, &ctx->pinv_off, &ctx->blob_start_copy,
                       &ctx->flag, &ctx->sol_r, &ctx->sol_V, &ctx->sol_Z, &ctx->sol_b,
                       &ctx->sol_x, &ctx->sol_w, &ctx->sol_t, &ctx->sol_small, &ctx->sol_dots,
-                      &ctx->sol_body,
+                      &ctx->sol_body, &ctx->sol_V32,
                       &ctx->sol_dx, &ctx->sol_ym, &ctx->pc_type, &ctx->pc_theta, &ctx->pc_ref,
                       &ctx->eval_hi, &ctx->eval_lo, &ctx->render_r, &ctx->render_f,
                       &ctx->sort_perm, &ctx->sort_key, &ctx->sort_count, &ctx->sort_hi,

@@ -322,6 +322,12 @@ __device__ __forceinline__ float rsqrt_t(float x)
     return y * (1.5f - 0.5f * x * y * y);
 }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+
 // post (optional): mapped host memory [est, step count]; rank 0 writes the
 // residual estimate, then (after a system-scope fence) the incremented count
 // kept at *seq, so that the host can read the estimate without a stream
@@ -334,7 +340,7 @@ template <typename T>
 __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClusterThreads)
     orth_cluster_kernel(double *__restrict__ V, int64_t L, int j, double *__restrict__ sm, Small S,
                         double *__restrict__ post, unsigned long long *__restrict__ seq,
-                        int stage, SaddleIn sd)
+                        int stage, SaddleIn sd, float *__restrict__ V32)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -364,6 +370,20 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     const int64_t e0 = rank * per, e1 = e0 + per < L ? e0 + per : L;
     const int cnt = e1 > e0 ? (int)(e1 - e0) : 0;  // this CTA's slice length
     double *w = V + (int64_t)(j + 1) * L;
+    // V32 (FP32 passes, staged): an FP32 copy of the basis, each vector
+    // written by the step that formed it (vector 0 by step 0).  From step 1
+    // on, this CTA's slices of V_0 .. V_j are copied into shared memory with
+    // cp.async before the saddle rows, so that the copy overlaps them; only
+    // V_{j+1} = w is staged after them.  The staged values equal T(V) either
+    // way.
+    const bool async_stage = stage && V32 && j >= 1;
+    if (async_stage) {
+        for (int x = threadIdx.x; x < (j + 1) * cnt; x += blockDim.x) {
+            const int i = x / cnt, k = x - i * cnt;
+            cp_async4(sV + (int64_t)i * per + k, V32 + (int64_t)i * L + e0 + k);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     if (sd.partial) {
         // w = A x from the pair kernel's partials; the cluster barrier orders
         // the body rows (written by any CTA) before every CTA's reads of w
@@ -386,15 +406,17 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     }
     if (stage) {
         // batches of kBatch loads per thread in flight before their stores
+        // (vectors i0 .. j + 1; i0 = j + 1 when V_0 .. V_j came by cp.async)
         constexpr int kBatch = 8;
-        const int total = (j + 2) * cnt;
+        const int i0 = async_stage ? j + 1 : 0;
+        const int total = (j + 2 - i0) * cnt;
         for (int x0 = threadIdx.x; x0 < total; x0 += kBatch * (int)blockDim.x) {
             double v[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const int x = x0 + u * (int)blockDim.x;
                 if (x < total) {
-                    const int i = x / cnt, k = x - i * cnt;
+                    const int i = i0 + x / cnt, k = x % cnt;
                     v[u] = V[(int64_t)i * L + e0 + k];
                 }
             }
@@ -402,11 +424,14 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             for (int u = 0; u < kBatch; ++u) {
                 const int x = x0 + u * (int)blockDim.x;
                 if (x < total) {
-                    const int i = x / cnt, k = x - i * cnt;
+                    const int i = i0 + x / cnt, k = x % cnt;
                     sV[(int64_t)i * per + k] = T(v[u]);
+                    // step 0 also leaves V_0's FP32 copy for the later steps
+                    if (V32 && i == 0) V32[e0 + k] = float(v[u]);
                 }
             }
         }
+        if (async_stage) asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
     }
     // element e0 + k of vector i, staged (in T) or in place (FP64)
@@ -502,7 +527,11 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         __syncthreads();
         for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sm[S.H(i, j)] = double(hc[i]);
     }
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) w[e0 + k] = double(ld(j + 1, k)) * inv;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const double v = double(ld(j + 1, k)) * inv;
+        w[e0 + k] = v;
+        if (V32 && stage) V32[(int64_t)(j + 1) * L + e0 + k] = float(v);
+    }
     cluster.sync();  // no CTA exits while another still reads its partials; w is final
 }
 
@@ -968,6 +997,12 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
         MB_TRY(precond_make_f32(ctx, s));
         S.pc_f32 = ctx->pc_f32_ready;
     }
+    // small systems with FP32 passes: the basis' FP32 copy (see orth_cluster_kernel)
+    float *V32 = nullptr;
+    if (L <= kOrthSmallMax && inner == MB_FP32_KAHAN) {
+        MB_TRY(ensure(ctx, ctx->sol_V32, sizeof(float) * (size_t)L * (m + 1), "FP32 Krylov basis"));
+        V32 = (float *)ctx->sol_V32.ptr;
+    }
     // small systems: the body of every blob, for the saddle rows formed in the
     // orthogonalisation
     const int *body_map = nullptr;
@@ -1067,10 +1102,12 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                         const int stage = orth_cluster_stage(L, j) ? 1 : 0;
                         if (inner == MB_FP32_KAHAN)
                             orth_cluster_kernel<float><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
+                                V32);
                         else
                             orth_cluster_kernel<double><<<kOrthCluster, kOrthClusterThreads, osm, cs>>>(
-                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd);
+                                S.V, L, j, S.sm, sl, ctx->host_post_dev, ctx->post_seq_dev, stage, sd,
+                                nullptr);
                         count_launch();
                         MB_CUDA_TRY(ctx, cudaGetLastError());
                         return MB_OK;

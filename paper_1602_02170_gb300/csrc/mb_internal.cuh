@@ -108,6 +108,7 @@ struct mb_context {
     mb::DevBuf sol_dx, sol_ym;   // mixed precision: cycle correction, running M lambda
     mb::DevBuf sol_small;        // Hessenberg, Givens, dots (doubles)
     mb::DevBuf sol_dots;         // Cholesky scratch of the preconditioner setup
+    mb::DevBuf sol_V32;          // FP32 copy of the Krylov basis (small systems, FP32 passes)
     mb::DevBuf sol_body;         // int body of every blob (small-system steps)
     mb::DevBuf batch_ws;         // batched-solve workspace (mb_solve_batch)
     void *host_small = nullptr;  // pinned host mirror of small scalars
