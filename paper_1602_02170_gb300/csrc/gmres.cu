@@ -272,7 +272,8 @@ struct SaddleIn {
 };
 
 // Row e of w = A x: blob rows scale sum_s partial[s][e] - (K U)_e (one
-// thread each, rounded as saddle_rows_kernel); body rows -(K^T lambda)_p,c
+// thread each, the partials summed in four interleaved chains); body rows
+// -(K^T lambda)_p,c
 // (one warp each, lanes over the body's blobs).  Blob rows [b0, b1) are
 // this CTA's; body rows are dealt to the warps of the whole cluster.
 __device__ void saddle_rows_cluster(const SaddleIn &sd, double *__restrict__ w, int64_t b0,
@@ -280,8 +281,14 @@ __device__ void saddle_rows_cluster(const SaddleIn &sd, double *__restrict__ w, 
 {
     const int64_t m3 = 3 * sd.n;
     for (int64_t e = b0 + threadIdx.x; e < b1 && e < m3; e += blockDim.x) {
-        double acc = 0.0;
-        for (int sc = 0; sc < sd.S; ++sc) acc += sd.partial[sc * m3 + e];
+        // four interleaved sums: a dependent FP64 add costs ~64 cycles here
+        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+        int sc = 0;
+        for (; sc + 4 <= sd.S; sc += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a4[u] += sd.partial[(sc + u) * m3 + e];
+        for (; sc < sd.S; ++sc) a4[0] += sd.partial[sc * m3 + e];
+        const double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
         const int64_t i = e / 3;
         const int c = (int)(e - 3 * i);
         const int64_t p = sd.body ? (int64_t)sd.body[i] : body_of(sd.start, sd.nb, i);

@@ -847,8 +847,9 @@ mb_status f32_run(mb_context *ctx, int v, const double *f, int64_t n, double a, 
 {
     const int res = wall ? f32_resident<true>(ctx, v) : f32_resident<false>(ctx, v);
     if (v == 4) {
-        // small problems: 64-target blocks, source chunks of 32 or more, many CTAs
-        const Plan p = make_plan(n, f32_targets_per_cta(4), res, 1024, kSmallNT, kSmallNT);
+        // small problems: 64-target blocks, source chunks of 16 or more (half a
+        // tile: one warp per CTA walks fewer sources, more CTAs share the work)
+        const Plan p = make_plan(n, f32_targets_per_cta(4), res, 1024, kSmallNT / 2, kSmallNT / 2);
         double *out = u;
         const int direct = p.S == 1;
         if (!direct) {

@@ -85,8 +85,10 @@ __device__ __forceinline__ void x2_item(float4 *__restrict__ sP, const float4 *_
         float2 ax[NP], ay[NP], az[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) ax[q] = ay[q] = az[q] = make_float2(0.f, 0.f);
+        // the staged sources of this tile (chunks may be shorter than NT)
+        const int cnt = j_end - jt < NT ? (int)(j_end - jt) : NT;
 #pragma unroll 2
-        for (int s = 0; s < NT; ++s) {
+        for (int s = 0; s < cnt; ++s) {
             const float4 *P = sP + kX2SmemFloat4PerSource * s;
             const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
             const float2 nxh = make_float2(P0.x, P0.y), nyh = make_float2(P0.z, P0.w);
