@@ -348,6 +348,55 @@ __global__ void refine_blobs_kernel(const double *__restrict__ r, const double *
     }
 }
 
+// Double-float, forward only, for the smallest problems: blocks of kSmallNT
+// targets (one per thread) against source chunks of kSmallNT / 2, every
+// ordered pair evaluated (the forward half of pair_sym_rg; the reverse half
+// is dead code for the compiler), the block's sums added to u (zeroed) with
+// FP64 atomics.  Twice the pair evaluations of the symmetric kernel, in
+// several times as many one-warp CTAs: a few hundred blobs fill the GPU.
+template <bool WALL, int NT>
+__global__ void __launch_bounds__(NT) pair_dfx_kernel(
+    const float4 *__restrict__ hi, const float4 *__restrict__ lo, const double *__restrict__ f,
+    int64_t n, int64_t chunk, int n_tblocks, int64_t n_items, PairConsts<dfl> k,
+    double *__restrict__ u, double scale)
+{
+    __shared__ float4 sD[3 * NT];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tb = (int)(item % n_tblocks);
+        const int64_t j0 = (item / n_tblocks) * chunk;
+        const int64_t j1 = j0 + chunk < n ? j0 + chunk : n;
+        const int64_t i = (int64_t)tb * NT + threadIdx.x;
+        const int64_t ic = i < n ? i : n - 1;
+        const float4 th = hi[ic], tl = lo[ic];
+        const dfl xi(th.x, tl.x), yi(th.y, tl.y), zi(th.z, tl.z);
+        __syncthreads();  // the previous item is done with sD
+        if (j0 + threadIdx.x < j1) {
+            const int64_t j = j0 + threadIdx.x;
+            const float4 h = hi[j], l = lo[j];
+            const dfl fx(f[3 * j]), fy(f[3 * j + 1]), fz(f[3 * j + 2]);
+            float4 *d = sD + 3 * threadIdx.x;
+            d[0] = make_float4(h.x, l.x, h.y, l.y);
+            d[1] = make_float4(h.z, l.z, fx.hi, fx.lo);
+            d[2] = make_float4(fy.hi, fy.lo, fz.hi, fz.lo);
+        }
+        __syncthreads();
+        dfl ux, uy, uz, vx, vy, vz;
+        const int cnt = (int)(j1 - j0);
+        for (int s = 0; s < cnt; ++s) {
+            const float4 A = sD[3 * s], B = sD[3 * s + 1], C = sD[3 * s + 2];
+            const dfl zj(B.x, B.y);
+            pair_sym_rg<WALL, dfl>(xi - dfl(A.x, A.y), yi - dfl(A.z, A.w), zi - zj, zi, zj,
+                                   dfl(B.z, B.w), dfl(C.x, C.y), dfl(C.z, C.w), dfl(), dfl(), dfl(),
+                                   k, ux, uy, uz, vx, vy, vz);
+        }
+        if (i < n) {
+            atomicAdd(u + 3 * i, scale * to_double(ux));
+            atomicAdd(u + 3 * i + 1, scale * to_double(uy));
+            atomicAdd(u + 3 * i + 2, scale * to_double(uz));
+        }
+    }
+}
+
 // box (optional, spatial order): the bounding boxes of the sort's blocks of
 // 2 kNT blobs (two blocks of this kernel each); block pairs whose boxes are
 // 64 a or more apart take the FAR instance of the item.
@@ -458,6 +507,7 @@ constexpr int kTPT = MB_PAIR_TPT;  // targets per thread
 constexpr int kF32Variants = 5;
 constexpr int kSmallNT = 32;        // CTA size of the small-problem kernels
 constexpr int64_t kSmallN = 8192;   // below this the FP64 and double-float paths use them
+constexpr int64_t kDfxMaxN = 1024;  // up to this the double-float product is forward only
 constexpr int kSmallF64Chunk = 8;   // smallest source chunk of the small FP64 kernel
 
 int f32_targets_per_cta(int v)
@@ -1063,7 +1113,20 @@ mb_status matvec_packed(mb_context *ctx, const double *r, const double *f, int64
         }
         auto *ev = profile_begin(ctx, s);
         const PairConsts<dfl> k = PairConsts<dfl>::make(a);
-        if (small && wall)
+        if (n <= kDfxMaxN) {
+            // the smallest problems: every ordered pair, many one-warp CTAs
+            const int rx = wall ? resident_ctas(ctx, pair_dfx_kernel<true, kSmallNT>, kSmallNT)
+                                : resident_ctas(ctx, pair_dfx_kernel<false, kSmallNT>, kSmallNT);
+            const Plan px = make_plan(n, kSmallNT, rx, 1024, kSmallNT / 2, kSmallNT / 2);
+            if (wall)
+                pair_dfx_kernel<true, kSmallNT><<<px.grid, kSmallNT, 0, s>>>(hi, lo, fk, n, px.chunk,
+                                                                   px.n_tblocks, px.items, k, uk,
+                                                                   scale);
+            else
+                pair_dfx_kernel<false, kSmallNT><<<px.grid, kSmallNT, 0, s>>>(hi, lo, fk, n, px.chunk,
+                                                                    px.n_tblocks, px.items, k, uk,
+                                                                    scale);
+        } else if (small && wall)
             pair_df_kernel<true, kSmallNT><<<grid, kSmallNT, 0, s>>>(hi, lo, fk, n, nb, items, k, uk,
                                                                     scale, nullptr, 0.f);
         else if (small)
