@@ -409,21 +409,39 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
     }
 }
 
-// 1 / sqrt(d) for the pivots of the cluster factorisation by Newton-Raphson,
-// y <- y (3 - d y^2) / 2: the FP32 hardware reciprocal square root refined by
-// one step in FP32, then one step in FP64 (quadratic convergence: from FP32
-// accuracy to ~1e-14 relative).  Each dependent FP64 operation costs about
-// 64 cycles on this chip, so the short chain matters: the division of 1 by an
-// FP64 square root is about three times longer.  Pivots outside the FP32
-// range take that path.
-__device__ __forceinline__ double rsqrt_newton(double d)
+// The pivot test and 1 / sqrt(d) of the factorisations, with few FP64
+// instructions: an FP64 warp instruction (compares and conversions included)
+// issues only about once per 76 cycles on each SM sub-partition of this chip,
+// and the pivots sit on the factorisation's serial chain.
+//   pivot_ok: d > 0 and finite, from the bit pattern (integer compares).
+//   pivot_rsqrt: an FP32 estimate from d's truncated bits (integer
+//     operations), one FP32 Newton step, back to FP64 through the bit pattern
+//     (exact), then one FP64 Newton step y + (y / 2)(1 - d y^2) in three FP64
+//     instructions: about 2e-14 relative (quadratic convergence from the
+//     FP32 estimate's ~2^-23).  Exponents outside 2^-100 .. 2^100 take
+//     1 / sqrt(d).
+__device__ __forceinline__ bool pivot_ok(double d)
 {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    const float df = (float)d;
-    float yf = rsqrtf(df);
-    yf = yf * (1.5f - 0.5f * df * yf * yf);
-    const double y = (double)yf;
-    return y * (1.5 - 0.5 * d * y * y);
+    const long long b = __double_as_longlong(d);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+__device__ __forceinline__ double pivot_rsqrt(double d)
+{
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / sqrt(d);
+    // the FP32 number with d's exponent and the top 23 bits of its mantissa
+    const float f = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
+    float y = rsqrtf(f);
+    y = y * (1.5f - 0.5f * f * y * y);
+    const unsigned yb = __float_as_uint(y);  // positive and normal
+    const double yd = __hiloint2double((int)((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)),
+                                       (int)((yb & 7u) << 29));
+    const double h = __hiloint2double(__double2hiint(yd) - (1 << 20), __double2loint(yd));  // yd / 2
+    const double p = d * yd;
+    return fma(h, fma(-p, yd, 1.0), yd);
 }
 
 // Entry (row, col) of K_p (rows 3 i + al of blob i are [I, -[d_i]x],
@@ -495,13 +513,11 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
                 int f = 0;
                 for (int c = c0; c < c0 + w; ++c) {
                     const double d = L[(size_t)c * ld + c];
-                    if (!(d > 0.0)) {  // the same value in every lane
+                    if (!pivot_ok(d)) {  // the same value in every lane
                         f = 1;
                         break;
                     }
-                    double il = 0.0;
-                    if (lane == 0) il = 1.0 / sqrt(d);
-                    il = __shfl_sync(0xffffffffu, il, 0);
+                    const double il = pivot_rsqrt(d);
                     if (lane == 0) ils[c] = il;
                     double *pc = pT + (size_t)(c - c0) * n;
                     for (int i = c + lane; i < n; i += 32) {
@@ -573,13 +589,11 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const double d = col[c] - acc;
-            if (!(d > 0.0)) {  // the same value in every thread
+            if (!pivot_ok(d)) {  // the same value in every thread
                 fail = 1;
                 break;
             }
-            double il = 0.0;
-            if (lane == 0) il = 1.0 / sqrt(d);
-            il = __shfl_sync(0xffffffffu, il, 0);
+            const double il = pivot_rsqrt(d);
             if (threadIdx.x == 0) {
                 ils[c] = il;
                 L[(size_t)c * ld + c] = d * il;  // sqrt(d)
@@ -764,12 +778,12 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 for (int c = 0; c < kPanel; ++c) {
                     if (c < w && !f) {
                         const double d = __shfl_sync(0xffffffffu, drow[c], c);
-                        if (!(d > 0.0)) {
+                        if (!pivot_ok(d)) {
                             f = 1;  // the same value in every lane
                         } else {
                             // selects instead of branches; entries above a
                             // lane's diagonal may take junk and are never read
-                            const double il = rsqrt_newton(d);
+                            const double il = pivot_rsqrt(d);
                             if (lane == 0) ils[c0 + c] = il;
                             drow[c] *= lane >= c ? il : 1.0;  // lane c: sqrt(d)
                             const double lac = lane > c && lane < w ? drow[c] : 0.0;
