@@ -748,7 +748,41 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
         int fail = 0;
         for (int c0 = 0; c0 < n; c0 += kPanel) {
             const int w = n - c0 < kPanel ? n - c0 : kPanel, t0 = c0 + w;
-            cluster.sync();  // (a) the previous trailing updates are complete
+            cluster.sync();  // (a) the previous panel's (h1) is complete everywhere
+            // (h2) of the previous panel: own rows i >= c0 + kPanel, columns
+            // [c0 + kPanel, i], by the warps of sub-partitions 1..3 other
+            // than warp 1 (warp 0 runs the diagonal chain on sub-partition
+            // 0, whose FP64 unit warp 4 then leaves to it), while the chain
+            // runs.  It reads Pn (the previous panel) and the rows' previous
+            // panel entries, and writes columns that no one reads before the
+            // barrier after the chain.
+            if (c0 > 0 && (warp & 3) != 0 && warp != 1) {
+                const int cp = c0 - kPanel, jlo = c0 + kPanel;  // the previous panel is full
+                const int widx = warp < 4 ? warp - 2 : warp - 3, nwk = nw - 3;
+                for (int li = widx; li < nown; li += nwk) {
+                    const int i = rank + kFacCluster * li;
+                    if (i < jlo) continue;
+                    double *Li = own(li);
+                    double lk[kPanel];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) lk[k] = Li[cp + k];
+                    // two entries per step and two partial sums per entry
+                    for (int j = jlo + lane; j <= i; j += 64) {
+                        const int j2 = j + 32;
+                        const bool two = j2 <= i;
+                        double a0 = Li[j], a1 = 0.0, b0 = two ? Li[j2] : 0.0, b1 = 0.0;
+#pragma unroll
+                        for (int k = 0; k < kPanel; k += 2) {
+                            a0 -= lk[k] * Pn[(size_t)k * nmax + j];
+                            if (two) b0 -= lk[k] * Pn[(size_t)k * nmax + j2];
+                            a1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j];
+                            if (two) b1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j2];
+                        }
+                        Li[j] = a0 + a1;
+                        if (two) Li[j2] = b0 + b1;
+                    }
+                }
+            }
             // (b) + (c) warp 0: lane a < w reads row a of the diagonal block
             // from its owner into registers, then the block's Cholesky runs on
             // registers (the column loop unrolled, the other rows' entries by
@@ -877,34 +911,23 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 if (row % kFacCluster == rank) Br[6 * (row / kFacCluster) + e % 6] = Bd[e];
             }
             __syncthreads();
-            // (h) trailing update of own rows i >= t0
-            for (int li = warp; li < nown; li += nw) {
-                const int i = rank + kFacCluster * li;
-                if (i < t0) continue;
+            // (h1) the next panel's columns [t0, t0 + kPanel) of own rows
+            // i >= t0, one entry per thread: the next panel's diagonal chain
+            // and row solves need them.  The rest of the trailing update,
+            // (h2), runs during that chain.  Each entry takes the same
+            // operations in the same order as in one pass.
+            for (int e = threadIdx.x; e < nown * kPanel; e += blockDim.x) {
+                const int li = e / kPanel, q = e - li * kPanel;
+                const int i = rank + kFacCluster * li, j = t0 + q;
+                if (i < t0 || j > i) continue;
                 double *Li = own(li);
-                double lk[kPanel];
+                double a0 = Li[j], a1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < kPanel; ++k) lk[k] = k < w ? Li[c0 + k] : 0.0;
-                // two entries per step and two partial sums per entry: four
-                // independent FP64 chains instead of one
-                for (int j = t0 + lane; j <= i; j += 64) {
-                    const int j2 = j + 32;
-                    const bool two = j2 <= i;
-                    double a0 = Li[j], a1 = 0.0, b0 = two ? Li[j2] : 0.0, b1 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < kPanel; k += 2) {
-                        if (k < w) {
-                            a0 -= lk[k] * Pn[(size_t)k * nmax + j];
-                            if (two) b0 -= lk[k] * Pn[(size_t)k * nmax + j2];
-                        }
-                        if (k + 1 < w) {
-                            a1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j];
-                            if (two) b1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j2];
-                        }
-                    }
-                    Li[j] = a0 + a1;
-                    if (two) Li[j2] = b0 + b1;
+                for (int k = 0; k < kPanel; k += 2) {
+                    if (k < w) a0 -= Li[c0 + k] * Pn[(size_t)k * nmax + j];
+                    if (k + 1 < w) a1 -= Li[c0 + k + 1] * Pn[(size_t)(k + 1) * nmax + j];
                 }
+                Li[j] = a0 + a1;
             }
             // ... and of the own rows of B, the entries (row, column) spread
             // over all threads
