@@ -916,32 +916,35 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
             // and row solves need them.  The rest of the trailing update,
             // (h2), runs during that chain.  Each entry takes the same
             // operations in the same order as in one pass.
-            for (int e = threadIdx.x; e < nown * kPanel; e += blockDim.x) {
-                const int li = e / kPanel, q = e - li * kPanel;
-                const int i = rank + kFacCluster * li, j = t0 + q;
-                if (i < t0 || j > i) continue;
-                double *Li = own(li);
-                double a0 = Li[j], a1 = 0.0;
+            // ... together with the own rows of B (entries after the first
+            // nown * kPanel of the loop), so that both take the same pass
+            const int h1n = nown * kPanel;
+            for (int e = threadIdx.x; e < h1n + 6 * nown; e += blockDim.x) {
+                if (e < h1n) {
+                    const int li = e / kPanel, q = e - li * kPanel;
+                    const int i = rank + kFacCluster * li, j = t0 + q;
+                    if (i < t0 || j > i) continue;
+                    double *Li = own(li);
+                    double a0 = Li[j], a1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < kPanel; k += 2) {
-                    if (k < w) a0 -= Li[c0 + k] * Pn[(size_t)k * nmax + j];
-                    if (k + 1 < w) a1 -= Li[c0 + k + 1] * Pn[(size_t)(k + 1) * nmax + j];
-                }
-                Li[j] = a0 + a1;
-            }
-            // ... and of the own rows of B, the entries (row, column) spread
-            // over all threads
-            for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x) {
-                const int li = e / 6, x = e - 6 * li;
-                if (rank + kFacCluster * li < t0) continue;
-                const double *Li = own(li) + c0;
-                double a0 = Br[e], a1 = 0.0;
+                    for (int k = 0; k < kPanel; k += 2) {
+                        if (k < w) a0 -= Li[c0 + k] * Pn[(size_t)k * nmax + j];
+                        if (k + 1 < w) a1 -= Li[c0 + k + 1] * Pn[(size_t)(k + 1) * nmax + j];
+                    }
+                    Li[j] = a0 + a1;
+                } else {
+                    const int eb = e - h1n;
+                    const int li = eb / 6, x = eb - 6 * li;
+                    if (rank + kFacCluster * li < t0) continue;
+                    const double *Li = own(li) + c0;
+                    double a0 = Br[eb], a1 = 0.0;
 #pragma unroll
-                for (int k = 0; k < kPanel; k += 2) {
-                    if (k < w) a0 -= Li[k] * Bd[6 * k + x];
-                    if (k + 1 < w) a1 -= Li[k + 1] * Bd[6 * (k + 1) + x];
+                    for (int k = 0; k < kPanel; k += 2) {
+                        if (k < w) a0 -= Li[k] * Bd[6 * k + x];
+                        if (k + 1 < w) a1 -= Li[k + 1] * Bd[6 * (k + 1) + x];
+                    }
+                    Br[eb] = a0 + a1;
                 }
-                Br[e] = a0 + a1;
             }
         }
         if (fail) {
