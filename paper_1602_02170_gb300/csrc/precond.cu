@@ -32,9 +32,73 @@ namespace {
 constexpr int kSetupThreads = 256;
 constexpr int kSmemMaxRows = 160;   // n = 3 n_p rows held in shared memory up to this
 
+// The pivot test and 1 / sqrt(d) of the factorisations, with few FP64
+// instructions: an FP64 warp instruction (compares and conversions included)
+// issues only about once per 76 cycles on each SM sub-partition of this chip,
+// and the pivots sit on the factorisation's serial chain.
+//   pivot_ok: d > 0 and finite, from the bit pattern (integer compares).
+//   pivot_rsqrt: an FP32 estimate from d's truncated bits (integer
+//     operations), one FP32 Newton step, back to FP64 through the bit pattern
+//     (exact), then one FP64 Newton step y + (y / 2)(1 - d y^2) in three FP64
+//     instructions: about 2e-14 relative (quadratic convergence from the
+//     FP32 estimate's ~2^-23).  Exponents outside 2^-100 .. 2^100 take
+//     1 / sqrt(d).
+__device__ __forceinline__ bool pivot_ok(double d)
+{
+    const long long b = __double_as_longlong(d);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// FP64 number with the bits of a positive normal FP32 number (exact)
+__device__ __forceinline__ double f32_to_f64_bits(float y)
+{
+    const unsigned yb = __float_as_uint(y);
+    return __hiloint2double((int)((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)),
+                            (int)((yb & 7u) << 29));
+}
+
+// FP32 number with the exponent of d (2^-100 .. 2^100) and the top 23 bits
+// of its mantissa
+__device__ __forceinline__ float f64_to_f32_trunc(double d)
+{
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    return __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
+}
+
+__device__ __forceinline__ bool f32_range(double d)
+{
+    const int e = (__double2hiint(d) >> 20) & 0x7ff;
+    return e >= 1023 - 100 && e <= 1023 + 100;
+}
+
+// 1 / d for positive d the same way: FP32 estimate with one FP32 Newton
+// step, then y + y (1 - d y) in two FP64 instructions (~1e-14 relative).
+__device__ __forceinline__ double pivot_rcp(double d)
+{
+    if (!f32_range(d)) return 1.0 / d;
+    const float f = f64_to_f32_trunc(d);
+    float y = __fdividef(1.0f, f);
+    y = y * (2.0f - f * y);
+    const double yd = f32_to_f64_bits(y);
+    return fma(yd, fma(-d, yd, 1.0), yd);
+}
+
+__device__ __forceinline__ double pivot_rsqrt(double d)
+{
+    if (!f32_range(d)) return 1.0 / sqrt(d);
+    const float f = f64_to_f32_trunc(d);
+    float y = rsqrtf(f);
+    y = y * (1.5f - 0.5f * f * y * y);
+    const double yd = f32_to_f64_bits(y);  // y is positive and normal
+    const double h = __hiloint2double(__double2hiint(yd) - (1 << 20), __double2loint(yd));  // yd / 2
+    const double p = d * yd;
+    return fma(h, fma(-p, yd, 1.0), yd);
+}
+
 // N = S^-1 for the symmetrised 6 x 6 S by Gauss-Jordan without pivoting, run
 // by one whole warp: lane b < 12 holds column b of [S | I] in registers (one
-// division per pivot, the eliminations as shuffles and FMAs).  Returns 1 in
+// reciprocal per pivot, the eliminations as shuffles and FMAs).  Returns 1 in
 // every lane when a pivot falls below 1e-12 of the largest diagonal entry: a
 // body that cannot resist some rigid motion (e.g. blobs on a line through
 // the tracking point cannot resist spin about it).  Writes Nm (row-major)
@@ -45,14 +109,21 @@ __device__ int inverse6_warp(const double *__restrict__ S, double *__restrict__ 
 #pragma unroll
     for (int a = 0; a < 6; ++a)
         col[a] = lane < 6 ? 0.5 * (S[a * 6 + lane] + S[lane * 6 + a]) : (lane - 6 == a ? 1.0 : 0.0);
-    double smax = 0.0;
+    // the largest |diagonal entry| and the pivot tests on bit patterns
+    // (integer compares: non-negative doubles order as their bits), the
+    // reciprocal by pivot_rcp: few FP64 instructions on this serial path
+    long long bmax = 0;
 #pragma unroll
-    for (int a = 0; a < 6; ++a) smax = fmax(smax, fabs(__shfl_sync(0xffffffffu, col[a], a)));
+    for (int a = 0; a < 6; ++a)
+        bmax = max(bmax, __double_as_longlong(__shfl_sync(0xffffffffu, col[a], a)) &
+                             0x7fffffffffffffffLL);
+    const long long tb = __double_as_longlong(1e-12 * __longlong_as_double(bmax));
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         const double d = __shfl_sync(0xffffffffu, col[c], c);
-        if (!(d > 1e-12 * smax)) return 1;  // the same value in every lane
-        const double rc = col[c] * (1.0 / d);
+        const long long db = __double_as_longlong(d);
+        if (!(db > tb && db < 0x7ff0000000000000LL)) return 1;  // the same value in every lane
+        const double rc = col[c] * pivot_rcp(d);
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             if (a == c) continue;
@@ -407,41 +478,6 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
                         scale * blk[3 * al + be] + (shift && bi == bj && al == be ? shift[b] : 0.0);
         }
     }
-}
-
-// The pivot test and 1 / sqrt(d) of the factorisations, with few FP64
-// instructions: an FP64 warp instruction (compares and conversions included)
-// issues only about once per 76 cycles on each SM sub-partition of this chip,
-// and the pivots sit on the factorisation's serial chain.
-//   pivot_ok: d > 0 and finite, from the bit pattern (integer compares).
-//   pivot_rsqrt: an FP32 estimate from d's truncated bits (integer
-//     operations), one FP32 Newton step, back to FP64 through the bit pattern
-//     (exact), then one FP64 Newton step y + (y / 2)(1 - d y^2) in three FP64
-//     instructions: about 2e-14 relative (quadratic convergence from the
-//     FP32 estimate's ~2^-23).  Exponents outside 2^-100 .. 2^100 take
-//     1 / sqrt(d).
-__device__ __forceinline__ bool pivot_ok(double d)
-{
-    const long long b = __double_as_longlong(d);
-    return b > 0 && b < 0x7ff0000000000000LL;
-}
-
-__device__ __forceinline__ double pivot_rsqrt(double d)
-{
-    const int hi = __double2hiint(d);
-    const unsigned lo = (unsigned)__double2loint(d);
-    const int e = (hi >> 20) & 0x7ff;
-    if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / sqrt(d);
-    // the FP32 number with d's exponent and the top 23 bits of its mantissa
-    const float f = __int_as_float(((hi - (896 << 20)) << 3) | (int)(lo >> 29));
-    float y = rsqrtf(f);
-    y = y * (1.5f - 0.5f * f * y * y);
-    const unsigned yb = __float_as_uint(y);  // positive and normal
-    const double yd = __hiloint2double((int)((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)),
-                                       (int)((yb & 7u) << 29));
-    const double h = __hiloint2double(__double2hiint(yd) - (1 << 20), __double2loint(yd));  // yd / 2
-    const double p = d * yd;
-    return fma(h, fma(-p, yd, 1.0), yd);
 }
 
 // Entry (row, col) of K_p (rows 3 i + al of blob i are [I, -[d_i]x],
