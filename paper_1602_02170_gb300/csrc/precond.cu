@@ -708,25 +708,52 @@ __global__ void __launch_bounds__(256) pc_factor_kernel(
 // S2 on a cluster of kFacCluster CTAs per body, for problems with fewer
 // bodies than SMs (one SM per body would leave most of the chip idle, and
 // one SM sustains only about 1.7 FP64 FMA per clock).  Rows are dealt cyclically:
-// CTA r holds rows i = r + kFacCluster t of M_p (and of B = K_p) in shared
-// memory.  Per panel of kPanel columns:
-//   (b) every CTA reads the panel's diagonal block and B rows from their
-//       owners and (c) factors them itself: the same data and arithmetic in
-//       every CTA, so the same pivots and the same failure decision;
-//   (d) each CTA solves its own rows below the panel for their panel entries;
-//   (g) after a cluster barrier each CTA gathers the factored panel of all
-//       rows below it and (h) subtracts its rank-kPanel product from its own
-//       rows' trailing entries and B rows.
-// A cluster barrier separates every read of another CTA's shared memory from
-// that CTA's next write of the same entries.  The outputs are those of
-// pc_factor_kernel.
+// CTA r holds rows i = r + kFacCluster t of M_p (and of B = K_p).  Panel q
+// (columns c0 .. c0 + w - 1, t0 = c0 + w) runs in three stages:
+//   (A) warp 0 factors the panel's diagonal block, which every CTA holds in
+//       shared memory (the same data and arithmetic in every CTA, so the
+//       same pivots and the same failure decision).  Meanwhile the warps of
+//       the other SM sub-partitions subtract panel q-1's outer product from
+//       the CTA's own rows i >= t0 (columns c0 .. i) and their B rows;
+//   (B) the CTA's rows i >= t0 solve for their panel entries, and every CTA
+//       solves the panel's B rows: triangular solves against the factored
+//       block, one row per 8 lanes (lane k holds entry k);
+//   (C) after the one cluster barrier of the panel, every CTA gathers the
+//       factored panel of the rows below it, and forms the next panel's
+//       diagonal block and B rows itself: their owners' current entries
+//       (panels < q applied) minus panel q's product.  The owners write the
+//       factored block rows and solved B rows back in place.
+// The next block's rows are left out of their owners' trailing updates, so
+// no CTA writes an entry that another CTA reads between two barriers: the
+// barrier of panel q+1 separates the stage-C reads of panel q from the
+// owners' next writes of the same entries.  The outputs are those of
+// pc_factor_kernel up to rounding (here each entry takes its products in one
+// FMA chain).
 constexpr int kFacCluster = 8;
 
 size_t factor_cluster_smem(int nmax, bool srows)
 {
     const size_t R = (size_t)(nmax + kFacCluster - 1) / kFacCluster;
-    return sizeof(double) * ((srows ? R * nmax : 0) + 6 * R + nmax + kPanel * kPanel +
-                             6 * kPanel + (size_t)kPanel * nmax + 72);
+    return sizeof(double) * ((srows ? R * nmax : 0) + 6 * R + nmax + 2 * kPanel * kPanel +
+                             2 * 6 * kPanel + (size_t)kPanel * nmax + 72);
+}
+
+// In-place triangular solve of the 8-lane group that holds y (lane k of the
+// group: entry k): y_k <- (y_k - sum_{j<k} x_j D[k][j]) / L_kk, column by
+// column (x_j, once final, leaves all later entries in one FMA each); dk[j]
+// = D[k][j] (j < k), ilk = 1 / L_kk.  All 32 lanes take part in the shuffles.
+__device__ __forceinline__ double panel_solve8(double y, const double (&dk)[kPanel], double ilk,
+                                               int k, int w, int lane)
+{
+#pragma unroll
+    for (int j = 0; j < kPanel; ++j) {
+        if (j < w) {
+            if (k == j) y *= ilk;
+            const double xj = __shfl_sync(0xffffffffu, y, (lane & ~7) | j);
+            if (k > j && k < w) y -= xj * dk[j];
+        }
+    }
+    return y;
 }
 
 // SROWS: the rows of M_p sit in the CTAs' shared memory (3 n_p <= 160);
@@ -751,12 +778,17 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
     double *Lr = sm;                    // R x nmax: own rows of M_p, becoming L (SROWS)
     double *Br = SROWS ? Lr + (size_t)R * nmax : sm;  // R x 6: own rows of K_p, becoming G
     double *ils = Br + 6 * R;           // nmax: 1 / L[c][c] (every CTA keeps all)
-    double *D = ils + nmax;             // kPanel x kPanel: the panel's diagonal block
-    double *Bd = D + kPanel * kPanel;   // kPanel x 6: the panel's rows of B
-    double *Pn = Bd + 6 * kPanel;       // kPanel x nmax: factored panel, transposed
+    double *Db = ils + nmax;            // 2 x kPanel x kPanel: diagonal blocks (by panel parity)
+    double *Bb = Db + 2 * kPanel * kPanel;  // 2 x kPanel x 6: the panels' B rows
+    double *Pn = Bb + 2 * 6 * kPanel;   // kPanel x nmax: factored panel, transposed
     double *Sp = Pn + (size_t)kPanel * nmax;  // 36: partial G^T G
     double *Nm = Sp + 36;               // 36
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // The trailing update's warps: 1..3 and 5..7, two on each of the SM
+    // sub-partitions 1..3 (warp 0 runs the diagonal chain on sub-partition
+    // 0; measured, a share for warp 4 there made the update slower).
+    constexpr int kHW = 6;
+    const int hw = (warp & 3) ? warp - 1 - (warp >> 2) : -1;
     for (int64_t p = cid; p < nb; p += ncl) {
         const int64_t b0 = start[p];
         const int np = (int)(start[p + 1] - b0);
@@ -774,214 +806,229 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                          : Pp + (size_t)row * m;
         };
         auto rd = [](const double *a) -> double { return SROWS ? *a : __ldcg(a); };
-        if (SROWS)
-            for (int e = threadIdx.x; e < nown * n; e += blockDim.x) {
-                const int li = e / n, j = e % n, i = rank + kFacCluster * li;
-                if (j <= i) Lr[(size_t)li * nmax + j] = Pp[(size_t)i * m + j];
+        auto brow_of = [&](int row) -> const double * {
+            return cluster.map_shared_rank(Br, row % kFacCluster) + 6 * (row / kFacCluster);
+        };
+        if (SROWS) {
+            // own rows' lower-triangle entries, loads issued in batches
+            constexpr int kLoad = 4;
+            const int tot = nown * n;
+            for (int base = 0; base < tot; base += kLoad * (int)blockDim.x) {
+                double v[kLoad];
+                int dst[kLoad];
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u) {
+                    const int e = base + threadIdx.x + u * (int)blockDim.x;
+                    const int li = e / n, j = e - li * n, i = rank + kFacCluster * li;
+                    dst[u] = e < tot && j <= i ? li * nmax + j : -1;
+                    if (dst[u] >= 0) v[u] = Pp[(size_t)i * m + j];
+                }
+#pragma unroll
+                for (int u = 0; u < kLoad; ++u)
+                    if (dst[u] >= 0) Lr[dst[u]] = v[u];
             }
+        }
         for (int e = threadIdx.x; e < 6 * nown; e += blockDim.x)
             Br[e] = k_entry(r + 3 * b0, qx, qy, qz, rank + kFacCluster * (e / 6), e % 6);
+        cluster.sync();  // every CTA's rows are in place
+        // the first diagonal block and its B rows from their owners
+        for (int e = threadIdx.x; e < kPanel * kPanel + 6 * kPanel; e += blockDim.x) {
+            if (e < kPanel * kPanel) {
+                const int a = e / kPanel, b = e % kPanel;
+                if (a < n && b <= a) Db[e] = rd(row_of(a) + b);
+            } else {
+                const int eb = e - kPanel * kPanel, a = eb / 6;
+                if (a < n) Bb[eb] = brow_of(a)[eb % 6];
+            }
+        }
+        __syncthreads();
         int fail = 0;
-        for (int c0 = 0; c0 < n; c0 += kPanel) {
+        for (int c0 = 0, par = 0; c0 < n; c0 += kPanel, par ^= 1) {
             const int w = n - c0 < kPanel ? n - c0 : kPanel, t0 = c0 + w;
-            cluster.sync();  // (a) the previous panel's (h1) is complete everywhere
-            // (h2) of the previous panel: own rows i >= c0 + kPanel, columns
-            // [c0 + kPanel, i], by the warps of sub-partitions 1..3 other
-            // than warp 1 (warp 0 runs the diagonal chain on sub-partition
-            // 0, whose FP64 unit warp 4 then leaves to it), while the chain
-            // runs.  It reads Pn (the previous panel) and the rows' previous
-            // panel entries, and writes columns that no one reads before the
-            // barrier after the chain.
-            if (c0 > 0 && (warp & 3) != 0 && warp != 1) {
-                const int cp = c0 - kPanel, jlo = c0 + kPanel;  // the previous panel is full
-                const int widx = warp < 4 ? warp - 2 : warp - 3, nwk = nw - 3;
-                for (int li = widx; li < nown; li += nwk) {
-                    const int i = rank + kFacCluster * li;
-                    if (i < jlo) continue;
-                    double *Li = own(li);
-                    double lk[kPanel];
-#pragma unroll
-                    for (int k = 0; k < kPanel; ++k) lk[k] = Li[cp + k];
-                    // two entries per step and two partial sums per entry
-                    for (int j = jlo + lane; j <= i; j += 64) {
-                        const int j2 = j + 32;
-                        const bool two = j2 <= i;
-                        double a0 = Li[j], a1 = 0.0, b0 = two ? Li[j2] : 0.0, b1 = 0.0;
-#pragma unroll
-                        for (int k = 0; k < kPanel; k += 2) {
-                            a0 -= lk[k] * Pn[(size_t)k * nmax + j];
-                            if (two) b0 -= lk[k] * Pn[(size_t)k * nmax + j2];
-                            a1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j];
-                            if (two) b1 -= lk[k + 1] * Pn[(size_t)(k + 1) * nmax + j2];
-                        }
-                        Li[j] = a0 + a1;
-                        if (two) Li[j2] = b0 + b1;
-                    }
-                }
-            }
-            // (b) + (c) warp 0: lane a < w reads row a of the diagonal block
-            // from its owner into registers, then the block's Cholesky runs on
-            // registers (the column loop unrolled, the other rows' entries by
-            // shuffles); the factored rows go to D.  Meanwhile warp 1 fetches
-            // the panel's rows of B (lane x < 6 holds column x), which it
-            // solves against D once D is complete: FP64 instructions issue
-            // slowly on this chip, so the chain of warp 0 carries only the
-            // block's own arithmetic.
-            double bcol[kPanel];
-            if (warp == 1 && lane < 6) {
-#pragma unroll
-                for (int r = 0; r < kPanel; ++r) {
-                    const int row = c0 + r;
-                    bcol[r] = r < w ? cluster.map_shared_rank(Br, row % kFacCluster)
-                                          [6 * (row / kFacCluster) + lane]
-                                    : 0.0;
-                }
-            }
+            double *D = Db + par * kPanel * kPanel, *Bd = Bb + par * 6 * kPanel;
+            // own rows below the panel: li >= li0
+            const int li0 = t0 > rank ? (t0 - rank + kFacCluster - 1) / kFacCluster : 0;
+            const int nr = nown > li0 ? nown - li0 : 0;
             if (warp == 0) {
-                double drow[kPanel];
-                const int row = c0 + lane;
-                const double *src = lane < w ? row_of(row) + c0 : nullptr;
-#pragma unroll
-                for (int b = 0; b < kPanel; ++b) drow[b] = lane < w && b <= lane ? rd(src + b) : 0.0;
+                // (A) the block's Cholesky on registers: lane l + 8 g holds
+                // entries (l, g) and (l, g + 4) (v0, v1), so that a pivot
+                // costs two FMAs per lane rather than one per later column;
+                // the column loop unrolled, the other lanes' entries by
+                // shuffles.  Entries above a row's diagonal may take finite
+                // junk and are never read.
+                const int l = lane & 7, g = lane >> 3;
+                double v0 = l < w && g <= l ? D[l * kPanel + g] : 0.0;
+                double v1 = l < w && g + 4 <= l ? D[l * kPanel + g + 4] : 0.0;
                 int f = 0;
 #pragma unroll
                 for (int c = 0; c < kPanel; ++c) {
                     if (c < w && !f) {
-                        const double d = __shfl_sync(0xffffffffu, drow[c], c);
+                        const int sc = 8 * (c & 3);  // lanes of column c: sc .. sc + 7
+                        double &vc = c < 4 ? v0 : v1;
+                        const double d = __shfl_sync(0xffffffffu, vc, c + sc);
                         if (!pivot_ok(d)) {
                             f = 1;  // the same value in every lane
                         } else {
-                            // selects instead of branches; entries above a
-                            // lane's diagonal may take junk and are never read
                             const double il = pivot_rsqrt(d);
                             if (lane == 0) ils[c0 + c] = il;
-                            drow[c] *= lane >= c ? il : 1.0;  // lane c: sqrt(d)
-                            const double lac = lane > c && lane < w ? drow[c] : 0.0;
-#pragma unroll
-                            for (int b = c + 1; b < kPanel; ++b)
-                                drow[b] -= lac * __shfl_sync(0xffffffffu, drow[c], b);
+                            vc *= g == (c & 3) && l >= c ? il : 1.0;  // lane (c, .): sqrt(d)
+                            double lac = __shfl_sync(0xffffffffu, vc, l + sc);  // L[l][c]
+                            lac = l > c && l < w ? lac : 0.0;
+                            if (c < 4) {
+                                const double x0 = __shfl_sync(0xffffffffu, vc, g + sc);  // L[g][c]
+                                v0 -= (g > c ? lac : 0.0) * x0;
+                            }
+                            const double x1 = __shfl_sync(0xffffffffu, vc, g + 4 + sc);  // L[g+4][c]
+                            v1 -= (g + 4 > c ? lac : 0.0) * x1;
                         }
                     }
                 }
-                if (lane < w) {
-#pragma unroll
-                    for (int b = 0; b < kPanel; ++b)
-                        if (b <= lane) D[lane * kPanel + b] = drow[b];
+                if (l < w) {
+                    if (g <= l) D[l * kPanel + g] = v0;
+                    if (g + 4 <= l) D[l * kPanel + g + 4] = v1;
                 }
                 if (lane == 0) fail_s = f;
+            } else if (hw >= 0 && c0 > 0) {
+                // (A) the previous panel's product out of own rows i >= t0
+                // (columns c0 .. i) and out of their B rows, in items of 32
+                // entries (one per lane, one FMA chain each) dealt to the
+                // warps in turn: row q's ceil((i - c0 + 1) / 32) items, then
+                // the B rows' ceil(6 nr / 32)
+                const int cp = c0 - kPanel;  // the previous panel is full
+                const double *Bp = Bb + (par ^ 1) * 6 * kPanel;
+                int item = 0;
+                for (int qq = 0; qq < nr; ++qq) {
+                    const int li = li0 + qq, i = rank + kFacCluster * li;
+                    const int nit = (i - c0 + 32) >> 5, it0 = item;
+                    item += nit;
+                    int it = it0 + ((hw - it0) % kHW + kHW) % kHW;  // this warp's first item here
+                    if (it >= item) continue;
+                    double *Li = own(li);
+                    double lk[kPanel];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) lk[k] = Li[cp + k];
+                    for (; it < item; it += kHW) {
+                        const int j = c0 + 32 * (it - it0) + lane;
+                        if (j <= i) {
+                            double a0 = Li[j];
+#pragma unroll
+                            for (int k = 0; k < kPanel; ++k) a0 -= lk[k] * Pn[(size_t)k * nmax + j];
+                            Li[j] = a0;
+                        }
+                    }
+                }
+                const int itb = item + ((hw - item) % kHW + kHW) % kHW;
+                for (int e = 32 * (itb - item) + lane; e < 6 * nr; e += 32 * kHW) {
+                    const int li = li0 + e / 6, x = e % 6;
+                    const double *Li = own(li) + cp;
+                    double a0 = Br[6 * li + x];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) a0 -= Li[k] * Bp[6 * k + x];
+                    Br[6 * li + x] = a0;
+                }
             }
             __syncthreads();
             if (fail_s) {  // uniform over the cluster
-                cluster.sync();  // every CTA has finished reading in (b)
+                cluster.sync();  // no CTA still reads another's rows
                 fail = 1;
                 break;
             }
-            // warp 1: the panel's B rows by forward substitution against D
-            // (Bd[r] = (B[c0 + r] - sum_{k<r} D[r][k] Bd[k]) / L_rr)
-            if (warp == 1 && lane < 6) {
+            // (B) the panel's B rows (groups 0..5, column x = group) and own
+            // rows i >= t0 (groups 6..), solved against the factored block
+            {
+                const int k = lane & 7, ng = nr + 6;
+                double dk[kPanel];
 #pragma unroll
-                for (int r = 0; r < kPanel; ++r) {
-                    if (r < w) {
-                        double v = bcol[r];
+                for (int j = 0; j < kPanel; ++j) dk[j] = j < k && k < w ? D[k * kPanel + j] : 0.0;
+                const double ilk = k < w ? ils[c0 + k] : 0.0;
+                for (int g0 = 4 * warp; g0 < ng; g0 += 4 * nw) {  // uniform over the warp
+                    const int g = g0 + (lane >> 3);
+                    double *dst = nullptr;
+                    double y = 0.0;
+                    if (g < ng && k < w) {
+                        dst = g < 6 ? Bd + 6 * k + g : own(li0 + g - 6) + c0 + k;
+                        y = *dst;
+                    }
+                    y = panel_solve8(y, dk, ilk, k, w, lane);
+                    if (dst) *dst = y;
+                }
+            }
+            cluster.sync();  // every CTA's panel entries are final
+            // (C) warps 0..4: the factored panel of rows t0..n-1 from their
+            // owners into Pn (remote loads issued in batches of kGather per
+            // thread before any store, so that their latencies overlap)
+            const int w2 = n - t0 < kPanel ? n - t0 : kPanel;  // the next panel's width
+            if (warp < 5) {
+                constexpr int kGather = 8;
+                const int total = (n - t0) * w, nt = 5 * 32;
+                for (int base = 0; base < total; base += kGather * nt) {
+                    double v[kGather];
+                    int dst[kGather];
 #pragma unroll
-                        for (int k = 0; k < kPanel; ++k)
-                            if (k < r) v -= D[r * kPanel + k] * bcol[k];
-                        bcol[r] = v * ils[c0 + r];
-                        Bd[6 * r + lane] = bcol[r];
+                    for (int u = 0; u < kGather; ++u) {
+                        const int e = base + threadIdx.x + u * nt;
+                        dst[u] = -1;
+                        if (e < total) {
+                            const int j = t0 + e / w, k = e % w;
+                            v[u] = rd(row_of(j) + c0 + k);
+                            dst[u] = k * nmax + j;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kGather; ++u)
+                        if (dst[u] >= 0) Pn[dst[u]] = v[u];
+                }
+            } else if (w2 > 0) {
+                // warps 5..7: the next diagonal block (entry (a, b), b <= a,
+                // 36 of them) and its B rows (entry (a, x), 48): the owners'
+                // entries minus this panel's product, which is full here
+                double *Dn = Db + (par ^ 1) * kPanel * kPanel, *Bn = Bb + (par ^ 1) * 6 * kPanel;
+                const int e = threadIdx.x - 5 * 32;
+                constexpr int kTri = kPanel * (kPanel + 1) / 2;
+                if (e < kTri) {
+                    int a = 0;
+                    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+                    const int b = e - a * (a + 1) / 2;
+                    if (a < w2) {
+                        const double *ra = row_of(t0 + a), *rb = row_of(t0 + b);
+                        double la[kPanel], lb[kPanel];
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k) {
+                            la[k] = rd(ra + c0 + k);
+                            lb[k] = rd(rb + c0 + k);
+                        }
+                        double a0 = rd(ra + t0 + b);
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k) a0 -= la[k] * lb[k];
+                        Dn[a * kPanel + b] = a0;
+                    }
+                } else if (e < kTri + 6 * kPanel) {
+                    const int a = (e - kTri) / 6, x = (e - kTri) % 6;
+                    if (a < w2) {
+                        const double *ra = row_of(t0 + a);
+                        double la[kPanel];
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k) la[k] = rd(ra + c0 + k);
+                        double a0 = brow_of(t0 + a)[x];
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k) a0 -= la[k] * Bd[6 * k + x];
+                        Bn[6 * a + x] = a0;
                     }
                 }
             }
-            // (d) own rows below the panel: L[i][c0 + k] by forward substitution,
-            // column-oriented (each x[k], once known, is subtracted from all
-            // later entries at once: a dependent chain of 2 w operations)
-            for (int li = threadIdx.x; li < nown; li += blockDim.x) {
-                const int i = rank + kFacCluster * li;
-                if (i < t0) continue;
-                double *Li = own(li) + c0;
-                double x[kPanel];
-#pragma unroll
-                for (int k = 0; k < kPanel; ++k) x[k] = k < w ? Li[k] : 0.0;
-#pragma unroll
-                for (int k = 0; k < kPanel; ++k) {
-                    if (k < w) {
-                        x[k] *= ils[c0 + k];
-#pragma unroll
-                        for (int kk = k + 1; kk < kPanel; ++kk)
-                            if (kk < w) x[kk] -= x[k] * D[kk * kPanel + k];
-                    }
+            // the owners of the block's rows store its factored rows and B rows
+            for (int e = threadIdx.x; e < kPanel * kPanel + 6 * kPanel; e += blockDim.x) {
+                if (e < kPanel * kPanel) {
+                    const int a = e / kPanel, b = e % kPanel, row = c0 + a;
+                    if (a < w && b <= a && row % kFacCluster == rank)
+                        own(row / kFacCluster)[c0 + b] = D[e];
+                } else {
+                    const int eb = e - kPanel * kPanel, row = c0 + eb / 6;
+                    if (eb / 6 < w && row % kFacCluster == rank)
+                        Br[6 * (row / kFacCluster) + eb % 6] = Bd[eb];
                 }
-#pragma unroll
-                for (int k = 0; k < kPanel; ++k)
-                    if (k < w) Li[k] = x[k];
-            }
-            cluster.sync();  // (f) every CTA's panel entries are final
-            // (g) the factored panel of rows t0..n-1 from their owners; the owners
-            // of the diagonal block's rows store its factored rows and B rows
-            // (remote loads issued in batches of kGather per thread before any
-            // store, so that their latencies overlap)
-            constexpr int kGather = 5;
-            const int total = (n - t0) * w;
-            for (int base = 0; base < total; base += kGather * (int)blockDim.x) {
-                double v[kGather];
-                int dst[kGather];
-#pragma unroll
-                for (int u = 0; u < kGather; ++u) {
-                    const int e = base + threadIdx.x + u * (int)blockDim.x;
-                    dst[u] = -1;
-                    if (e < total) {
-                        const int j = t0 + e / w, k = e % w;
-                        v[u] = rd(row_of(j) + c0 + k);
-                        dst[u] = k * nmax + j;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kGather; ++u)
-                    if (dst[u] >= 0) Pn[dst[u]] = v[u];
-            }
-            for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-                const int a = e / w, b = e % w, row = c0 + a;
-                if (row % kFacCluster == rank && b <= a) own(row / kFacCluster)[c0 + b] = D[a * kPanel + b];
-            }
-            for (int e = threadIdx.x; e < 6 * w; e += blockDim.x) {
-                const int row = c0 + e / 6;
-                if (row % kFacCluster == rank) Br[6 * (row / kFacCluster) + e % 6] = Bd[e];
             }
             __syncthreads();
-            // (h1) the next panel's columns [t0, t0 + kPanel) of own rows
-            // i >= t0, one entry per thread: the next panel's diagonal chain
-            // and row solves need them.  The rest of the trailing update,
-            // (h2), runs during that chain.  Each entry takes the same
-            // operations in the same order as in one pass.
-            // ... together with the own rows of B (entries after the first
-            // nown * kPanel of the loop), so that both take the same pass
-            const int h1n = nown * kPanel;
-            for (int e = threadIdx.x; e < h1n + 6 * nown; e += blockDim.x) {
-                if (e < h1n) {
-                    const int li = e / kPanel, q = e - li * kPanel;
-                    const int i = rank + kFacCluster * li, j = t0 + q;
-                    if (i < t0 || j > i) continue;
-                    double *Li = own(li);
-                    double a0 = Li[j], a1 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < kPanel; k += 2) {
-                        if (k < w) a0 -= Li[c0 + k] * Pn[(size_t)k * nmax + j];
-                        if (k + 1 < w) a1 -= Li[c0 + k + 1] * Pn[(size_t)(k + 1) * nmax + j];
-                    }
-                    Li[j] = a0 + a1;
-                } else {
-                    const int eb = e - h1n;
-                    const int li = eb / 6, x = eb - 6 * li;
-                    if (rank + kFacCluster * li < t0) continue;
-                    const double *Li = own(li) + c0;
-                    double a0 = Br[eb], a1 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < kPanel; k += 2) {
-                        if (k < w) a0 -= Li[k] * Bd[6 * k + x];
-                        if (k + 1 < w) a1 -= Li[k + 1] * Bd[6 * (k + 1) + x];
-                    }
-                    Br[eb] = a0 + a1;
-                }
-            }
         }
         if (fail) {
             if (rank == 0 && threadIdx.x == 0) {
@@ -1022,11 +1069,11 @@ __global__ void __cluster_dims__(kFacCluster, 1, 1) __launch_bounds__(256, 2) pc
                 double acc = 0.0;
                 for (int rr = 0; rr < kFacCluster; ++rr)
                     acc += cluster.map_shared_rank(Sp, rr)[threadIdx.x];
-                D[threadIdx.x] = acc;  // the 36 entries of S (the block is free now)
+                Db[threadIdx.x] = acc;  // the 36 entries of S (the blocks are free now)
             }
             __syncthreads();
             if (warp == 0) {
-                const int f = inverse6_warp(D, Nm, lane);
+                const int f = inverse6_warp(Db, Nm, lane);
                 if (lane == 0) bad = f ? schur : 0;
             }
             __syncthreads();
