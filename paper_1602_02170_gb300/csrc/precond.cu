@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(256) precond_apply_kernel(
 // Split setup for bodies with 3 n_p <= kSplitMaxRows.  The single kernel
 // above runs every step of a body on one SM; here only the Cholesky does,
 // and the O(n^3) rest is spread over many CTAs:
-//   S1 pc_assemble_kernel  M_p written into P_p's n x n block (warp per blob row);
+//   S1 pc_assemble_kernel  M_p's lower triangle written into P_p's n x n block
+//                          (warp per blob row and 32 columns);
 //   S2 pc_factor_kernel    one CTA per body: Cholesky M_p = L L^T carried out
 //                          together with G = L^-1 K_p (the six K columns are
 //                          eliminated alongside), then S = G^T G = K^T M^-1 K,
@@ -449,7 +450,11 @@ struct SplitScratch {
 
 int64_t split_stride(int nmax) { return (int64_t)nmax * nmax + 19 * (int64_t)nmax + 36; }
 
-// S1: M_p (scaled) into P_p[0:n, 0:n], row stride m = n + 6.
+// S1: M_p (scaled) into P_p[0:n, 0:n], row stride m = n + 6: the blocks on
+// and below the diagonal (bj <= bi), the only ones the factorisations read
+// (M_p is symmetric), one warp per blob row and 32 columns (blockIdx.y).
+// Launched with small CTAs so that the rows of a few bodies still reach
+// every SM: the blocks' dependent FP64 arithmetic is the cost.
 template <bool WALL>
 __global__ void __launch_bounds__(256) pc_assemble_kernel(
     int64_t nb, const double *__restrict__ r, const int64_t *__restrict__ start,
@@ -467,7 +472,8 @@ __global__ void __launch_bounds__(256) pc_assemble_kernel(
         const int np = (int)(start[p + 1] - b0), bi = (int)(b - b0);
         const int m = 3 * np + 6;
         double *Pp = P + poff[p];
-        for (int bj = lane; bj < np; bj += 32) {
+        const int bj = 32 * (int)blockIdx.y + lane;
+        if (bj <= bi) {
             double blk[9];
             block_f64<WALL>(r + 3 * b, r + 3 * (b0 + bj), k, blk);
 #pragma unroll
@@ -1214,16 +1220,32 @@ __global__ void __launch_bounds__(256) pc_to_df_kernel(int64_t nb,
 // double-float, the border entries -Q N of P_p in FP64.  1 / L_kk travels
 // through the chain by shuffles from registers.  With STAGE (few bodies,
 // where the chain's latency is the time) the CTA first copies the packed
-// rows of L^T that its eight columns need (from its first column on) and
-// their rows of G into shared memory, so that no step of a chain waits on
-// L2; with many bodies the CTAs stay small and read them from L2.
+// rows of L^T that its columns need (from its first column on; row k holds
+// entries k+1 .. n-1, rows back to back) and their rows of G into shared
+// memory, so that no step of a chain waits on L2.  It is launched then with
+// four warps, one per SM sub-partition, so that the long chains of the first
+// columns do not share an issue slot.  With many bodies the CTAs stay small
+// and read L^T and G from L2.
+__device__ __forceinline__ void cp_async8(double *smem, const double *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Offset of row k of the staged triangle (rows cmin ..), n rows in all
+__device__ __forceinline__ int tri_row_off(int k, int cmin, int n)
+{
+    return (k - cmin) * (2 * (n - 1) - (cmin + k - 1)) / 2;
+}
 template <bool STAGE>
 __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     double *__restrict__ P, SplitScratch scr, int col_groups)
 {
     constexpr int R = 4;
-    extern __shared__ double sLt[];  // rows cmin .. n-1 of L^T (packed), row stride n; then G
+    extern __shared__ double sLt[];  // rows cmin .. n-1 of L^T (packed triangle); then G
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
         const int64_t p = item / col_groups;
@@ -1232,36 +1254,23 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
         const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
         // row k of L^T at Lk + (k - cmin) * ldl, row k of G at Gk + 6 (k - cmin)
         const double *Lk = P + poff[p] + (size_t)cmin * m, *Gk = scr.G(p) + 6 * cmin;
-        int ldl = m;
+        const int ldl = m;
         if constexpr (STAGE) {
-            double *sG = sLt + (size_t)(n - cmin) * n;
+            double *sG = sLt + (cmin < n ? tri_row_off(n, cmin, n) : 0);
             __syncthreads();  // the previous item is finished with sLt
             if (cmin < n) {
-                // batches of kBatch loads per thread in flight before their stores
-                constexpr int kBatch = 8;
+                // asynchronous copies, all in flight at once: a warp per row
                 const double *Lg = P + poff[p];
-                const int total = (n - cmin) * n;
-                for (int e0 = threadIdx.x; e0 < total; e0 += kBatch * (int)blockDim.x) {
-                    double v[kBatch];
-#pragma unroll
-                    for (int b = 0; b < kBatch; ++b) {
-                        const int e = e0 + b * (int)blockDim.x;
-                        const int k = cmin + e / n, i = e % n;
-                        v[b] = e < total && i > k ? Lg[(size_t)k * m + i] : 0.0;
-                    }
-#pragma unroll
-                    for (int b = 0; b < kBatch; ++b) {
-                        const int e = e0 + b * (int)blockDim.x;
-                        if (e < total) sLt[e] = v[b];
-                    }
+                for (int k = cmin + warp; k < n; k += nw) {
+                    double *dst = sLt + tri_row_off(k, cmin, n) - (k + 1);
+                    for (int i = k + 1 + lane; i < n; i += 32) cp_async8(dst + i, Lg + (size_t)k * m + i);
                 }
                 for (int e = threadIdx.x; e < 6 * (n - cmin); e += blockDim.x)
-                    sG[e] = scr.G(p)[6 * cmin + e];
+                    cp_async8(sG + e, scr.G(p) + 6 * cmin + e);
+                cp_async_wait_all();
             }
             __syncthreads();
-            Lk = sLt;
             Gk = sG;
-            ldl = n;
         }
         if (c >= n) continue;  // warp-uniform
         double *W = scr.W(p);
@@ -1277,24 +1286,66 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
         dfl dwr[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) dwr[t] = 32 * t + lane < n ? df_unpack(dW[32 * t + lane]) : dfl();
+        if constexpr (STAGE) {
+            // per tile of 32 rows: the chain of its steps updates only the
+            // tile's own rows; the tile's product out of the rows below it
+            // and its share of Q follow, off the chain (each entry takes the
+            // same operations in the same order as in one pass)
+            dfl ws[R];  // lane l of tile t: W[32 t + l][c]
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            if (32 * t + 31 < c) continue;
-            if (32 * t >= n) break;
-            for (int l = 0; l < 32; ++l) {
-                const int k = 32 * t + l;
-                if (k < c) continue;
-                if (k >= n) break;
-                const dfl wl(__shfl_sync(0xffffffffu, w[t].hi, l), __shfl_sync(0xffffffffu, w[t].lo, l));
-                const dfl dk(__shfl_sync(0xffffffffu, dwr[t].hi, l), __shfl_sync(0xffffffffu, dwr[t].lo, l));
-                const dfl wk = wl * dk;
-                if (lane == l) W[(size_t)k * ldw + c] = df_pack(wk);
-                if (lane < 6) qa += wk * df_unpack(Gk[6 * (k - cmin) + lane]);
-                const double *lk = Lk + (size_t)(k - cmin) * ldl;
+            for (int t = 0; t < R; ++t) {
+                ws[t] = dfl();
+                if (32 * t + 31 < c) continue;
+                if (32 * t >= n) break;
+                const int i = 32 * t + lane;
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 * t + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl lik = i > k && i < n ? df_unpack(sLt[tri_row_off(k, cmin, n) - (k + 1) + i])
+                                                   : dfl();
+                    const dfl wl(__shfl_sync(0xffffffffu, w[t].hi, l), __shfl_sync(0xffffffffu, w[t].lo, l));
+                    const dfl dk(__shfl_sync(0xffffffffu, dwr[t].hi, l), __shfl_sync(0xffffffffu, dwr[t].lo, l));
+                    const dfl wk = wl * dk;
+                    ws[t] = lane == l ? wk : ws[t];
+                    const dfl wn = w[t] - lik * wk;
+                    w[t] = i > k && i < n ? wn : w[t];
+                }
+                if (i >= c && i < n) W[(size_t)i * ldw + c] = df_pack(ws[t]);
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 * t + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wk(__shfl_sync(0xffffffffu, ws[t].hi, l), __shfl_sync(0xffffffffu, ws[t].lo, l));
+                    if (lane < 6) qa += wk * df_unpack(Gk[6 * (k - cmin) + lane]);
+                    const double *lk = sLt + tri_row_off(k, cmin, n) - (k + 1);
 #pragma unroll
-                for (int t2 = t; t2 < R; ++t2) {
-                    const int i = 32 * t2 + lane;
-                    if (i > k && i < n) w[t2] = w[t2] - df_unpack(lk[i]) * wk;
+                    for (int t2 = t + 1; t2 < R; ++t2) {
+                        const int i2 = 32 * t2 + lane;
+                        if (i2 < n) w[t2] = w[t2] - df_unpack(lk[i2]) * wk;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                if (32 * t + 31 < c) continue;
+                if (32 * t >= n) break;
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 * t + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wl(__shfl_sync(0xffffffffu, w[t].hi, l), __shfl_sync(0xffffffffu, w[t].lo, l));
+                    const dfl dk(__shfl_sync(0xffffffffu, dwr[t].hi, l), __shfl_sync(0xffffffffu, dwr[t].lo, l));
+                    const dfl wk = wl * dk;
+                    if (lane == l) W[(size_t)k * ldw + c] = df_pack(wk);
+                    if (lane < 6) qa += wk * df_unpack(Gk[6 * (k - cmin) + lane]);
+                    const double *lk = Lk + (size_t)(k - cmin) * ldl;  // row k of L^T
+#pragma unroll
+                    for (int t2 = t; t2 < R; ++t2) {
+                        const int i = 32 * t2 + lane;
+                        if (i > k && i < n) w[t2] = w[t2] - df_unpack(lk[i]) * wk;
+                    }
                 }
             }
         }
@@ -1315,47 +1366,51 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
     }
 }
 
-// S4 in double-float: P_p's n x n block = W^T W - (Q N) Q^T in 32 x 32 tiles
-// (as pc_product_kernel), the tiles of W staged in shared memory as
-// double-float, the result stored in FP64.
+// S4 in double-float: P_p's n x n block = W^T W - (Q N) Q^T in TILE x TILE
+// tiles (as pc_product_kernel; 16 x 16 when there are few bodies, so that the
+// tiles reach more SMs), the tiles of W staged in shared memory as
+// double-float, the result stored in FP64.  256 threads: thread (ty, tx)
+// forms rows ty + (256 / TILE) rr of the tile's column tx.
+template <int TILE>
 __global__ void __launch_bounds__(256) pc_product_df_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     double *__restrict__ P, SplitScratch scr, int tiles_per_body, int schur)
 {
-    __shared__ dfl Wi[kTile][kTile + 1], Wj[kTile][kTile + 1];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    constexpr int kRows = 256 / TILE, kRR = TILE / kRows;
+    __shared__ dfl Wi[TILE][TILE + 1], Wj[TILE][TILE + 1];
+    const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
     for (int64_t item = blockIdx.x; item < nb * tiles_per_body; item += gridDim.x) {
         const int64_t p = item / tiles_per_body;
         int I, J;
         tri_index((int)(item % tiles_per_body), I, J);
         const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
-        const int i0 = I * kTile, j0 = J * kTile;
+        const int i0 = I * TILE, j0 = J * TILE;
         if (i0 >= n) continue;  // CTA-uniform
         const double *W = scr.W(p);
         const int ldw = scr.nmax;
-        dfl acc[4];
-        for (int k0 = i0; k0 < n; k0 += kTile) {
+        dfl acc[kRR];
+        for (int k0 = i0; k0 < n; k0 += TILE) {
             __syncthreads();
-            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-                const int kk = e / kTile, cc = e % kTile;
+            for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+                const int kk = e / TILE, cc = e % TILE;
                 const int k = k0 + kk;
                 Wi[kk][cc] = (k < n && i0 + cc < n) ? df_unpack(W[(size_t)k * ldw + i0 + cc]) : dfl();
                 Wj[kk][cc] = (k < n && j0 + cc < n) ? df_unpack(W[(size_t)k * ldw + j0 + cc]) : dfl();
             }
             __syncthreads();
 #pragma unroll 4
-            for (int kk = 0; kk < kTile; ++kk) {
+            for (int kk = 0; kk < TILE; ++kk) {
                 const dfl wj = Wj[kk][tx];
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr) acc[rr] += Wi[kk][ty + 8 * rr] * wj;
+                for (int rr = 0; rr < kRR; ++rr) acc[rr] += Wi[kk][ty + kRows * rr] * wj;
             }
         }
         const double *Qs = scr.Q(p), *QN = scr.QN(p);
         double *Pp = P + poff[p];
         const int j = j0 + tx;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const int i = i0 + ty + 8 * rr;
+        for (int rr = 0; rr < kRR; ++rr) {
+            const int i = i0 + ty + kRows * rr;
             if (i >= n || j >= n || (I == J && j > i)) continue;
             dfl v = acc[rr];
             if (schur)
@@ -1520,11 +1575,12 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
         const int64_t ng = std::min(group, nb - g0);
         const int64_t *st = start + g0;
         const int64_t *po = poff + g0;
-        const int ga = (int)std::min<int64_t>(ceil_div(ng * max_np, 8), 8 * (int64_t)ctx->sm_count);
+        const dim3 ga((unsigned)std::min<int64_t>(ceil_div(ng * max_np, 2), 32 * (int64_t)ctx->sm_count),
+                      (unsigned)ceil_div(max_np, 32));
         if (wall)
-            pc_assemble_kernel<true><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
+            pc_assemble_kernel<true><<<ga, 64, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         else
-            pc_assemble_kernel<false><<<ga, 256, 0, s>>>(ng, r, st, po, k, scale, P, shift);
+            pc_assemble_kernel<false><<<ga, 64, 0, s>>>(ng, r, st, po, k, scale, P, shift);
         if (ng < ctx->sm_count) {
             // fewer bodies than SMs: a cluster of CTAs per body, the rows in
             // shared memory or in place in global memory
@@ -1561,16 +1617,22 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
             const int gc = (int)std::min<int64_t>(ceil_div(ng * nmax, 8), 8 * (int64_t)ctx->sm_count);
             pc_to_df_kernel<<<gc, 256, 0, s>>>(ng, st, po, P, scr);
             if (ng < ctx->sm_count) {
-                const size_t tsm = sizeof(double) * (size_t)nmax * (nmax + 6);
+                // four columns per CTA; the staged triangle of L^T and G
+                const int cg4 = (int)ceil_div(nmax, 4);
+                const int gt4 = (int)std::min<int64_t>(ng * cg4, 16 * (int64_t)ctx->sm_count);
+                const size_t tsm = sizeof(double) * ((size_t)nmax * (nmax - 1) / 2 + 6 * (size_t)nmax);
                 MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_trinv_df_kernel<true>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)tsm));
-                pc_trinv_df_kernel<true><<<gt, 256, tsm, s>>>(ng, st, po, P, scr, col_groups);
+                pc_trinv_df_kernel<true><<<gt4, 128, tsm, s>>>(ng, st, po, P, scr, cg4);
+                const int T16 = (int)ceil_div(nmax, 16), tiles16 = T16 * (T16 + 1) / 2;
+                const int gp = (int)std::min<int64_t>(ng * tiles16, 16 * (int64_t)ctx->sm_count);
+                pc_product_df_kernel<16><<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles16, schur);
             } else {
                 pc_trinv_df_kernel<false><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+                const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
+                pc_product_df_kernel<kTile><<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles, schur);
             }
-            const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
-            pc_product_df_kernel<<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles, schur);
             count_launch(5);
             MB_CUDA_TRY(ctx, cudaGetLastError());
             continue;
