@@ -167,7 +167,8 @@ struct Small {
 };
 
 // Start a cycle: g = [beta, 0, ...], beta = sqrt(nrm2); beta is posted like
-// the Arnoldi steps' estimates (post: mapped host memory [value, count])
+// the Arnoldi steps' estimates (post: mapped host memory [value, count, step
+// word]; a cycle start writes the first two, in FP64, behind a fence)
 __global__ void cycle_start_kernel(double *__restrict__ sm, Small L, double *__restrict__ post,
                                    unsigned long long *__restrict__ seq)
 {
@@ -182,6 +183,16 @@ __global__ void cycle_start_kernel(double *__restrict__ sm, Small L, double *__r
         __threadfence_system();
         *(volatile unsigned long long *)(post + 1) = q;
     }
+}
+
+// The latest posted count in the mapped words [value, count, step word]: a
+// cycle start's full count, or a later step's (its low 32 bits ahead of it).
+static unsigned long long posted_count(const double *hp)
+{
+    const unsigned long long c1 = *(volatile const unsigned long long *)(hp + 1);
+    const unsigned long long w = *(volatile const unsigned long long *)(hp + 2);
+    const int32_t d = (int32_t)((uint32_t)(w >> 32) - (uint32_t)c1);
+    return d > 0 ? c1 + (unsigned long long)d : c1;
 }
 
 // Column j of H is h[0..j] with H[j+1, j] = sqrt(nrm2); apply the previous
@@ -335,10 +346,10 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem) : "memory");
 }
 
-// post (optional): mapped host memory [est, step count]; rank 0 writes the
-// residual estimate, then (after a system-scope fence) the incremented count
-// kept at *seq, so that the host can read the estimate without a stream
-// synchronisation.
+// post (optional): mapped host memory [value, count, step word]; rank 0
+// writes the step word, the incremented count kept at *seq (low 32 bits)
+// over the residual estimate in FP32, in one 8-byte store, so that the host
+// can read the estimate without a stream synchronisation.
 //
 // When staged, the slices are held in T (the passes' arithmetic), so that
 // FP32 passes convert each element once instead of at every use, and the
@@ -524,11 +535,13 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             sm[S.est()] = fabs(-sg * gj);
             sm[S.nrm2()] = nrm2;
             if (post) {
+                // one 8-byte store, so that no system-scope fence holds the
+                // step: the count's low 32 bits over the estimate in FP32
+                // (the precision of the inner stopping test it serves)
                 const unsigned long long q = (unsigned long long)__double_as_longlong(red[17]) + 1;
                 *seq = q;
-                post[0] = fabs(-sg * gj);
-                __threadfence_system();
-                *(volatile unsigned long long *)(post + 1) = q;
+                const float e32 = (float)fabs(-sg * gj);
+                *(volatile unsigned long long *)(post + 2) = (q << 32) | __float_as_uint(e32);
             }
         }
         __syncthreads();
@@ -790,17 +803,29 @@ struct Solver {
         count_launch();
     }
 
-    // The estimate posted by the step just launched: poll the mapped count for
-    // up to 2 ms, then fall back to a stream synchronisation (long steps, or
-    // no mapped memory), which also resynchronises the count.
-    mb_status read_posted_est(double *est)
+    // The estimate posted by the kernel just launched: poll the mapped count
+    // for up to 2 ms, then fall back to a stream synchronisation (long steps,
+    // or no mapped memory), which also resynchronises the count.  A cycle
+    // start posts [value, count] in FP64 behind a fence; an Arnoldi step
+    // (`step`) posts one word, the count's low 32 bits over an FP32 estimate.
+    mb_status read_posted_est(double *est, bool step = false)
     {
         if (!ctx->host_post) return read_est(est);
         const unsigned long long want = ++ctx->post_seq;
         volatile unsigned long long *cnt = (volatile unsigned long long *)(ctx->host_post + 1);
+        volatile unsigned long long *word = (volatile unsigned long long *)(ctx->host_post + 2);
         const auto t0 = std::chrono::steady_clock::now();
         for (long it = 0;; ++it) {
-            if (*cnt >= want) {
+            if (step) {
+                const unsigned long long wv = *word;
+                if ((int32_t)((uint32_t)(wv >> 32) - (uint32_t)want) >= 0) {
+                    const uint32_t bits = (uint32_t)wv;
+                    float e;
+                    std::memcpy(&e, &bits, sizeof e);
+                    *est = (double)e;
+                    return MB_OK;
+                }
+            } else if (*cnt >= want) {
                 std::atomic_thread_fence(std::memory_order_acquire);
                 *est = *(volatile double *)ctx->host_post;
                 return MB_OK;
@@ -817,7 +842,7 @@ struct Solver {
             }
         }
         MB_TRY(read_est(est));
-        ctx->post_seq = *cnt;  // the stream is idle: every posting has arrived
+        ctx->post_seq = posted_count(ctx->host_post);  // the stream is idle: every posting has arrived
         return MB_OK;
     }
 
@@ -981,7 +1006,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
     const auto t1 = clk::now();
     // the stream is idle, so every posting of earlier calls has arrived (an
     // earlier call that ran out of its wait limit may have left some behind)
-    if (ctx->host_post) ctx->post_seq = *(volatile unsigned long long *)(ctx->host_post + 1);
+    if (ctx->host_post) ctx->post_seq = posted_count(ctx->host_post);
 
     Solver S;
     S.resist = resist != 0;
@@ -1135,7 +1160,7 @@ static mb_status solve_rigid(mb_context *ctx, int resist, int64_t nb, int64_t n,
                     }
                     if (!ran) MB_TRY(step(s));
                     double est = 0.0;
-                    MB_TRY(S.read_posted_est(&est));
+                    MB_TRY(S.read_posted_est(&est, true));
                     if (!(est > inner_abs)) break;
                     continue;
                 }
