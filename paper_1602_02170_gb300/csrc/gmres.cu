@@ -363,12 +363,12 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    // shared (slots of 8 bytes): part[3][m + 1] partial sums (pass 0, pass 1,
-    // |w|^2), one spare row, hc[m + 2] merged column j of H, cs[m], sn[m]
-    // previous rotations (rank 0), red[32] block partials, hT[m + 1] the
-    // summed coefficients, then (stage != 0) the staged slices sV[(j + 2) x
-    // per].  The partial sums, H's column, the rotations and the block
-    // partials are held in T: with FP32 inner iterations (mixed precision)
+    // shared (slots of 8 bytes): part[2][m + 1] partial sums (pass 0; pass 1
+    // with |w|^2 after pass 0 at j + 1), two spare rows, hc[m + 2] merged
+    // column j of H, cs[m], sn[m] previous rotations (rank 0), red[32]
+    // scalars, hT[m + 1] the summed coefficients, then (stage != 0) the
+    // staged slices sV[(j + 2) x per].  The partial sums, H's column and the
+    // rotations are held in T: with FP32 inner iterations (mixed precision)
     // the serial sums, the norm and the Givens update then run on the FP32
     // pipe, where a dependent operation takes a few cycles instead of the
     // ~64 of FP64 on this chip; the Hessenberg entries have the FP32
@@ -380,7 +380,6 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
     T *cs = (T *)(part + 4 * m1 + S.m + 2);
     T *sn = (T *)(part + 4 * m1 + 2 * S.m + 2);
     double *red = part + 4 * m1 + 3 * S.m + 2;
-    T *redT = (T *)red;
     T *hT = (T *)(red + 32);
     T *sV = (T *)(red + 32 + m1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -460,9 +459,16 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         if (stage) sV[(int64_t)(j + 1) * per + k] = v;
         else w[e0 + k] = double(v);
     };
+    // The second pass also sums |w|^2 (entry j + 1), w as the first pass
+    // left it; the norm after the second pass then follows without another
+    // reduction: |w2|^2 = |w1|^2 - sum_i h2_i^2, the coefficients h2 being of
+    // rounding size against |w1| (the Pythagorean norm of low-synchronisation
+    // CGS2), in every CTA alike from the same sums.
+    T n1 = T(0);
     for (int pass = 0; pass < 2; ++pass) {
         T *pp = (T *)(part + pass * m1);
-        for (int i = warp; i <= j; i += nw) {
+        const int top = j + pass;  // entry j + 1 of the second pass: |w|^2
+        for (int i = warp; i <= top; i += nw) {
             T acc = T(0);
             for (int k = lane; k < cnt; k += 32) acc += ld(i, k) * ld(j + 1, k);
 #pragma unroll
@@ -470,13 +476,14 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
             if (lane == 0) pp[i] = acc;
         }
         cluster.sync();  // every CTA's partials of this pass are written
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        for (int i = threadIdx.x; i <= top; i += blockDim.x) {
             T acc = T(0);
             for (int rr = 0; rr < kOrthCluster; ++rr) acc += cluster.map_shared_rank(pp, rr)[i];
             hT[i] = acc;
-            hc[i] = pass == 0 ? acc : hc[i] + acc;
+            if (i <= j) hc[i] = pass == 0 ? acc : hc[i] + acc;
         }
         __syncthreads();
+        if (pass == 1) n1 = hT[j + 1];
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             T acc = ld(j + 1, k);
             for (int i = 0; i <= j; ++i) acc -= ld(i, k) * hT[i];
@@ -484,27 +491,11 @@ __global__ void __cluster_dims__(kOrthCluster, 1, 1) __launch_bounds__(kOrthClus
         }
         __syncthreads();  // hs, hT are rewritten by the next pass; w is final
     }
-    T *pn = (T *)(part + 2 * m1);
-    T acc = T(0);
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const T v = ld(j + 1, k);
-        acc += v * v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) redT[warp] = acc;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        T t = T(0);
-        for (int k = 0; k < nw; ++k) t += redT[k];
-        pn[0] = t;
-    }
-    cluster.sync();  // every CTA's |w|^2 partial is written
-    if (threadIdx.x == 0) {
-        T t = T(0);
-        for (int rr = 0; rr < kOrthCluster; ++rr) t += cluster.map_shared_rank(pn, rr)[0];
+        T t = n1;
+        for (int i = 0; i <= j; ++i) t -= hT[i] * hT[i];
         const T y = t > T(0) ? rsqrt_t(t) : T(0);  // 1 / |w|
-        red[0] = double(t);
+        red[0] = double(t > T(0) ? t : T(0));
         red[1] = double(y);
     }
     __syncthreads();
