@@ -1222,10 +1222,10 @@ __global__ void __launch_bounds__(256) pc_to_df_kernel(int64_t nb,
 // where the chain's latency is the time) the CTA first copies the packed
 // rows of L^T that its columns need (from its first column on; row k holds
 // entries k+1 .. n-1, rows back to back) and their rows of G into shared
-// memory, so that no step of a chain waits on L2.  It is launched then with
-// four warps, one per SM sub-partition, so that the long chains of the first
-// columns do not share an issue slot.  With many bodies the CTAs stay small
-// and read L^T and G from L2.
+// memory, so that no step of a chain waits on L2 (the staged form; the setup
+// launches pc_trinv_df_pair_kernel for few bodies, which splits each column
+// over a pair of warps).  With many bodies the CTAs stay small and read L^T
+// and G from L2.
 __device__ __forceinline__ void cp_async8(double *smem, const double *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -1362,6 +1362,194 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
             const double v = -to_double(qn);
             P[poff[p] + (size_t)c * m + n + lane] = v;
             P[poff[p] + (size_t)(n + lane) * m + c] = v;
+        }
+    }
+}
+
+// One 32-row tile t of a column's chain (the steps of pc_trinv_df_kernel):
+// lane l holds row 32 t + l in wt; the step of row k leaves W[k][c] in lane
+// k - 32 t of wst and updates only the tile's own rows.
+__device__ __forceinline__ void trinv_tile_chain(int t, int c, int n, int cmin,
+                                                 const double *__restrict__ sLt, dfl &wt, dfl dwrt,
+                                                 dfl &wst, int lane)
+{
+    const int i = 32 * t + lane;
+    for (int l = 0; l < 32; ++l) {
+        const int k = 32 * t + l;
+        if (k < c) continue;
+        if (k >= n) break;
+        const dfl lik = i > k && i < n ? df_unpack(sLt[tri_row_off(k, cmin, n) - (k + 1) + i]) : dfl();
+        const dfl wl(__shfl_sync(0xffffffffu, wt.hi, l), __shfl_sync(0xffffffffu, wt.lo, l));
+        const dfl dk(__shfl_sync(0xffffffffu, dwrt.hi, l), __shfl_sync(0xffffffffu, dwrt.lo, l));
+        const dfl wk = wl * dk;
+        wst = lane == l ? wk : wst;
+        const dfl wn = wt - lik * wk;
+        wt = i > k && i < n ? wn : wt;
+    }
+}
+
+// S3 in double-float for few bodies (rows n <= 128): four columns per CTA,
+// a pair of warps per column.  Warp A holds the column's rows 0..63 (tiles
+// 0, 1), warp B rows 64..127 (tiles 2, 3).  The pace is set by a warp's
+// instruction count (about 5 cycles each: every step is a dependent chain),
+// so the pair splits the column's work in three phases between barriers:
+//   1. A runs tile 0's chain and leaves its W entries in shared memory;
+//   2. A subtracts tile 0's product from tile 1, runs tile 1 and leaves its
+//      entries and Q's sums over tiles 0, 1; meanwhile B subtracts tile 0's
+//      product from its rows;
+//   3. B subtracts tile 1's product, runs tiles 2 and 3 and carries Q on
+//      from A's sums.
+// Every entry takes the same operations in the same order as in one warp
+// (pc_trinv_df_kernel).  L^T is staged in shared memory as a packed
+// triangle with cp.async, as pc_trinv_df_kernel<true> does.
+__global__ void __launch_bounds__(256) pc_trinv_df_pair_kernel(
+    int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
+    double *__restrict__ P, SplitScratch scr, int col_groups)
+{
+    constexpr int kCols = 4;
+    extern __shared__ double sLt[];  // L^T rows cmin .. n-1 (packed triangle), G rows, exchange
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int q = warp >> 1, role = warp & 1;
+    const int nmax = scr.nmax;
+    dfl *xw = (dfl *)(sLt + (size_t)nmax * (nmax - 1) / 2 + 6 * (size_t)nmax);  // [kCols][2][32]
+    dfl *xq = xw + kCols * 2 * 32;                                               // [kCols][6]
+    for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
+        const int64_t p = item / col_groups;
+        const int cmin = (int)(item % col_groups) * kCols;
+        const int c = cmin + q;
+        const int n = 3 * (int)(start[p + 1] - start[p]), m = n + 6;
+        double *sG = sLt + (cmin < n ? tri_row_off(n, cmin, n) : 0);
+        __syncthreads();  // the previous item is finished with the shared arrays
+        if (cmin < n) {
+            // asynchronous copies, all in flight at once: a warp per row
+            const double *Lg = P + poff[p];
+            for (int k = cmin + warp; k < n; k += nw) {
+                double *dst = sLt + tri_row_off(k, cmin, n) - (k + 1);
+                for (int i = k + 1 + lane; i < n; i += 32) cp_async8(dst + i, Lg + (size_t)k * m + i);
+            }
+            for (int e = threadIdx.x; e < 6 * (n - cmin); e += blockDim.x)
+                cp_async8(sG + e, scr.G(p) + 6 * cmin + e);
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const bool active = c < n;  // the same in both warps of the pair
+        double *W = scr.W(p);
+        const double *dW = scr.dW(p), *Nm = scr.N(p);
+        const int ldw = scr.nmax;
+        // this warp's tiles 2 role + tt: rows 64 role + 32 tt + lane
+        dfl w[2], ws[2], dwr[2];
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) {
+            const int i = 64 * role + 32 * tt + lane;
+            w[tt] = dfl(i == c ? 1.f : 0.f, 0.f);
+            ws[tt] = dfl();
+            dwr[tt] = i < n ? df_unpack(dW[i]) : dfl();
+        }
+        dfl qa;  // lane b < 6: Q[c][b]
+        // whether tile t holds steps of column c
+        auto has = [&](int t) { return 32 * t + 31 >= c && 32 * t < n; };
+        // (1) A: tile 0
+        if (active && role == 0) {
+            // zero the rows of column c that the tiled product reads above the diagonal
+            for (int kk = (c & ~(kTile - 1)) + lane; kk < c; kk += 32) W[(size_t)kk * ldw + c] = 0.0;
+            if (has(0)) {
+                trinv_tile_chain(0, c, n, cmin, sLt, w[0], dwr[0], ws[0], lane);
+                if (lane >= c && lane < n) W[(size_t)lane * ldw + c] = df_pack(ws[0]);
+                xw[(q * 2) * 32 + lane] = ws[0];
+            }
+        }
+        __syncthreads();
+        if (active && role == 0) {
+            // (2) A: tile 0's product out of tile 1 and its share of Q, then tile 1
+            if (has(0))
+                for (int l = 0; l < 32; ++l) {
+                    const int k = l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wk(__shfl_sync(0xffffffffu, ws[0].hi, l), __shfl_sync(0xffffffffu, ws[0].lo, l));
+                    if (lane < 6) qa += wk * df_unpack(sG[6 * (k - cmin) + lane]);
+                    const int i1 = 32 + lane;
+                    if (i1 < n) w[1] = w[1] - df_unpack(sLt[tri_row_off(k, cmin, n) - (k + 1) + i1]) * wk;
+                }
+            if (has(1)) {
+                trinv_tile_chain(1, c, n, cmin, sLt, w[1], dwr[1], ws[1], lane);
+                const int i = 32 + lane;
+                if (i >= c && i < n) W[(size_t)i * ldw + c] = df_pack(ws[1]);
+                xw[(q * 2 + 1) * 32 + lane] = ws[1];
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wk(__shfl_sync(0xffffffffu, ws[1].hi, l), __shfl_sync(0xffffffffu, ws[1].lo, l));
+                    if (lane < 6) qa += wk * df_unpack(sG[6 * (k - cmin) + lane]);
+                }
+            }
+            if (lane < 6) xq[q * 6 + lane] = qa;
+        } else if (active && role == 1 && has(0)) {
+            // (2) B: tile 0's product out of rows 64 .. n-1
+            for (int l = 0; l < 32; ++l) {
+                const int k = l;
+                if (k < c) continue;
+                if (k >= n) break;
+                const dfl wk = xw[(q * 2) * 32 + l];
+                const double *lk = sLt + tri_row_off(k, cmin, n) - (k + 1);
+#pragma unroll
+                for (int tt = 0; tt < 2; ++tt) {
+                    const int i2 = 64 + 32 * tt + lane;
+                    if (i2 < n) w[tt] = w[tt] - df_unpack(lk[i2]) * wk;
+                }
+            }
+        }
+        __syncthreads();
+        if (active && role == 1) {
+            // (3) B: tile 1's product out of its rows, then tiles 2 and 3
+            qa = lane < 6 ? xq[q * 6 + lane] : dfl();
+            if (has(1))
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wk = xw[(q * 2 + 1) * 32 + l];
+                    const double *lk = sLt + tri_row_off(k, cmin, n) - (k + 1);
+#pragma unroll
+                    for (int tt = 0; tt < 2; ++tt) {
+                        const int i2 = 64 + 32 * tt + lane;
+                        if (i2 < n) w[tt] = w[tt] - df_unpack(lk[i2]) * wk;
+                    }
+                }
+#pragma unroll
+            for (int tt = 0; tt < 2; ++tt) {
+                const int t = 2 + tt;
+                if (!has(t)) continue;
+                trinv_tile_chain(t, c, n, cmin, sLt, w[tt], dwr[tt], ws[tt], lane);
+                const int i = 32 * t + lane;
+                if (i >= c && i < n) W[(size_t)i * ldw + c] = df_pack(ws[tt]);
+                for (int l = 0; l < 32; ++l) {
+                    const int k = 32 * t + l;
+                    if (k < c) continue;
+                    if (k >= n) break;
+                    const dfl wk(__shfl_sync(0xffffffffu, ws[tt].hi, l), __shfl_sync(0xffffffffu, ws[tt].lo, l));
+                    if (lane < 6) qa += wk * df_unpack(sG[6 * (k - cmin) + lane]);
+                    if (tt == 0) {
+                        const int i1 = 96 + lane;
+                        if (i1 < n) w[1] = w[1] - df_unpack(sLt[tri_row_off(k, cmin, n) - (k + 1) + i1]) * wk;
+                    }
+                }
+            }
+            // QN[c][b] = sum_a Q[c][a] N[a][b]
+            dfl qn;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const dfl qv(__shfl_sync(0xffffffffu, qa.hi, a), __shfl_sync(0xffffffffu, qa.lo, a));
+                if (lane < 6) qn += qv * df_unpack(Nm[a * 6 + lane]);
+            }
+            if (lane < 6) {
+                scr.Q(p)[6 * c + lane] = df_pack(qa);
+                scr.QN(p)[6 * c + lane] = df_pack(qn);
+                const double v = -to_double(qn);
+                P[poff[p] + (size_t)c * m + n + lane] = v;
+                P[poff[p] + (size_t)(n + lane) * m + c] = v;
+            }
         }
     }
 }
@@ -1617,14 +1805,16 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
             const int gc = (int)std::min<int64_t>(ceil_div(ng * nmax, 8), 8 * (int64_t)ctx->sm_count);
             pc_to_df_kernel<<<gc, 256, 0, s>>>(ng, st, po, P, scr);
             if (ng < ctx->sm_count) {
-                // four columns per CTA; the staged triangle of L^T and G
+                // four columns per CTA, a warp pair each; the staged triangle
+                // of L^T, G and the pairs' exchange
                 const int cg4 = (int)ceil_div(nmax, 4);
                 const int gt4 = (int)std::min<int64_t>(ng * cg4, 16 * (int64_t)ctx->sm_count);
-                const size_t tsm = sizeof(double) * ((size_t)nmax * (nmax - 1) / 2 + 6 * (size_t)nmax);
-                MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_trinv_df_kernel<true>,
+                const size_t tsm = sizeof(double) * ((size_t)nmax * (nmax - 1) / 2 + 6 * (size_t)nmax) +
+                                   sizeof(dfl) * (4 * 2 * 32 + 4 * 6);
+                MB_CUDA_TRY(ctx, cudaFuncSetAttribute(pc_trinv_df_pair_kernel,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)tsm));
-                pc_trinv_df_kernel<true><<<gt4, 128, tsm, s>>>(ng, st, po, P, scr, cg4);
+                pc_trinv_df_pair_kernel<<<gt4, 256, tsm, s>>>(ng, st, po, P, scr, cg4);
                 const int T16 = (int)ceil_div(nmax, 16), tiles16 = T16 * (T16 + 1) / 2;
                 const int gp = (int)std::min<int64_t>(ng * tiles16, 16 * (int64_t)ctx->sm_count);
                 pc_product_df_kernel<16><<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles16, schur);
