@@ -1215,17 +1215,6 @@ __global__ void __launch_bounds__(256) pc_to_df_kernel(int64_t nb,
     }
 }
 
-// S3 in double-float: warp per column c of W = L^-1, rows 32 t + lane in
-// registers, as pc_trinv_kernel; W, Q and Q N go to the scratch as packed
-// double-float, the border entries -Q N of P_p in FP64.  1 / L_kk travels
-// through the chain by shuffles from registers.  With STAGE (few bodies,
-// where the chain's latency is the time) the CTA first copies the packed
-// rows of L^T that its columns need (from its first column on; row k holds
-// entries k+1 .. n-1, rows back to back) and their rows of G into shared
-// memory, so that no step of a chain waits on L2 (the staged form; the setup
-// launches pc_trinv_df_pair_kernel for few bodies, which splits each column
-// over a pair of warps).  With many bodies the CTAs stay small and read L^T
-// and G from L2.
 __device__ __forceinline__ void cp_async8(double *smem, const double *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -1239,13 +1228,18 @@ __device__ __forceinline__ int tri_row_off(int k, int cmin, int n)
 {
     return (k - cmin) * (2 * (n - 1) - (cmin + k - 1)) / 2;
 }
-template <bool STAGE>
+
+// S3 in double-float: warp per column c of W = L^-1, rows 32 t + lane in
+// registers, as pc_trinv_kernel; W, Q and Q N go to the scratch as packed
+// double-float, the border entries -Q N of P_p in FP64.  1 / L_kk travels
+// through the chain by shuffles from registers.  L^T and G are read from
+// L2: this form serves many bodies, whose CTAs stay small; few bodies take
+// pc_trinv_df_pair_kernel.
 __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     double *__restrict__ P, SplitScratch scr, int col_groups)
 {
     constexpr int R = 4;
-    extern __shared__ double sLt[];  // rows cmin .. n-1 of L^T (packed triangle); then G
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t item = blockIdx.x; item < nb * col_groups; item += gridDim.x) {
         const int64_t p = item / col_groups;
@@ -1255,23 +1249,6 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
         // row k of L^T at Lk + (k - cmin) * ldl, row k of G at Gk + 6 (k - cmin)
         const double *Lk = P + poff[p] + (size_t)cmin * m, *Gk = scr.G(p) + 6 * cmin;
         const int ldl = m;
-        if constexpr (STAGE) {
-            double *sG = sLt + (cmin < n ? tri_row_off(n, cmin, n) : 0);
-            __syncthreads();  // the previous item is finished with sLt
-            if (cmin < n) {
-                // asynchronous copies, all in flight at once: a warp per row
-                const double *Lg = P + poff[p];
-                for (int k = cmin + warp; k < n; k += nw) {
-                    double *dst = sLt + tri_row_off(k, cmin, n) - (k + 1);
-                    for (int i = k + 1 + lane; i < n; i += 32) cp_async8(dst + i, Lg + (size_t)k * m + i);
-                }
-                for (int e = threadIdx.x; e < 6 * (n - cmin); e += blockDim.x)
-                    cp_async8(sG + e, scr.G(p) + 6 * cmin + e);
-                cp_async_wait_all();
-            }
-            __syncthreads();
-            Gk = sG;
-        }
         if (c >= n) continue;  // warp-uniform
         double *W = scr.W(p);
         const double *dW = scr.dW(p), *Nm = scr.N(p);
@@ -1286,47 +1263,7 @@ __global__ void __launch_bounds__(256) pc_trinv_df_kernel(
         dfl dwr[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) dwr[t] = 32 * t + lane < n ? df_unpack(dW[32 * t + lane]) : dfl();
-        if constexpr (STAGE) {
-            // per tile of 32 rows: the chain of its steps updates only the
-            // tile's own rows; the tile's product out of the rows below it
-            // and its share of Q follow, off the chain (each entry takes the
-            // same operations in the same order as in one pass)
-            dfl ws[R];  // lane l of tile t: W[32 t + l][c]
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
-                ws[t] = dfl();
-                if (32 * t + 31 < c) continue;
-                if (32 * t >= n) break;
-                const int i = 32 * t + lane;
-                for (int l = 0; l < 32; ++l) {
-                    const int k = 32 * t + l;
-                    if (k < c) continue;
-                    if (k >= n) break;
-                    const dfl lik = i > k && i < n ? df_unpack(sLt[tri_row_off(k, cmin, n) - (k + 1) + i])
-                                                   : dfl();
-                    const dfl wl(__shfl_sync(0xffffffffu, w[t].hi, l), __shfl_sync(0xffffffffu, w[t].lo, l));
-                    const dfl dk(__shfl_sync(0xffffffffu, dwr[t].hi, l), __shfl_sync(0xffffffffu, dwr[t].lo, l));
-                    const dfl wk = wl * dk;
-                    ws[t] = lane == l ? wk : ws[t];
-                    const dfl wn = w[t] - lik * wk;
-                    w[t] = i > k && i < n ? wn : w[t];
-                }
-                if (i >= c && i < n) W[(size_t)i * ldw + c] = df_pack(ws[t]);
-                for (int l = 0; l < 32; ++l) {
-                    const int k = 32 * t + l;
-                    if (k < c) continue;
-                    if (k >= n) break;
-                    const dfl wk(__shfl_sync(0xffffffffu, ws[t].hi, l), __shfl_sync(0xffffffffu, ws[t].lo, l));
-                    if (lane < 6) qa += wk * df_unpack(Gk[6 * (k - cmin) + lane]);
-                    const double *lk = sLt + tri_row_off(k, cmin, n) - (k + 1);
-#pragma unroll
-                    for (int t2 = t + 1; t2 < R; ++t2) {
-                        const int i2 = 32 * t2 + lane;
-                        if (i2 < n) w[t2] = w[t2] - df_unpack(lk[i2]) * wk;
-                    }
-                }
-            }
-        } else {
+        {
 #pragma unroll
             for (int t = 0; t < R; ++t) {
                 if (32 * t + 31 < c) continue;
@@ -1400,8 +1337,10 @@ __device__ __forceinline__ void trinv_tile_chain(int t, int c, int n, int cmin,
 //   3. B subtracts tile 1's product, runs tiles 2 and 3 and carries Q on
 //      from A's sums.
 // Every entry takes the same operations in the same order as in one warp
-// (pc_trinv_df_kernel).  L^T is staged in shared memory as a packed
-// triangle with cp.async, as pc_trinv_df_kernel<true> does.
+// (pc_trinv_df_kernel).  The CTA first copies the rows of L^T its columns
+// need (from its first column on; row k holds entries k+1 .. n-1, rows back
+// to back, all copies in flight at once by cp.async) and their rows of G
+// into shared memory, so that no step of a chain waits on L2.
 __global__ void __launch_bounds__(256) pc_trinv_df_pair_kernel(
     int64_t nb, const int64_t *__restrict__ start, const int64_t *__restrict__ poff,
     double *__restrict__ P, SplitScratch scr, int col_groups)
@@ -1819,7 +1758,7 @@ mb_status setup_split(mb_context *ctx, int64_t nb, const double *r, const double
                 const int gp = (int)std::min<int64_t>(ng * tiles16, 16 * (int64_t)ctx->sm_count);
                 pc_product_df_kernel<16><<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles16, schur);
             } else {
-                pc_trinv_df_kernel<false><<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
+                pc_trinv_df_kernel<<<gt, 256, 0, s>>>(ng, st, po, P, scr, col_groups);
                 const int gp = (int)std::min<int64_t>(ng * tiles, 16 * (int64_t)ctx->sm_count);
                 pc_product_df_kernel<kTile><<<gp, 256, 0, s>>>(ng, st, po, P, scr, tiles, schur);
             }
